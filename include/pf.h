@@ -1,0 +1,191 @@
+/*
+ * pf.h -- C ABI of the batched AC power-flow library (libpf).
+ *
+ * The library solves many AC power-flow scenarios that share one network
+ * (one admittance matrix Ybus and one bus-type partition) with Newton-Raphson
+ * on the polar mismatch equations, and differentiates the solution by the
+ * implicit-function theorem.  It follows SABLE (arXiv 2606.07099):
+ *
+ *   - Sec. II-A: bus sets D (PQ), G (PV), R (slack/reference, any number >= 1),
+ *     Ybus = G + jB, V_i = Vm_i e^{j theta_i}, dP = P_spec - P, dQ = Q_spec - Q;
+ *   - Sec. II-B.1, Eqs. reduced_pf_system .. step1_jacobian: Step 1 solves
+ *     F1 = [dP_{B\R}; dQ_D] = 0 for z1 = [Vm_D; theta_{B\R}] by Newton steps
+ *     J1 dz = -F1 from the flat start of Sec. IV-A;
+ *   - Eq. F2_completion: Step 2 recovers pg_R and qg_{B\D} explicitly;
+ *   - Sec. II-B.2: the backward pass solves J1^T lambda = g_z1 and maps lambda to
+ *     gradients (Eqs. chain_rule .. Jstep3_impl), here extended to the loads;
+ *   - Sec. III-B, Alg. 1: the Jacobian values are refreshed in place on one fixed
+ *     sparsity template computed once per network;
+ *   - Sec. III-C, Table I: stagewise mixed precision (FP32 factorisation and
+ *     triangular solves, FP64 mismatch, residuals and convergence control).
+ *
+ * Conventions shared by every call
+ *   - Bus arrays are row-major [batch][n_bus] float64, bus index fastest.
+ *   - bus_type: 0 = PQ (load), 1 = PV (generator), 2 = slack (reference).
+ *   - "device" pointers are CUDA device (or managed) memory owned by the caller;
+ *     "host" pointers are ordinary host memory owned by the caller and only read
+ *     during the call.  The library keeps no pointer the caller passed in.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     pf_solve / pf_adjoint only enqueue work on it and return without waiting.
+ *   - A non-PF_OK return code means the call did nothing on the device (argument
+ *     or state errors are found before any launch), except PF_ECUDA, which
+ *     reports a CUDA error raised by a launch.  Per-scenario numerical failure is
+ *     never an error code: it is reported in the per-scenario `status` array.
+ */
+#ifndef PF_H_
+#define PF_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_handle pf_handle; /* opaque; owns the network plan on host and device */
+
+typedef enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,             /* bad argument (size, pointer, bus types, CSR) */
+    PF_ESINGULAR_PATTERN = 2,  /* a bus has no path to a slack bus, or no diagonal */
+    PF_ENOMEM = 3,             /* host or device allocation failed (pf_create only) */
+    PF_ECUDA = 4,              /* a CUDA runtime call failed */
+    PF_ESTATE = 5,             /* pf_adjoint without a matching preceding pf_solve */
+    PF_ENOTSUP = 6             /* no device path for this size (reported, not faked) */
+} pf_err;
+
+/* Per-scenario outcome, written to status[b]. */
+typedef enum {
+    PF_CONVERGED = 0, /* ||F1||_inf <= tol */
+    PF_MAXITER = 1,   /* max_iter Newton steps done without reaching tol */
+    PF_DIVERGED = 2,  /* non-finite mismatch or ||F1||_inf > 1e10 */
+    PF_SINGULAR = 3   /* a pivot block of J1 was singular or non-finite */
+} pf_status;
+
+typedef enum {
+    PF_FP64 = 0,  /* every stage in FP64 */
+    PF_MIXED = 1  /* Table I: FP32 factor + solves, FP64 mismatch / residual / update,
+                     with `ir_steps` FP64-residual refinement sweeps per Newton step */
+} pf_precision;
+
+/* Read-only facts about a network plan (host side). */
+typedef struct {
+    int n_bus;         /* buses */
+    int n_slack;       /* |R| */
+    int n_pv;          /* |G| */
+    int n_pq;          /* |D| */
+    int n_unknowns;    /* |z1| = |B\R| + |D|  (Newton unknowns) */
+    int n_block;       /* 2x2 pivot blocks = |B\R| (PV buses padded with an identity row) */
+    int nnz_ybus;      /* stored Ybus entries */
+    int nnz_j1;        /* scalar nonzeros of J1 (Eq. step1_jacobian) */
+    int nnzb_lu;       /* 2x2 blocks in the filled L+U pattern */
+    int n_levels;      /* depth of the elimination tree */
+    long long schur_block_ops; /* 2x2 multiply-subtracts of one factorisation */
+} pf_plan_info;
+
+/* Tunables of a solve; zero-initialise and set what you need. */
+typedef struct {
+    int precision;     /* pf_precision */
+    int ir_steps;      /* PF_MIXED: max refinement sweeps per Newton step (0 = the paper's
+                          scheme without refinement); ignored for PF_FP64 */
+    double ir_rtol;    /* PF_MIXED: stop refining once ||r||_inf <= ir_rtol * ||F1||_inf
+                          (0 = always run ir_steps sweeps) */
+    int group_threads; /* threads per scenario (32..1024, multiple of 32; 0 = auto) */
+    int keep_factors;  /* nonzero: store each scenario's last LU factor in the workspace
+                          so that pf_adjoint can reuse it (required before pf_adjoint) */
+} pf_solve_opts;
+
+/*
+ * pf_build_ybus -- host helper: Ybus of pi-model branches (Sec. II-A's Ybus).
+ * Branch k joins f[k] -> t[k] with series impedance r[k] + j x[k], total line
+ * charging b[k] and off-nominal tap ratio tap[k] on the from side:
+ *   Yff += (ys + j b/2) / tap^2, Ytt += ys + j b/2, Yft += Ytf += -ys / tap,
+ * ys = 1 / (r + j x).  Output is CSR with sorted column indices and summed
+ * duplicates.  Call once with indices/g/bv = NULL to get *nnz; then call again
+ * with arrays of that size (indptr: n_bus + 1).  All pointers are host.
+ * Errors: PF_EINVAL for n_bus < 1, n_branch < 0, a bus index out of range, a
+ * zero series impedance or a non-positive tap, or *nnz too small on the second call.
+ */
+pf_err pf_build_ybus(int n_bus, int n_branch, const int* f, const int* t,
+                     const double* r, const double* x, const double* b, const double* tap,
+                     int* indptr, int* indices, double* g, double* bv, int* nnz);
+
+/*
+ * pf_create -- one-time symbolic analysis (Sec. III-B: pattern, indexing metadata
+ * and LU analysis built once per topology) and upload of the plan to the current
+ * CUDA device.  Host inputs: Ybus in CSR (n_bus x n_bus, y_re = G, y_im = B; any
+ * column order; duplicates are summed) and bus_type[n_bus].  The plan holds the
+ * fill-reducing ordering of the bus graph, the 2x2-block LU pattern, its
+ * elimination-tree level schedule and the Jacobian fill map.  *out receives the
+ * handle (NULL on error).  Errors: PF_EINVAL (bad sizes, bus types, no slack
+ * bus, CSR out of range), PF_ESINGULAR_PATTERN (an island without a slack bus or
+ * a non-slack bus without a diagonal entry), PF_ENOMEM, PF_ECUDA.
+ */
+pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices,
+                 const double* y_re, const double* y_im, const int* bus_type,
+                 pf_handle** out);
+
+/* Plan facts (host only, no device work).  PF_EINVAL on NULL arguments. */
+pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info);
+
+/*
+ * pf_workspace_size -- device bytes pf_solve / pf_adjoint need for `batch`
+ * scenarios with these options.  The caller allocates the workspace (any device
+ * allocator, 256-byte alignment) and passes the same buffer to pf_adjoint after
+ * pf_solve.  Errors: PF_EINVAL.
+ */
+pf_err pf_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts,
+                         size_t* bytes);
+
+/*
+ * pf_solve -- batched Newton-Raphson power flow, Step 1 + Step 2 of Sec. II-B.1.
+ * Inputs (device, [batch][n_bus]): Pd, Qd loads; Pg generation (read on PV buses
+ * only); Vset voltage set points (read on PV and slack buses only).  Flat start:
+ * Vm = 1 on PQ buses, Vset elsewhere, theta = 0.  Each scenario iterates until
+ * ||F1||_inf <= tol (checked before every Newton step) or max_iter steps.
+ * Outputs (device): Vm, Va [batch][n_bus] (the final iterate); Pg_out, Qg_out
+ * [batch][n_bus] -- the completed generation of Eq. F2_completion (Pg_out: the
+ * input pg on G, the recovered pg_R on R, 0 on D; Qg_out: recovered qg on B\D,
+ * 0 on D); iters[batch] (Newton steps taken), status[batch] (pf_status),
+ * final_mismatch[batch] (||F1||_inf of the final iterate).  Any output pointer
+ * except Vm, Va, status may be NULL.  Errors: PF_EINVAL (batch < 1, tol <= 0,
+ * max_iter < 0, NULL input, workspace too small), PF_ENOTSUP, PF_ECUDA.
+ */
+pf_err pf_solve(pf_handle* h, int batch,
+                const double* Pd, const double* Qd, const double* Pg, const double* Vset,
+                double tol, int max_iter, const pf_solve_opts* opts,
+                double* Vm, double* Va, double* Pg_out, double* Qg_out,
+                int* iters, int* status, double* final_mismatch,
+                void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * pf_adjoint -- implicit-differentiation backward pass of Sec. II-B.2 at the
+ * solution returned by the preceding pf_solve on this handle (same batch, same
+ * workspace, keep_factors set).  Cotangents (device, [batch][n_bus]; dPg and dQg
+ * may be NULL = 0): dVm, dVa, dPg, dQg with respect to the pf_solve outputs
+ * Vm, Va, Pg_out, Qg_out.  Outputs (device, [batch][n_bus]): gradients with
+ * respect to the pf_solve inputs -- dPd, dQd, dPg_in (nonzero on G only), dVset
+ * (nonzero on B\D only).  The transposed system J1^T lambda = g_z1 is solved with
+ * the stored factors of the last Newton step as preconditioner and FP64-residual
+ * refinement against J1 at the solution; a scenario whose refinement stalls is
+ * refactored at the solution.  adj_status[batch] (nullable) gets 0 on success,
+ * 3 (PF_SINGULAR) if the refactorisation failed, and copies the forward status
+ * for scenarios that did not converge (their gradients are written as 0).
+ * Errors: PF_EINVAL, PF_ESTATE (no preceding pf_solve with keep_factors, or a
+ * different batch), PF_ECUDA.
+ */
+pf_err pf_adjoint(pf_handle* h, int batch,
+                  const double* dVm, const double* dVa, const double* dPg, const double* dQg,
+                  double* dPd, double* dQd, double* dPg_in, double* dVset, int* adj_status,
+                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* pf_destroy -- frees the handle's host and device memory (waits for the device). */
+void pf_destroy(pf_handle* h);
+
+/* pf_error_string -- static text for an error code. */
+const char* pf_error_string(pf_err e);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H_ */
