@@ -1,0 +1,368 @@
+"""Benchmark of the batched AC power flow on the 118-bus / 4096-scenario workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+One step = one pf_solve over the whole batch (every Newton iteration of every
+scenario, inputs already resident on the device).  Prints one JSON line:
+converged solves/s of the mixed-precision form (FP32 factor + FP64 mismatch and
+refinement) as the headline, the all-FP64 form and the implicit layer's
+forward+backward rate beside it, the end-to-end rate through host buffers, the
+ALU/HBM roofline of the solve kernel and the CPU oracle's rate.
+
+``--impl reference`` times the CPU oracle (the plain FP64 Newton-Raphson the
+tests compare against) on the host cores instead; there is no other reference
+implementation of this method to run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c1"
+WORKLOAD_DESC = ("synthetic 118-bus meshed grid (186 branches, 9 transformers, 1 slack, 53 PV, "
+                 "64 PQ), 4096 load scenarios x U(0.7, 1.3), flat start, tol 1e-8 pu, max 20 iterations")
+METRIC = "PF solves/s at <=1e-8 pu mismatch (mixed precision form)"
+UNIT = "solves/s"
+L2_FLUSH_BYTES = 256 << 20
+# Peaks for the roofline.  HBM: measured copy bandwidth of this GPU family.
+# ALU: FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 = 1.25 TFLOP/s nominal.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- oracle leg (CPU)
+def _oracle_chunk(args):
+    name, lo, hi = args
+    sys.path.insert(0, ROOT)
+    import oracle.pf_oracle as O
+    from synthgrid import configs
+    g = configs.grid(name)
+    sc = configs.scenarios(name, g=g)
+    Y = O.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+    conv = 0
+    for s in range(lo, hi):
+        r = O.nr_solve(Y, g.bus_type, sc.Pd[s], sc.Qd[s], sc.Pg[s], sc.Vset[s], 1e-8, 20)
+        conv += r["status"] == 0
+    return conv
+
+
+def oracle_rate(n_sample: int):
+    """Converged solves/s of the CPU oracle on the first n_sample scenarios, all cores."""
+    cores = os.cpu_count() or 1
+    procs = max(1, min(cores, n_sample))
+    bounds = np.linspace(0, n_sample, procs + 1).astype(int)
+    chunks = [(WORKLOAD, int(bounds[i]), int(bounds[i + 1])) for i in range(procs)]
+    # one BLAS thread per worker process: the workers are the parallelism
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_chunk, [(WORKLOAD, 0, 1)] * procs)  # warm the workers (imports)
+        t0 = time.perf_counter()
+        conv = sum(pool.map(_oracle_chunk, chunks))
+        dt = time.perf_counter() - t0
+    return conv / dt, procs, dt, conv
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for k, nm in enumerate(names):
+            if any(r[5 + k].strip().lower().startswith("active") for r in rows if len(r) > 5 + k):
+                reasons.append(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU leg
+def alg_counts(info: dict, n_bus: int, iters: np.ndarray, ir_steps: int, precision: str):
+    """Algorithmic FP64 / FP32 flops and HBM bytes of one pf_solve launch.
+
+    Per Newton iteration of one scenario: the FP64 mismatch (complex SpMV, 8
+    flop per Ybus entry, plus ~20 flop per bus for V, S and F), the Jacobian
+    fill (~12 flop per 2x2 block, FP64), the block LU (16 flop per Schur block
+    update, ~24 per L-column scaling), the triangular solves (8 flop per stored
+    block per sweep pair member), and per refinement sweep a matrix-free FP64
+    residual (another complex SpMV + ~30 flop per bus) and one more solve.  One
+    final mismatch evaluation per scenario follows the last update.
+    """
+    nnzY, nnzb, nb = info["nnz_ybus"], info["nnzb_lu"], info["n_block"]
+    schur, la = info["schur_block_ops"], nnzb - nb  # L entries scaled once each (half of off-diag)
+    it = float(iters.sum())
+    n_sc = iters.shape[0]
+    mism = 8 * nnzY + 20 * n_bus
+    fill = 12 * nnzb
+    lu = 16 * schur + 24 * (la // 2) + 10 * nb
+    solve = 8 * nnzb
+    resid = 8 * nnzY + 30 * n_bus
+    mixed = precision == "mixed"
+    f64 = (it + n_sc) * mism + it * fill + (it * ir_steps * resid if mixed else 0)
+    fsolve = it * (lu + solve * (1 + (ir_steps if mixed else 0)))
+    f32 = fsolve if mixed else 0.0
+    if not mixed:
+        f64 += fsolve
+    hbm = n_sc * (8 * 4 * n_bus + 8 * 4 * n_bus + 16 + 16 * n_bus + 16)
+    return f64, f32, hbm
+
+
+def gpu_leg(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_07099_gb300.powerflow import PowerFlow
+    from synthgrid import configs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    g = configs.grid(WORKLOAD)
+    sc = configs.scenarios(WORKLOAD, g=g)
+    N, nb = sc.n, g.n_bus
+    pf = PowerFlow.from_grid(g)
+    info = pf.info()
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (sc.Pd, sc.Qd, sc.Pg, sc.Vset)]
+    Pd, Qd, Pg, Vset = [h.to(dev) for h in host]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.fill_(1)  # evict the previous step's data from L2 (outside the timed events)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        barrier()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    opts = dict(precision="mixed", ir_steps=args.ir_steps, ir_rtol=args.ir_rtol)
+    res = pf.solve(Pd, Qd, Pg, Vset, **opts)
+    mixed_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **opts)  # noqa: E731
+    res64 = pf.solve(Pd, Qd, Pg, Vset, precision="fp64")
+    fp64_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64)  # noqa: E731
+
+    # forward + backward of the implicit layer with the config-2 style loss cotangents
+    slack = torch.as_tensor(g.bus_type == 2, device=dev)
+    resk = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, **opts)
+
+    def fwd_bwd():
+        r = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, out=resk, **opts)
+        Vm = r.Vm
+        dVm = 2 * torch.relu(Vm - 1.06) - 2 * torch.relu(0.94 - Vm)
+        dPg = 2 * r.Pg * slack
+        pf.adjoint(dVm, torch.zeros_like(Vm), dPg, None)
+
+    # end to end through the public API with host buffers
+    out_host = [torch.empty(N, nb, dtype=torch.float64).pin_memory() for _ in range(2)]
+    st_host = torch.empty(N, dtype=torch.int32).pin_memory()
+    dev_in = [torch.empty_like(Pd) for _ in range(4)]
+    rese = pf.solve(Pd, Qd, Pg, Vset, **opts)
+
+    def e2e():
+        for d, h in zip(dev_in, host):
+            d.copy_(h, non_blocking=True)
+        pf.solve(*dev_in, out=rese, **opts)
+        out_host[0].copy_(rese.Vm, non_blocking=True)
+        out_host[1].copy_(rese.Va, non_blocking=True)
+        st_host.copy_(rese.status, non_blocking=True)
+
+    with ClockSampler(dev.index) as clk:
+        t_mixed = timed(mixed_fn, args.steps, args.warmup)
+        t_fp64 = timed(fp64_fn, args.steps, args.warmup)
+        t_fb = timed(fwd_bwd, args.steps, args.warmup)
+        t_e2e = timed(e2e, args.steps, args.warmup)
+    clocks = clk.summary()
+    torch.cuda.synchronize(dev)
+    st = res.status.cpu().numpy()
+    its = res.iters.cpu().numpy()
+    conv = int((st == 0).sum())
+    conv64 = int((res64.status.cpu().numpy() == 0).sum())
+    conve = int((rese.status.cpu().numpy() == 0).sum())
+    fmax = float(res.final_mismatch.max().item())
+
+    def agg(ts):
+        tot = sum(ts)
+        if world > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return tot
+
+    T_mixed, T_fp64, T_fb, T_e2e = (agg(t) for t in (t_mixed, t_fp64, t_fb, t_e2e))
+    K = args.steps
+    value = world * conv * K / (T_mixed / 1e3)
+    ms_launch = statistics.mean(t_mixed)
+    f64, f32, hbm_bytes = alg_counts(info, nb, its, args.ir_steps, "mixed")
+    # ALU roofline: the kernel needs at least max(F64/peak64, F32/peak32) seconds
+    t_alu = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
+    achieved_eq = (t_alu * FP64_PEAK_TFLOPS * 1e12) / (ms_launch / 1e3) / 1e12
+    hbm_peak_gbs, hbm_src = hbm_peak()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": T_mixed / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "n_bus": nb, "batch_per_gpu": N,
+                   "global_batch": N * world, "precision": "mixed (FP32 LU + FP64 mismatch/refinement)",
+                   "ir_steps": args.ir_steps, "ir_rtol": args.ir_rtol,
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "parallelism": f"replicas x{world} (scenarios sharded, no collective)"},
+        "converged": conv, "max_final_mismatch": fmax, "mean_iters": float(its.mean()),
+        "fp64_form": {"value": world * conv64 * K / (T_fp64 / 1e3), "unit": UNIT,
+                      "ms_per_step": T_fp64 / K, "mixed_speedup": T_fp64 / T_mixed},
+        "fwd_bwd": {"value": world * N * K / (T_fb / 1e3), "unit": "fwd+bwd/s",
+                    "ms_per_step": T_fb / K},
+        "e2e": {"value": world * conve * K / (T_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N},
+        "gpu_launches": K,
+        "roofline": {"bound": "alu", "achieved": achieved_eq, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_eq / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "nr_solve_kernel<float>",
+                     "note": ("FP64-equivalent rate: F64 + F32*(peak64/peak32) flops per launch over "
+                              "the launch time; peaks derived from unit counts (FP32 "
+                              f"{FP32_PEAK_TFLOPS:.1f}, FP64 {FP64_PEAK_TFLOPS} TFLOP/s nominal)"),
+                     "flops_f64": f64, "flops_f32": f32},
+        "hbm": {"achieved_gbs": hbm_bytes / (ms_launch / 1e3) / 1e9, "peak_gbs": hbm_peak_gbs,
+                "peak_source": hbm_src, "frac": hbm_bytes / (ms_launch / 1e3) / 1e9 / hbm_peak_gbs,
+                "bytes_per_launch": hbm_bytes},
+        "clocks": clocks,
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ir-steps", type=int, default=1)
+    ap.add_argument("--ir-rtol", type=float, default=0.0)
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the CPU oracle on a bounded sample of the workload, per step
+        per_step = max(16, args.cpu_sample // 4)
+        rates = []
+        for _ in range(args.steps):
+            r, procs, dt, conv = oracle_rate(per_step)
+            rates.append(r)
+        v = statistics.median(rates)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "ms_per_step": 1e3 * per_step / v, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "n_bus": 118, "batch_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": f"first {per_step} of the 4096 scenarios per step",
+                             "cpu": cpu_model()},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    line = gpu_leg(args, rank, world)
+    if rank == 0:
+        r, procs, dt, conv = oracle_rate(args.cpu_sample)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": f"first {args.cpu_sample} of the 4096 scenarios "
+                                          f"({dt:.1f} s wall)", "cpu": cpu_model()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

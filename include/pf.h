@@ -124,6 +124,20 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices,
                  const double* y_re, const double* y_im, const int* bus_type,
                  pf_handle** out);
 
+/*
+ * pf_analyze -- the host half of pf_create without any device work: validates the
+ * network and runs the symbolic analysis, then reports the plan.  Inputs as in
+ * pf_create (host).  If pos2bus / lu_ptr / lu_col / lev_ptr are non-NULL they
+ * receive the block ordering (pos2bus[n_block]: bus of pivot position p), the
+ * filled L+U block pattern in CSR over positions (lu_ptr[n_block + 1],
+ * lu_col[nnzb_lu]) and the level ranges (lev_ptr[n_levels + 1]); call first with
+ * them NULL to learn the sizes from *info.  Errors as pf_create, minus
+ * PF_ENOMEM / PF_ECUDA.
+ */
+pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices,
+                  const double* y_re, const double* y_im, const int* bus_type,
+                  pf_plan_info* info, int* pos2bus, int* lu_ptr, int* lu_col, int* lev_ptr);
+
 /* Plan facts (host only, no device work).  PF_EINVAL on NULL arguments. */
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info);
 

@@ -1,0 +1,83 @@
+"""ctypes declarations of libpf (the C ABI in include/pf.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpf.so")
+
+PF_OK, PF_EINVAL, PF_ESINGULAR_PATTERN, PF_ENOMEM, PF_ECUDA, PF_ESTATE, PF_ENOTSUP = range(7)
+PF_CONVERGED, PF_MAXITER, PF_DIVERGED, PF_SINGULAR = range(4)
+PF_FP64, PF_MIXED = 0, 1
+
+# every function and its (restype, argtypes); the CPU tests check this list against pf.h
+_p = C.c_void_p
+_i = C.c_int
+_d = C.c_double
+_sz = C.c_size_t
+_ip = C.POINTER(C.c_int)
+_dp = C.POINTER(C.c_double)
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n_bus", C.c_int), ("n_slack", C.c_int), ("n_pv", C.c_int), ("n_pq", C.c_int),
+                ("n_unknowns", C.c_int), ("n_block", C.c_int), ("nnz_ybus", C.c_int),
+                ("nnz_j1", C.c_int), ("nnzb_lu", C.c_int), ("n_levels", C.c_int),
+                ("schur_block_ops", C.c_longlong)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("ir_steps", C.c_int), ("ir_rtol", C.c_double),
+                ("group_threads", C.c_int), ("keep_factors", C.c_int)]
+
+
+SIGNATURES = {
+    "pf_build_ybus": (_i, [_i, _i, _ip, _ip, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _ip]),
+    "pf_create": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(_p)]),
+    "pf_analyze": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanInfo), _ip, _ip, _ip, _ip]),
+    "pf_get_plan_info": (_i, [_p, C.POINTER(PlanInfo)]),
+    "pf_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
+    "pf_solve": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
+                      _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_adjoint": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_destroy": (None, [_p]),
+    "pf_error_string": (C.c_char_p, [_i]),
+}
+
+_lib = None
+
+
+class PFError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (code {code})")
+
+
+def load() -> C.CDLL:
+    """Load libpf.so from the package directory; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpf.so is not built ({LIB_PATH}); run "
+                          "`python -m paper_2606_07099_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def error_string(code: int) -> str:
+    try:
+        return load().pf_error_string(code).decode()
+    except Exception:
+        return "error"
+
+
+def check(code: int, where: str) -> None:
+    if code != PF_OK:
+        raise PFError(code, where)

@@ -1,0 +1,393 @@
+// pf_api.cpp -- the C ABI of libpf (declared in include/pf.h).
+//
+// Host-side responsibilities only: argument checks, the one-time plan
+// (pf_plan.cpp), its upload, the shared-memory/workspace layout of a solve, and
+// the kernel launches (pf_kernels.cu).  No numerical work runs here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_launch.h"
+#include "pf_plan.h"
+
+struct pf_handle {
+    pf::Plan plan;
+    int device = 0;
+    int smem_optin = 0;
+    int num_sms = 0;
+    void* d_buf = nullptr;
+    pf::DevPlan dp{};
+    // state of the last pf_solve (for pf_adjoint)
+    int last_batch = -1;
+    int last_ft = 0;
+    int last_keep = 0;
+    int last_threads = 0;
+    const void* last_ws = nullptr;
+    pf::SlotLayout last_layout{};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+int auto_threads(int n) {
+    if (n <= 48) return 32;
+    if (n <= 400) return 64;
+    if (n <= 1600) return 128;
+    if (n <= 6000) return 256;
+    return 512;
+}
+
+// Shared memory reserved for the kernels' static arrays and the runtime.
+constexpr size_t kStaticSmemReserve = 1024;
+
+pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep) {
+    const pf::Plan& P = h->plan;
+    pf::SlotLayout L{};
+    L.vec_bytes = pf::carve(nullptr, P.n_bus, P.n, ft_bytes, nullptr);
+    L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
+    const size_t budget = (size_t)h->smem_optin > kStaticSmemReserve
+                              ? (size_t)h->smem_optin - kStaticSmemReserve : 0;
+    if (L.vec_bytes + L.fac_bytes <= budget) {
+        L.vec_in_smem = 1;
+        L.fac_in_smem = 1;
+        L.smem_fac_off = L.vec_bytes;
+        L.smem_bytes = L.vec_bytes + L.fac_bytes;
+    } else if (L.vec_bytes <= budget) {
+        L.vec_in_smem = 1;
+        L.fac_in_smem = 0;
+        L.smem_bytes = L.vec_bytes;
+    } else {
+        L.vec_in_smem = 0;
+        L.fac_in_smem = 0;
+        L.smem_bytes = 0;
+    }
+    L.fac_global = (!L.fac_in_smem || keep) ? 1 : 0;
+    size_t o = 0;
+    L.off_state = o;
+    o = pf::align_up(o + sizeof(double) * 2 * (size_t)P.n_bus, 256);
+    L.off_flags = o;
+    o = pf::align_up(o + 16, 256);
+    if (L.fac_global) {
+        L.off_fac = o;
+        o = pf::align_up(o + L.fac_bytes, 256);
+    }
+    if (!L.vec_in_smem) {
+        L.off_vec = o;
+        o = pf::align_up(o + L.vec_bytes, 256);
+    }
+    L.slot_bytes = o;
+    return L;
+}
+
+bool opts_ok(const pf_solve_opts* o) {
+    if (!o) return false;
+    if (o->precision != PF_FP64 && o->precision != PF_MIXED) return false;
+    if (o->ir_steps < 0 || o->ir_steps > 64) return false;
+    if (!(o->ir_rtol >= 0.0)) return false;
+    if (o->group_threads != 0 &&
+        (o->group_threads < 32 || o->group_threads > 1024 || o->group_threads % 32)) return false;
+    return true;
+}
+
+template <typename T>
+size_t push(std::vector<unsigned char>& buf, const std::vector<T>& v) {
+    size_t off = pf::align_up(buf.size(), 16);
+    buf.resize(off + sizeof(T) * v.size());
+    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), sizeof(T) * v.size());
+    return off;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pf_error_string(pf_err e) {
+    switch (e) {
+        case PF_OK: return "ok";
+        case PF_EINVAL: return "invalid argument";
+        case PF_ESINGULAR_PATTERN: return "singular network pattern (island without slack or missing diagonal)";
+        case PF_ENOMEM: return "out of memory";
+        case PF_ECUDA: return "CUDA error";
+        case PF_ESTATE: return "no matching pf_solve state for pf_adjoint";
+        case PF_ENOTSUP: return "not supported";
+    }
+    return "unknown error";
+}
+
+pf_err pf_build_ybus(int n_bus, int n_branch, const int* f, const int* t, const double* r,
+                     const double* x, const double* b, const double* tap, int* indptr,
+                     int* indices, double* g, double* bv, int* nnz) {
+    if (n_bus < 1 || n_branch < 0 || !nnz || !indptr) return PF_EINVAL;
+    if (n_branch > 0 && (!f || !t || !r || !x || !b || !tap)) return PF_EINVAL;
+    std::vector<std::vector<std::pair<int, std::complex<double>>>> rows(n_bus);
+    for (int k = 0; k < n_branch; ++k) {
+        if (f[k] < 0 || f[k] >= n_bus || t[k] < 0 || t[k] >= n_bus) return PF_EINVAL;
+        std::complex<double> z(r[k], x[k]);
+        if (std::abs(z) == 0.0 || !(tap[k] > 0.0)) return PF_EINVAL;
+        const std::complex<double> ys = 1.0 / z, sh(0.0, 0.5 * b[k]);
+        const double a = tap[k];
+        rows[f[k]].push_back({f[k], (ys + sh) / (a * a)});
+        rows[t[k]].push_back({t[k], ys + sh});
+        rows[f[k]].push_back({t[k], -ys / a});
+        rows[t[k]].push_back({f[k], -ys / a});
+    }
+    int count = 0;
+    indptr[0] = 0;
+    std::vector<std::vector<std::pair<int, std::complex<double>>>> merged(n_bus);
+    for (int i = 0; i < n_bus; ++i) {
+        auto& rw = rows[i];
+        std::stable_sort(rw.begin(), rw.end(),
+                         [](const auto& p, const auto& q) { return p.first < q.first; });
+        for (auto& e : rw) {
+            if (!merged[i].empty() && merged[i].back().first == e.first) merged[i].back().second += e.second;
+            else merged[i].push_back(e);
+        }
+        count += (int)merged[i].size();
+        indptr[i + 1] = count;
+    }
+    if (!indices || !g || !bv) {
+        *nnz = count;
+        return PF_OK;
+    }
+    if (*nnz < count) return PF_EINVAL;
+    int o = 0;
+    for (int i = 0; i < n_bus; ++i)
+        for (auto& e : merged[i]) {
+            indices[o] = e.first;
+            g[o] = e.second.real();
+            bv[o] = e.second.imag();
+            ++o;
+        }
+    *nnz = count;
+    return PF_OK;
+}
+
+pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
+                 const double* y_im, const int* bus_type, pf_handle** out) {
+    if (!out) return PF_EINVAL;
+    *out = nullptr;
+    pf_handle* h = new (std::nothrow) pf_handle();
+    if (!h) return PF_ENOMEM;
+    pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, h->plan);
+    if (bs != pf::BUILD_OK) {
+        delete h;
+        return bs == pf::BUILD_ESINGULAR ? PF_ESINGULAR_PATTERN : PF_EINVAL;
+    }
+    const pf::Plan& P = h->plan;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return PF_ECUDA;
+    }
+    // pack every plan array into one device buffer
+    std::vector<unsigned char> buf;
+    std::vector<double2> ygb(P.y_g.size()), ytgb(P.yt_g.size());
+    for (size_t k = 0; k < P.y_g.size(); ++k) ygb[k] = make_double2(P.y_g[k], P.y_b[k]);
+    for (size_t k = 0; k < P.yt_g.size(); ++k) ytgb[k] = make_double2(P.yt_g[k], P.yt_b[k]);
+    std::vector<int2> la(P.la_L.size()), sch(P.sch_L.size());
+    for (size_t k = 0; k < la.size(); ++k) la[k] = make_int2(P.la_L[k], P.la_D[k]);
+    for (size_t k = 0; k < sch.size(); ++k) sch[k] = make_int2(P.sch_L[k], P.sch_U[k]);
+    size_t o_ygb = push(buf, ygb), o_ytgb = push(buf, ytgb);
+    size_t o_yptr = push(buf, P.y_ptr), o_yidx = push(buf, P.y_idx);
+    size_t o_ytptr = push(buf, P.yt_ptr), o_ytidx = push(buf, P.yt_idx);
+    size_t o_bt = push(buf, P.bus_type), o_p2b = push(buf, P.pos2bus), o_b2p = push(buf, P.bus2pos);
+    size_t o_lev = push(buf, P.lev_ptr), o_lup = push(buf, P.lu_ptr), o_lur = push(buf, P.lu_row);
+    size_t o_luc = push(buf, P.lu_col), o_lud = push(buf, P.lu_diag), o_lum = push(buf, P.lu_mirror);
+    size_t o_fy = push(buf, P.fill_y), o_lap = push(buf, P.la_ptr), o_la = push(buf, la);
+    size_t o_stp = push(buf, P.sch_tptr), o_stg = push(buf, P.sch_tgt), o_scp = push(buf, P.sch_cptr);
+    size_t o_sch = push(buf, sch);
+    if (buf.empty()) buf.resize(16);
+    if (cudaMalloc(&h->d_buf, buf.size()) != cudaSuccess) {
+        delete h;
+        return PF_ENOMEM;
+    }
+    if (cudaMemcpy(h->d_buf, buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(h->d_buf);
+        delete h;
+        return PF_ECUDA;
+    }
+    auto* base = static_cast<unsigned char*>(h->d_buf);
+    auto I = [&](size_t o) { return reinterpret_cast<const int*>(base + o); };
+    pf::DevPlan& d = h->dp;
+    d.n_bus = P.n_bus;
+    d.n = P.n;
+    d.nnzb = P.nnzb();
+    d.n_levels = P.n_levels;
+    d.y_ptr = I(o_yptr);
+    d.y_idx = I(o_yidx);
+    d.y_gb = reinterpret_cast<const double2*>(base + o_ygb);
+    d.yt_ptr = I(o_ytptr);
+    d.yt_idx = I(o_ytidx);
+    d.yt_gb = reinterpret_cast<const double2*>(base + o_ytgb);
+    d.bus_type = I(o_bt);
+    d.pos2bus = I(o_p2b);
+    d.bus2pos = I(o_b2p);
+    d.lev_ptr = I(o_lev);
+    d.lu_ptr = I(o_lup);
+    d.lu_row = I(o_lur);
+    d.lu_col = I(o_luc);
+    d.lu_diag = I(o_lud);
+    d.lu_mirror = I(o_lum);
+    d.fill_y = I(o_fy);
+    d.la_ptr = I(o_lap);
+    d.la = reinterpret_cast<const int2*>(base + o_la);
+    d.sch_tptr = I(o_stp);
+    d.sch_tgt = I(o_stg);
+    d.sch_cptr = I(o_scp);
+    d.sch = reinterpret_cast<const int2*>(base + o_sch);
+    *out = h;
+    return PF_OK;
+}
+
+static void fill_info(const pf::Plan& P, pf_plan_info* info) {
+    info->n_bus = P.n_bus;
+    info->n_slack = P.n_slack;
+    info->n_pv = P.n_pv;
+    info->n_pq = P.n_pq;
+    info->n_unknowns = (P.n_bus - P.n_slack) + P.n_pq;
+    info->n_block = P.n;
+    info->nnz_ybus = (int)P.y_idx.size();
+    info->nnz_j1 = P.nnz_j1;
+    info->nnzb_lu = P.nnzb();
+    info->n_levels = P.n_levels;
+    info->schur_block_ops = P.schur_ops;
+}
+
+pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info) {
+    if (!h || !info) return PF_EINVAL;
+    fill_info(h->plan, info);
+    return PF_OK;
+}
+
+pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
+                  const double* y_im, const int* bus_type, pf_plan_info* info, int* pos2bus,
+                  int* lu_ptr, int* lu_col, int* lev_ptr) {
+    if (!info) return PF_EINVAL;
+    pf::Plan P;
+    pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, P);
+    if (bs != pf::BUILD_OK) return bs == pf::BUILD_ESINGULAR ? PF_ESINGULAR_PATTERN : PF_EINVAL;
+    fill_info(P, info);
+    if (pos2bus) std::copy(P.pos2bus.begin(), P.pos2bus.end(), pos2bus);
+    if (lu_ptr) std::copy(P.lu_ptr.begin(), P.lu_ptr.end(), lu_ptr);
+    if (lu_col) std::copy(P.lu_col.begin(), P.lu_col.end(), lu_col);
+    if (lev_ptr) std::copy(P.lev_ptr.begin(), P.lev_ptr.end(), lev_ptr);
+    return PF_OK;
+}
+
+pf_err pf_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts, size_t* bytes) {
+    if (!h || !bytes || batch < 1 || !opts_ok(opts)) return PF_EINVAL;
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors);
+    *bytes = L.slot_bytes * (size_t)batch;
+    return PF_OK;
+}
+
+pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
+                const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
+                double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
+                double* final_mismatch, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
+        return PF_EINVAL;
+    if (!(tol > 0.0) || max_iter < 0 || !opts_ok(opts)) return PF_EINVAL;
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors);
+    if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
+    const int threads = opts->group_threads ? opts->group_threads : auto_threads(h->plan.n);
+    DeviceGuard guard(h->device);
+    pf::SolveArgs A{};
+    A.batch = batch;
+    A.tol = tol;
+    A.max_iter = max_iter;
+    A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
+    A.ir_rtol = opts->ir_rtol;
+    A.keep_factors = opts->keep_factors ? 1 : 0;
+    A.Pd = Pd;
+    A.Qd = Qd;
+    A.Pg = Pg;
+    A.Vset = Vset;
+    A.Vm = Vm;
+    A.Va = Va;
+    A.Pg_out = Pg_out;
+    A.Qg_out = Qg_out;
+    A.fmis = final_mismatch;
+    A.iters = iters;
+    A.status = status;
+    A.ws = static_cast<char*>(workspace);
+    A.L = L;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = ft == 4 ? pf::launch_solve<float>(h->dp, A, threads, s)
+                            : pf::launch_solve<double>(h->dp, A, threads, s);
+    if (e != cudaSuccess) {
+        h->last_batch = -1;
+        return PF_ECUDA;
+    }
+    h->last_batch = batch;
+    h->last_ft = ft;
+    h->last_keep = A.keep_factors;
+    h->last_threads = threads;
+    h->last_ws = workspace;
+    h->last_layout = L;
+    return PF_OK;
+}
+
+pf_err pf_adjoint(pf_handle* h, int batch, const double* dVm, const double* dVa, const double* dPg,
+                  const double* dQg, double* dPd, double* dQd, double* dPg_in, double* dVset,
+                  int* adj_status, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!h || batch < 1 || !dVm || !dVa || !dPd || !dQd || !dPg_in || !dVset || !workspace)
+        return PF_EINVAL;
+    if (h->last_batch != batch || !h->last_keep || h->last_ws != workspace) return PF_ESTATE;
+    const pf::SlotLayout& L = h->last_layout;
+    if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    pf::AdjArgs A{};
+    A.batch = batch;
+    A.ir_max = 8;
+    A.ir_rtol = 1e-12;
+    A.dVm = dVm;
+    A.dVa = dVa;
+    A.dPg = dPg;
+    A.dQg = dQg;
+    A.dPd = dPd;
+    A.dQd = dQd;
+    A.dPg_in = dPg_in;
+    A.dVset = dVset;
+    A.adj_status = adj_status;
+    A.ws = static_cast<char*>(workspace);
+    A.L = L;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = h->last_ft == 4 ? pf::launch_adjoint<float>(h->dp, A, h->last_threads, s)
+                                    : pf::launch_adjoint<double>(h->dp, A, h->last_threads, s);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+void pf_destroy(pf_handle* h) {
+    if (!h) return;
+    if (h->d_buf) {
+        DeviceGuard guard(h->device);
+        cudaDeviceSynchronize();
+        cudaFree(h->d_buf);
+    }
+    delete h;
+}
+
+}  // extern "C"

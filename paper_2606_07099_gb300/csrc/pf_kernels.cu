@@ -1,0 +1,655 @@
+// pf_kernels.cu -- the batched Newton-Raphson power flow and its adjoint on sm_103a.
+//
+// One CTA owns one scenario at a time (the grid has one CTA per scenario, so the
+// hardware block scheduler balances scenarios that need different iteration
+// counts).  Every step of a Newton iteration runs inside the same kernel, on the
+// scenario's state staged in shared memory when it fits:
+//
+//   mismatch  I = Y V, S = V conj(I), F1 = spec - S           (Sec. II-A, FP64)
+//   fill      polar 2x2 Jacobian blocks on the fixed pattern  (Alg. 1 values)
+//   factor    level-scheduled right-looking 2x2-block LU      (FT = float | double)
+//   solve     level-scheduled block triangular sweeps         (FT)
+//   refine    FP64 residual r = -F1 - J1 dz (matrix-free)     (Table I + refinement)
+//   update    theta_{B\R} += dtheta, Vm_D += dVm              (FP64)
+//
+// until ||F1||_inf <= tol; then Step 2 (Eq. F2_completion) writes the recovered
+// generation.  The convergence decision is taken on the device per scenario;
+// the host never waits inside the loop.
+#include <cfloat>
+#include <cmath>
+
+#include "pf_device.cuh"
+
+namespace pf {
+
+// ---------------------------------------------------------------- small helpers
+template <typename T>
+struct Blk {
+    T a, b, c, d;  // [[a, b], [c, d]]: rows (dP, dQ), columns (theta, Vm)
+};
+
+__device__ __forceinline__ Blk<float> ldb(const float* f, int e) {
+    float4 v = reinterpret_cast<const float4*>(f)[e];
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Blk<double> ldb(const double* f, int e) {
+    const double2* p = reinterpret_cast<const double2*>(f) + 2 * e;
+    double2 u = p[0], w = p[1];
+    return {u.x, u.y, w.x, w.y};
+}
+__device__ __forceinline__ void stb(float* f, int e, Blk<float> v) {
+    reinterpret_cast<float4*>(f)[e] = make_float4(v.a, v.b, v.c, v.d);
+}
+__device__ __forceinline__ void stb(double* f, int e, Blk<double> v) {
+    double2* p = reinterpret_cast<double2*>(f) + 2 * e;
+    p[0] = make_double2(v.a, v.b);
+    p[1] = make_double2(v.c, v.d);
+}
+template <typename T>
+__device__ __forceinline__ Blk<T> mul(Blk<T> x, Blk<T> y) {
+    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c,
+            x.c * y.b + x.d * y.d};
+}
+// x - y*z
+template <typename T>
+__device__ __forceinline__ Blk<T> msub(Blk<T> x, Blk<T> y, Blk<T> z) {
+    return {x.a - (y.a * z.a + y.b * z.c), x.b - (y.a * z.b + y.b * z.d),
+            x.c - (y.c * z.a + y.d * z.c), x.d - (y.c * z.b + y.d * z.d)};
+}
+// inverse of a 2x2 block; *bad = 1 if (numerically) singular or non-finite
+template <typename T>
+__device__ __forceinline__ Blk<T> inv2(Blk<T> m, int* bad) {
+    T det = m.a * m.d - m.b * m.c;
+    T amax = fmax(fmax(fabs(m.a), fabs(m.b)), fmax(fabs(m.c), fabs(m.d)));
+    if (!(fabs(det) > T(1e-30) * amax * amax) || !(amax < T(INFINITY))) *bad = 1;
+    T r = T(1) / det;
+    return {m.d * r, -m.b * r, -m.c * r, m.a * r};
+}
+
+template <typename T>
+__device__ __forceinline__ T* ftptr(void* p) { return reinterpret_cast<T*>(p); }
+
+__device__ __forceinline__ void gsync() {
+    if (blockDim.x == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// |v| with non-finite values mapped to +inf (so that max-reductions see them)
+__device__ __forceinline__ double absinf(double v) {
+    double a = fabs(v);
+    return (a <= DBL_MAX) ? a : INFINITY;
+}
+
+// Group-wide max; every thread gets the result.  `red` holds one double per warp.
+__device__ double group_max(double v, double* red) {
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (blockDim.x == 32) {
+        __syncwarp();  // also orders the shared-memory writes of the phase that reduced
+        return v;
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int i = 1; i < nw; ++i) r = fmax(r, red[i]);
+    return r;
+}
+
+// ---------------------------------------------------------------- FP64 network kernels
+// V = Vm e^{j theta}
+__device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        double s, c;
+        sincos(a.Va[i], &s, &c);
+        a.Vre[i] = a.Vm[i] * c;
+        a.Vim[i] = a.Vm[i] * s;
+    }
+}
+
+// I = Y V, S = V conj(I), F1 at pivot positions; returns ||F1||_inf (inf if non-finite)
+__device__ double phase_mismatch(const DevPlan& P, const Arrays& a, double* red) {
+    double lmax = 0.0;
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        double ir = 0.0, ii = 0.0;
+        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+            const int j = P.y_idx[k];
+            const double2 y = P.y_gb[k];
+            const double vr = a.Vre[j], vi = a.Vim[j];
+            ir = fma(y.x, vr, fma(-y.y, vi, ir));
+            ii = fma(y.x, vi, fma(y.y, vr, ii));
+        }
+        a.Ire[i] = ir;
+        a.Iim[i] = ii;
+        const int p = P.bus2pos[i];
+        if (p >= 0) {
+            const double vr = a.Vre[i], vi = a.Vim[i];
+            const double Pi = vr * ir + vi * ii;
+            const double Qi = vi * ir - vr * ii;
+            const double fP = a.Psp[i] - Pi;
+            const double fQ = (P.bus_type[i] == 0) ? a.Qsp[i] - Qi : 0.0;
+            a.F[2 * p] = fP;
+            a.F[2 * p + 1] = fQ;
+            lmax = fmax(lmax, fmax(absinf(fP), absinf(fQ)));
+        }
+    }
+    return group_max(lmax, red);
+}
+
+// G_j = conj(m_j I_j) + sum_i m_i conj(V_i) Y_ij;  w0_j = Re(G_j u_j) = d(m.S)/dVm_j,
+// w1_j = -Im(G_j V_j) = d(m.S)/dtheta_j, for the injection weights m = mP + j mQ held in
+// (Psp, Qsp).  This is (d[P;Q]/d[Vm;theta])^T [mP; mQ] without forming the Jacobian.
+__device__ void phase_jvt(const DevPlan& P, const Arrays& a) {
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const double mr = a.Psp[i], mi = a.Qsp[i];
+        // h = m conj(V)
+        a.dVre[i] = mr * a.Vre[i] + mi * a.Vim[i];
+        a.dVim[i] = mi * a.Vre[i] - mr * a.Vim[i];
+    }
+    gsync();
+    for (int j = threadIdx.x; j < P.n_bus; j += blockDim.x) {
+        double gr = 0.0, gi = 0.0;
+        for (int k = P.yt_ptr[j]; k < P.yt_ptr[j + 1]; ++k) {
+            const int i = P.yt_idx[k];
+            const double2 y = P.yt_gb[k];  // Y_ij
+            const double hr = a.dVre[i], hi = a.dVim[i];
+            gr = fma(hr, y.x, fma(-hi, y.y, gr));
+            gi = fma(hr, y.y, fma(hi, y.x, gi));
+        }
+        const double mr = a.Psp[j], mi = a.Qsp[j];
+        const double Ir = a.Ire[j], Ii = a.Iim[j];
+        gr += mr * Ir - mi * Ii;      // conj(m I) = (mr Ir - mi Ii) - j(mr Ii + mi Ir)
+        gi -= mr * Ii + mi * Ir;
+        const double vm = a.Vm[j];
+        const double vr = a.Vre[j], vi = a.Vim[j];
+        const double inv = 1.0 / vm;
+        a.w0[j] = (gr * vr - gi * vi) * inv;
+        a.w1[j] = -(gr * vi + gi * vr);
+    }
+}
+
+// ---------------------------------------------------------------- Jacobian fill (Alg. 1)
+// J1 = dF1/dz1 in 2x2 blocks; F = spec - S, so every entry is minus the derivative
+// of the calculated injection.  With W = V_i conj(Y_ij V_j) (i != j):
+//   dP_i/dtheta_j = Im W, dQ_i/dtheta_j = -Re W, dP_i/dVm_j = Re W / Vm_j,
+//   dQ_i/dVm_j = Im W / Vm_j;
+// on the diagonal: dP_i/dtheta_i = -Q_i - B_ii Vm_i^2, dQ_i/dtheta_i = P_i - G_ii Vm_i^2,
+//   dP_i/dVm_i = (P_i + G_ii Vm_i^2) / Vm_i, dQ_i/dVm_i = (Q_i - B_ii Vm_i^2) / Vm_i.
+template <typename FT>
+__device__ void phase_fill(const DevPlan& P, const Arrays& a, FT* fac) {
+    for (int e = threadIdx.x; e < P.nnzb; e += blockDim.x) {
+        const int p = P.lu_row[e], q = P.lu_col[e];
+        const int yi = P.fill_y[e];
+        const int i = P.pos2bus[p], j = P.pos2bus[q];
+        double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+        if (yi >= 0) {
+            const double2 y = P.y_gb[yi];
+            if (p == q) {
+                const double vr = a.Vre[i], vi = a.Vim[i], ir = a.Ire[i], ii = a.Iim[i];
+                const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
+                const double vm = a.Vm[i], vm2 = vm * vm, ivm = 1.0 / vm;
+                a00 = Qi + y.y * vm2;
+                a01 = -(Pi + y.x * vm2) * ivm;
+                a10 = -Pi + y.x * vm2;
+                a11 = -(Qi - y.y * vm2) * ivm;
+            } else {
+                const double vr = a.Vre[j], vi = a.Vim[j];
+                const double yvr = y.x * vr - y.y * vi, yvi = y.x * vi + y.y * vr;
+                const double Wr = a.Vre[i] * yvr + a.Vim[i] * yvi;
+                const double Wi = a.Vim[i] * yvr - a.Vre[i] * yvi;
+                const double ivm = 1.0 / a.Vm[j];
+                a00 = -Wi;
+                a10 = Wr;
+                a01 = -Wr * ivm;
+                a11 = -Wi * ivm;
+            }
+        }
+        // PV buses: no dQ row and no Vm column; padded with the identity equation
+        if (P.bus_type[i] == 1) { a10 = 0.0; a11 = 0.0; }
+        if (P.bus_type[j] == 1) { a01 = 0.0; a11 = 0.0; }
+        if (p == q && P.bus_type[i] == 1) a11 = 1.0;
+        stb(fac, e, Blk<FT>{FT(a00), FT(a01), FT(a10), FT(a11)});
+    }
+}
+
+// ---------------------------------------------------------------- block LU
+// Right-looking, one elimination-tree level at a time.  Phase A scales the L
+// columns of the level's pivots; phase B gathers every Schur update of the level
+// into its target block (no two threads write the same block) and replaces the
+// level's pivot blocks by their inverses.  Returns nonzero if a pivot was singular.
+template <typename FT>
+__device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
+    int bad = 0;
+    if (threadIdx.x == 0) *s_bad = 0;
+    for (int l = 0; l < P.n_levels; ++l) {
+        const int a0 = P.la_ptr[l], a1 = P.la_ptr[l + 1];
+        for (int c = a0 + threadIdx.x; c < a1; c += blockDim.x) {
+            const int2 ld = P.la[c];
+            int dummy = 0;
+            Blk<FT> dinv = inv2(ldb(fac, ld.y), &dummy);
+            stb(fac, ld.x, mul(ldb(fac, ld.x), dinv));
+        }
+        gsync();
+        const int t0 = P.sch_tptr[l], t1 = P.sch_tptr[l + 1];
+        const int p0 = P.lev_ptr[l], p1 = P.lev_ptr[l + 1];
+        const int nt = t1 - t0, nw = nt + (p1 - p0);
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+            if (w < nt) {
+                const int t = t0 + w;
+                const int tg = P.sch_tgt[t];
+                Blk<FT> acc = ldb(fac, tg);
+                for (int c = P.sch_cptr[t]; c < P.sch_cptr[t + 1]; ++c) {
+                    const int2 lu = P.sch[c];
+                    acc = msub(acc, ldb(fac, lu.x), ldb(fac, lu.y));
+                }
+                stb(fac, tg, acc);
+            } else {
+                const int dk = P.lu_diag[p0 + (w - nt)];
+                stb(fac, dk, inv2(ldb(fac, dk), &bad));
+            }
+        }
+        gsync();
+    }
+    if (bad) *s_bad = 1;
+    gsync();
+    return *s_bad;
+}
+
+// x <- (LU)^{-1} x, in place, x holds 2 values per pivot
+template <typename FT>
+__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x) {
+    for (int l = 0; l < P.n_levels; ++l) {
+        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
+            FT x0 = x[2 * p], x1 = x[2 * p + 1];
+            for (int e = P.lu_ptr[p]; e < P.lu_diag[p]; ++e) {
+                const int q = P.lu_col[e];
+                const Blk<FT> m = ldb(fac, e);
+                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
+                x0 -= m.a * y0 + m.b * y1;
+                x1 -= m.c * y0 + m.d * y1;
+            }
+            x[2 * p] = x0;
+            x[2 * p + 1] = x1;
+        }
+        gsync();
+    }
+    for (int l = P.n_levels - 1; l >= 0; --l) {
+        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
+            FT x0 = x[2 * p], x1 = x[2 * p + 1];
+            const int dg = P.lu_diag[p];
+            for (int e = dg + 1; e < P.lu_ptr[p + 1]; ++e) {
+                const int q = P.lu_col[e];
+                const Blk<FT> m = ldb(fac, e);
+                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
+                x0 -= m.a * y0 + m.b * y1;
+                x1 -= m.c * y0 + m.d * y1;
+            }
+            const Blk<FT> d = ldb(fac, dg);
+            x[2 * p] = d.a * x0 + d.b * x1;
+            x[2 * p + 1] = d.c * x0 + d.d * x1;
+        }
+        gsync();
+    }
+}
+
+// x <- (LU)^{-T} x: U^T y = x forward (U^T rows are mirrored L-part positions), then
+// L^T x = y backward (mirrored U-part positions).
+template <typename FT>
+__device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
+    for (int l = 0; l < P.n_levels; ++l) {
+        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
+            FT x0 = x[2 * p], x1 = x[2 * p + 1];
+            for (int e = P.lu_ptr[p]; e < P.lu_diag[p]; ++e) {
+                const int q = P.lu_col[e];
+                const Blk<FT> m = ldb(fac, P.lu_mirror[e]);  // U(q, p), used transposed
+                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
+                x0 -= m.a * y0 + m.c * y1;
+                x1 -= m.b * y0 + m.d * y1;
+            }
+            const Blk<FT> d = ldb(fac, P.lu_diag[p]);     // inverse of U(p,p); use its transpose
+            x[2 * p] = d.a * x0 + d.c * x1;
+            x[2 * p + 1] = d.b * x0 + d.d * x1;
+        }
+        gsync();
+    }
+    for (int l = P.n_levels - 1; l >= 0; --l) {
+        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
+            FT x0 = x[2 * p], x1 = x[2 * p + 1];
+            for (int e = P.lu_diag[p] + 1; e < P.lu_ptr[p + 1]; ++e) {
+                const int q = P.lu_col[e];
+                const Blk<FT> m = ldb(fac, P.lu_mirror[e]);  // L(q, p), used transposed
+                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
+                x0 -= m.a * y0 + m.c * y1;
+                x1 -= m.b * y0 + m.d * y1;
+            }
+            x[2 * p] = x0;
+            x[2 * p + 1] = x1;
+        }
+        gsync();
+    }
+}
+
+// r = -F1 - J1 dz with J1 dz = -[Re dS; Im dS] linearised through Ybus (FP64):
+// dV_i = u_i dVm_i + j V_i dtheta_i, dS_i = dV_i conj(I_i) + V_i conj(sum_k Y_ik dV_k).
+// Returns ||r||_inf over the true (unpadded) rows.
+__device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red) {
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const int p = P.bus2pos[i];
+        double dr = 0.0, di = 0.0;
+        if (p >= 0) {
+            const double dth = a.dz[2 * p];
+            const double dvm = (P.bus_type[i] == 0) ? a.dz[2 * p + 1] : 0.0;
+            const double vr = a.Vre[i], vi = a.Vim[i];
+            const double s = dvm / a.Vm[i];
+            dr = vr * s - vi * dth;
+            di = vi * s + vr * dth;
+        }
+        a.dVre[i] = dr;
+        a.dVim[i] = di;
+    }
+    gsync();
+    double lmax = 0.0;
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const int p = P.bus2pos[i];
+        if (p < 0) continue;
+        double ir = 0.0, ii = 0.0;
+        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+            const int j = P.y_idx[k];
+            const double2 y = P.y_gb[k];
+            const double vr = a.dVre[j], vi = a.dVim[j];
+            ir = fma(y.x, vr, fma(-y.y, vi, ir));
+            ii = fma(y.x, vi, fma(y.y, vr, ii));
+        }
+        const double vr = a.Vre[i], vi = a.Vim[i], Ir = a.Ire[i], Ii = a.Iim[i];
+        const double dvr = a.dVre[i], dvi = a.dVim[i];
+        // dS = dV conj(I) + V conj(dI)
+        const double dSr = dvr * Ir + dvi * Ii + vr * ir + vi * ii;
+        const double dSi = dvi * Ir - dvr * Ii + vi * ir - vr * ii;
+        const double rP = -a.F[2 * p] + dSr;
+        const double rQ = (P.bus_type[i] == 0) ? -a.F[2 * p + 1] + dSi : 0.0;
+        a.r[2 * p] = rP;
+        a.r[2 * p + 1] = rQ;
+        lmax = fmax(lmax, fmax(absinf(rP), absinf(rQ)));
+    }
+    return group_max(lmax, red);
+}
+
+// ---------------------------------------------------------------- forward kernel
+template <typename FT>
+__global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_bad;
+    const int b = blockIdx.x;
+    if (b >= A.batch) return;
+    const SlotLayout& L = A.L;
+    unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
+    unsigned char* vbase = L.vec_in_smem ? smem : slot + L.off_vec;
+    FT* fac = L.fac_in_smem ? reinterpret_cast<FT*>(smem + L.smem_fac_off)
+                            : reinterpret_cast<FT*>(slot + L.off_fac);
+    Arrays a;
+    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), &a);
+    FT* x = ftptr<FT>(a.x);
+    const bool mixed = sizeof(FT) == 4;
+    const size_t row = (size_t)b * P.n_bus;
+
+    // flat start and specified injections (Sec. II-A, Sec. IV-A)
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const int t = P.bus_type[i];
+        a.Vm[i] = (t == 0) ? 1.0 : A.Vset[row + i];
+        a.Va[i] = 0.0;
+        a.Psp[i] = ((t == 1) ? A.Pg[row + i] : 0.0) - A.Pd[row + i];
+        a.Qsp[i] = -A.Qd[row + i];
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    gsync();
+
+    int it = 0, status = 1;
+    double norm = 0.0;
+    bool factored = false;
+    for (;;) {
+        phase_voltage(P, a);
+        gsync();
+        norm = phase_mismatch(P, a, red);  // ends with a group barrier
+        if (!(norm <= 1e10)) { status = 2; break; }
+        if (norm <= A.tol) { status = 0; break; }
+        if (it >= A.max_iter) { status = 1; break; }
+        phase_fill<FT>(P, a, fac);
+        gsync();
+        if (phase_lu<FT>(P, fac, &s_bad)) { status = 3; factored = false; break; }
+        factored = true;
+        // first solve with the FT factor
+        for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(-a.F[k]);
+        gsync();
+        phase_solve<FT>(P, fac, x);
+        if (mixed) {
+            for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] = double(x[k]);
+            gsync();
+            for (int s = 0; s < A.ir_steps; ++s) {
+                const double rmax = phase_residual(P, a, red);
+                if (A.ir_rtol > 0.0 && rmax <= A.ir_rtol * norm) break;
+                for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
+                gsync();
+                phase_solve<FT>(P, fac, x);
+                for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] += double(x[k]);
+                gsync();
+            }
+        }
+        // update (FP64)
+        for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
+            const int i = P.pos2bus[p];
+            const double dth = mixed ? a.dz[2 * p] : double(x[2 * p]);
+            const double dvm = mixed ? a.dz[2 * p + 1] : double(x[2 * p + 1]);
+            a.Va[i] += dth;
+            if (P.bus_type[i] == 0) a.Vm[i] += dvm;
+        }
+        ++it;
+        gsync();
+    }
+
+    // Step 2 and outputs
+    double* st = reinterpret_cast<double*>(slot + L.off_state);
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const int t = P.bus_type[i];
+        const double vr = a.Vre[i], vi = a.Vim[i], ir = a.Ire[i], ii = a.Iim[i];
+        const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
+        A.Vm[row + i] = a.Vm[i];
+        A.Va[row + i] = a.Va[i];
+        st[i] = a.Vm[i];
+        st[P.n_bus + i] = a.Va[i];
+        if (A.Pg_out) A.Pg_out[row + i] = (t == 1) ? A.Pg[row + i] : (t == 2 ? Pi + A.Pd[row + i] : 0.0);
+        if (A.Qg_out) A.Qg_out[row + i] = (t == 0) ? 0.0 : Qi + A.Qd[row + i];
+    }
+    if (A.keep_factors && factored && L.fac_in_smem) {
+        FT* dst = reinterpret_cast<FT*>(slot + L.off_fac);
+        const int nv = P.nnzb * 4;
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) dst[k] = fac[k];
+    }
+    if (threadIdx.x == 0) {
+        A.status[b] = status;
+        if (A.iters) A.iters[b] = it;
+        if (A.fmis) A.fmis[b] = norm;
+        int* fl = reinterpret_cast<int*>(slot + L.off_flags);
+        fl[0] = status;
+        fl[1] = it;
+        fl[2] = (A.keep_factors && factored) ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------- adjoint kernel
+// Sec. II-B.2 at the converged state: v_bar2 = -J2^T c, g_z1, J1^T lambda = g_z1,
+// dL/dx = g_x - [lambda_G; J3^T lambda]; loads through dF1/dpd = dF1/dqd = -1.
+// All Jacobian-transpose products are taken matrix-free through Ybus^T (phase_jvt);
+// the transposed solve uses the stored factor of the last Newton step and refines
+// with the FP64 residual of J1 at the solution.
+template <typename FT>
+__global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_bad;
+    const int b = blockIdx.x;
+    if (b >= A.batch) return;
+    const SlotLayout& L = A.L;
+    unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
+    unsigned char* vbase = L.vec_in_smem ? smem : slot + L.off_vec;
+    FT* gfac = reinterpret_cast<FT*>(slot + L.off_fac);
+    FT* fac = L.fac_in_smem ? reinterpret_cast<FT*>(smem + L.smem_fac_off) : gfac;
+    Arrays a;
+    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), &a);
+    FT* x = ftptr<FT>(a.x);
+    const size_t row = (size_t)b * P.n_bus;
+    const int* fl = reinterpret_cast<const int*>(slot + L.off_flags);
+    const int fwd_status = fl[0];
+    const int has_factor = fl[2];
+
+    if (fwd_status != 0) {
+        for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+            A.dPd[row + i] = 0.0;
+            A.dQd[row + i] = 0.0;
+            A.dPg_in[row + i] = 0.0;
+            A.dVset[row + i] = 0.0;
+        }
+        if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = fwd_status;
+        return;
+    }
+    const double* st = reinterpret_cast<const double*>(slot + L.off_state);
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        a.Vm[i] = st[i];
+        a.Va[i] = st[P.n_bus + i];
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    gsync();
+    phase_voltage(P, a);
+    gsync();
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {  // I = Y V
+        double ir = 0.0, ii = 0.0;
+        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+            const int j = P.y_idx[k];
+            const double2 y = P.y_gb[k];
+            ir = fma(y.x, a.Vre[j], fma(-y.y, a.Vim[j], ir));
+            ii = fma(y.x, a.Vim[j], fma(y.y, a.Vre[j], ii));
+        }
+        a.Ire[i] = ir;
+        a.Iim[i] = ii;
+    }
+    // Step-2 weights: c_P on R (dL/dpg_R), c_Q on B\D (dL/dqg)
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const int t = P.bus_type[i];
+        a.Psp[i] = (t == 2 && A.dPg) ? A.dPg[row + i] : 0.0;
+        a.Qsp[i] = (t != 0 && A.dQg) ? A.dQg[row + i] : 0.0;
+    }
+    gsync();
+    phase_jvt(P, a);  // v_bar2 = -J2^T c = (d[P_R; Q_{B\D}]/dv)^T c
+    gsync();
+    double lg = 0.0;
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const double gvm = A.dVm[row + i] + a.w0[i];
+        const double gva = A.dVa[row + i] + a.w1[i];
+        a.gV[i] = gvm;
+        const int p = P.bus2pos[i];
+        if (p >= 0) {
+            a.F[2 * p] = gva;                                   // theta component of g_z1
+            a.F[2 * p + 1] = (P.bus_type[i] == 0) ? gvm : 0.0;  // Vm component (PQ only)
+            lg = fmax(lg, fmax(absinf(gva), absinf(a.F[2 * p + 1])));
+        }
+    }
+    const double gnorm = group_max(lg, red);
+
+    // stage the stored factor
+    bool have = has_factor != 0;
+    if (have && L.fac_in_smem) {
+        const int nv = P.nnzb * 4;
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) fac[k] = gfac[k];
+        gsync();
+    }
+    int astat = 0;
+    bool refactored = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (!have) {
+            phase_fill<FT>(P, a, fac);
+            gsync();
+            if (phase_lu<FT>(P, fac, &s_bad)) { astat = 3; break; }
+            have = true;
+            refactored = true;
+        }
+        for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.F[k]);
+        gsync();
+        phase_solve_t<FT>(P, fac, x);
+        for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] = double(x[k]);
+        gsync();
+        bool conv = false;
+        for (int s = 0;; ++s) {
+            // m1 = lambda on the F1 rows; r = g_z1 - J1^T lambda = g_z1 + (Jv^T m1)[z1]
+            for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+                const int p = P.bus2pos[i];
+                a.Psp[i] = (p >= 0) ? a.dz[2 * p] : 0.0;
+                a.Qsp[i] = (p >= 0 && P.bus_type[i] == 0) ? a.dz[2 * p + 1] : 0.0;
+            }
+            gsync();
+            phase_jvt(P, a);
+            gsync();
+            double lr = 0.0;
+            for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
+                const int i = P.pos2bus[p];
+                const double r0 = a.F[2 * p] + a.w1[i];
+                const double r1 = (P.bus_type[i] == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
+                a.r[2 * p] = r0;
+                a.r[2 * p + 1] = r1;
+                lr = fmax(lr, fmax(absinf(r0), absinf(r1)));
+            }
+            const double rmax = group_max(lr, red);
+            if (rmax <= A.ir_rtol * gnorm) { conv = true; break; }
+            if (s >= A.ir_max || !(rmax <= 1e300)) break;
+            for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
+            gsync();
+            phase_solve_t<FT>(P, fac, x);
+            for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] += double(x[k]);
+            gsync();
+        }
+        if (conv) break;
+        if (refactored) { astat = 1; break; }
+        have = false;  // stale factor did not converge: refactor at the solution
+    }
+    // gradients; w0 holds (Jv^T m1)_Vm for the final lambda
+    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+        const int t = P.bus_type[i];
+        const int p = P.bus2pos[i];
+        const double lP = (p >= 0) ? a.dz[2 * p] : 0.0;
+        const double lQ = (p >= 0 && t == 0) ? a.dz[2 * p + 1] : 0.0;
+        const double cP = A.dPg ? A.dPg[row + i] : 0.0;
+        const double cQ = A.dQg ? A.dQg[row + i] : 0.0;
+        A.dPd[row + i] = (t == 2) ? cP : lP;
+        A.dQd[row + i] = (t == 0) ? lQ : cQ;
+        A.dPg_in[row + i] = (t == 1) ? cP - lP : 0.0;
+        A.dVset[row + i] = (t != 0) ? a.gV[i] + a.w0[i] : 0.0;
+    }
+    if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = astat;
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename FT>
+cudaError_t launch_solve(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s) {
+    auto k = nr_solve_kernel<FT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)A.L.smem_bytes);
+    if (e != cudaSuccess) return e;
+    k<<<A.batch, threads, A.L.smem_bytes, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+template <typename FT>
+cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s) {
+    auto k = adjoint_kernel<FT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)A.L.smem_bytes);
+    if (e != cudaSuccess) return e;
+    k<<<A.batch, threads, A.L.smem_bytes, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_solve<float>(const DevPlan&, const SolveArgs&, int, cudaStream_t);
+template cudaError_t launch_solve<double>(const DevPlan&, const SolveArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint<float>(const DevPlan&, const AdjArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint<double>(const DevPlan&, const AdjArgs&, int, cudaStream_t);
+
+}  // namespace pf

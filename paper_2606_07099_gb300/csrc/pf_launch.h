@@ -1,0 +1,11 @@
+// pf_launch.h -- host entry points into the device code (internal to libpf).
+#pragma once
+
+#include "pf_device.cuh"
+
+namespace pf {
+template <typename FT>
+cudaError_t launch_solve(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s);
+template <typename FT>
+cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s);
+}  // namespace pf

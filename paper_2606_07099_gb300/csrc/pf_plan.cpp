@@ -1,0 +1,314 @@
+// pf_plan.cpp -- one-time symbolic analysis of a network (Sec. III-B).
+//
+// Steps, in order:
+//   1. validate and canonicalise the Ybus CSR (sorted columns, summed duplicates);
+//   2. check that every bus reaches a slack bus through nonzero Ybus entries;
+//   3. order the non-slack buses by minimum degree on the bus graph (the J1
+//      block pattern inherits the Ybus pattern, Sec. III-B.1), so that the 2x2
+//      block LU of J1 has little fill;
+//   4. build the elimination tree, group the pivots by tree level and renumber
+//      them level by level (any topological order of the tree gives the same
+//      fill, so this keeps the fill of step 3);
+//   5. emit the filled block pattern (CSR), the transpose ("mirror") map, the
+//      Ybus index of every block (the cached fill metadata of Alg. 1) and the
+//      per-level factorisation schedule.
+#include "pf_plan.h"
+
+#include <algorithm>
+#include <numeric>
+#include <set>
+#include <utility>
+
+namespace pf {
+
+namespace {
+
+// merge two sorted vectors, dropping values a and b
+void merge_without(const std::vector<int>& x, const std::vector<int>& y, int a, int b,
+                   std::vector<int>& out) {
+    out.clear();
+    out.reserve(x.size() + y.size());
+    size_t i = 0, j = 0;
+    auto push = [&](int v) {
+        if (v != a && v != b && (out.empty() || out.back() != v)) out.push_back(v);
+    };
+    while (i < x.size() || j < y.size()) {
+        if (j >= y.size() || (i < x.size() && x[i] < y[j])) push(x[i++]);
+        else if (i >= x.size() || y[j] < x[i]) push(y[j++]);
+        else { push(x[i]); ++i; ++j; }
+    }
+}
+
+int find_in_row(const std::vector<int>& ptr, const std::vector<int>& col, int r, int c) {
+    auto b = col.begin() + ptr[r], e = col.begin() + ptr[r + 1];
+    auto it = std::lower_bound(b, e, c);
+    if (it == e || *it != c) return -1;
+    return (int)(it - col.begin());
+}
+
+}  // namespace
+
+void minimum_degree(const std::vector<std::vector<int>>& adj0, std::vector<int>& order,
+                    std::vector<std::vector<int>>& structs) {
+    const int n = (int)adj0.size();
+    std::vector<std::vector<int>> adj = adj0;
+    std::vector<char> done(n, 0);
+    std::set<std::pair<int, int>> queue;  // (current degree, node): lowest degree, then lowest id
+    for (int v = 0; v < n; ++v) queue.insert({(int)adj[v].size(), v});
+    order.clear();
+    order.reserve(n);
+    structs.assign(n, {});
+    std::vector<int> tmp;
+    while (!queue.empty()) {
+        int v = queue.begin()->second;
+        queue.erase(queue.begin());
+        done[v] = 1;
+        order.push_back(v);
+        const std::vector<int> nb = adj[v];  // all alive (eliminated nodes are removed)
+        structs[v] = nb;
+        for (int u : nb) {
+            queue.erase({(int)adj[u].size(), u});
+            merge_without(adj[u], nb, u, v, tmp);  // u joins the clique of v's neighbours
+            adj[u].swap(tmp);
+            queue.insert({(int)adj[u].size(), u});
+        }
+        adj[v].clear();
+    }
+}
+
+BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
+                       const double* y_re, const double* y_im, const int* bus_type,
+                       Plan& P) {
+    if (n_bus < 1 || !y_indptr || !y_indices || !y_re || !y_im || !bus_type) return BUILD_EINVAL;
+    if (y_indptr[0] != 0) return BUILD_EINVAL;
+    for (int i = 0; i < n_bus; ++i)
+        if (y_indptr[i + 1] < y_indptr[i]) return BUILD_EINVAL;
+    P = Plan();
+    P.n_bus = n_bus;
+    P.bus_type.assign(bus_type, bus_type + n_bus);
+    for (int i = 0; i < n_bus; ++i) {
+        int t = bus_type[i];
+        if (t < 0 || t > 2) return BUILD_EINVAL;
+        if (t == 0) P.n_pq++;
+        else if (t == 1) P.n_pv++;
+        else P.n_slack++;
+    }
+    if (P.n_slack < 1) return BUILD_EINVAL;
+
+    // 1. canonical CSR
+    P.y_ptr.assign(n_bus + 1, 0);
+    std::vector<std::pair<int, std::pair<double, double>>> row;
+    for (int i = 0; i < n_bus; ++i) {
+        row.clear();
+        for (int k = y_indptr[i]; k < y_indptr[i + 1]; ++k) {
+            int j = y_indices[k];
+            if (j < 0 || j >= n_bus) return BUILD_EINVAL;
+            row.push_back({j, {y_re[k], y_im[k]}});
+        }
+        std::stable_sort(row.begin(), row.end(),
+                         [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t k = 0; k < row.size(); ++k) {
+            if (!P.y_idx.empty() && (int)P.y_idx.size() > P.y_ptr[i] && P.y_idx.back() == row[k].first) {
+                P.y_g.back() += row[k].second.first;
+                P.y_b.back() += row[k].second.second;
+            } else {
+                P.y_idx.push_back(row[k].first);
+                P.y_g.push_back(row[k].second.first);
+                P.y_b.push_back(row[k].second.second);
+            }
+        }
+        P.y_ptr[i + 1] = (int)P.y_idx.size();
+    }
+
+    // transpose (the adjoint needs products with Ybus^T; equal to Ybus without phase shifters)
+    {
+        const int nnz = (int)P.y_idx.size();
+        P.yt_ptr.assign(n_bus + 1, 0);
+        for (int k = 0; k < nnz; ++k) P.yt_ptr[P.y_idx[k] + 1]++;
+        for (int i = 0; i < n_bus; ++i) P.yt_ptr[i + 1] += P.yt_ptr[i];
+        P.yt_idx.resize(nnz);
+        P.yt_g.resize(nnz);
+        P.yt_b.resize(nnz);
+        std::vector<int> fill(P.yt_ptr.begin(), P.yt_ptr.end() - 1);
+        for (int i = 0; i < n_bus; ++i)
+            for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+                int d = fill[P.y_idx[k]]++;
+                P.yt_idx[d] = i;
+                P.yt_g[d] = P.y_g[k];
+                P.yt_b[d] = P.y_b[k];
+            }
+    }
+
+    // 2. every non-slack bus needs a diagonal entry and a path to a slack bus
+    for (int i = 0; i < n_bus; ++i)
+        if (bus_type[i] != 2 && find_in_row(P.y_ptr, P.y_idx, i, i) < 0) return BUILD_ESINGULAR;
+    {
+        std::vector<char> seen(n_bus, 0);
+        std::vector<int> stack;
+        for (int i = 0; i < n_bus; ++i)
+            if (bus_type[i] == 2) { seen[i] = 1; stack.push_back(i); }
+        while (!stack.empty()) {
+            int u = stack.back();
+            stack.pop_back();
+            for (int k = P.y_ptr[u]; k < P.y_ptr[u + 1]; ++k) {
+                int v = P.y_idx[k];
+                if (!seen[v] && (P.y_g[k] != 0.0 || P.y_b[k] != 0.0)) { seen[v] = 1; stack.push_back(v); }
+            }
+        }
+        for (int i = 0; i < n_bus; ++i)
+            if (!seen[i]) return BUILD_ESINGULAR;
+    }
+
+    // 3. bus graph of the non-slack buses and its minimum-degree order
+    std::vector<int> nodes;  // node id -> bus
+    std::vector<int> bus2node(n_bus, -1);
+    for (int i = 0; i < n_bus; ++i)
+        if (bus_type[i] != 2) { bus2node[i] = (int)nodes.size(); nodes.push_back(i); }
+    const int n = (int)nodes.size();
+    P.n = n;
+    std::vector<std::vector<int>> adj(n);
+    for (int a = 0; a < n; ++a) {
+        int i = nodes[a];
+        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+            int j = P.y_idx[k];
+            int b = bus2node[j];
+            if (b >= 0 && b != a) { adj[a].push_back(b); adj[b].push_back(a); }
+        }
+    }
+    for (auto& v : adj) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    std::vector<int> order;
+    std::vector<std::vector<int>> structs;
+    minimum_degree(adj, order, structs);
+    std::vector<int> elim(n);  // node -> elimination index
+    for (int k = 0; k < n; ++k) elim[order[k]] = k;
+
+    // 4. elimination tree and levels (children are eliminated before parents)
+    std::vector<int> level(n, 0);
+    for (int k = 0; k < n; ++k) {
+        int v = order[k];
+        int parent = -1;
+        for (int u : structs[v])
+            if (parent < 0 || elim[u] < elim[parent]) parent = u;
+        if (parent >= 0) level[parent] = std::max(level[parent], level[v] + 1);
+    }
+    int n_levels = 0;
+    for (int v = 0; v < n; ++v) n_levels = std::max(n_levels, level[v] + 1);
+    if (n == 0) n_levels = 0;
+    std::vector<int> byl(n);
+    std::iota(byl.begin(), byl.end(), 0);
+    std::sort(byl.begin(), byl.end(), [&](int a, int b) {
+        if (level[a] != level[b]) return level[a] < level[b];
+        return elim[a] < elim[b];
+    });
+    std::vector<int> node2pos(n);
+    for (int p = 0; p < n; ++p) node2pos[byl[p]] = p;
+    P.n_levels = n_levels;
+    P.lev_ptr.assign(n_levels + 1, 0);
+    for (int v = 0; v < n; ++v) P.lev_ptr[level[v] + 1]++;
+    for (int l = 0; l < n_levels; ++l) P.lev_ptr[l + 1] += P.lev_ptr[l];
+    P.pos2bus.resize(n);
+    P.bus2pos.assign(n_bus, -1);
+    for (int p = 0; p < n; ++p) {
+        P.pos2bus[p] = nodes[byl[p]];
+        P.bus2pos[nodes[byl[p]]] = p;
+    }
+
+    // 5. filled block pattern in position order
+    std::vector<std::vector<int>> upos(n);  // U(p, .) columns, ascending
+    for (int v = 0; v < n; ++v) {
+        int p = node2pos[v];
+        for (int u : structs[v]) upos[p].push_back(node2pos[u]);
+        std::sort(upos[p].begin(), upos[p].end());
+    }
+    std::vector<std::vector<int>> rows(n);
+    for (int p = 0; p < n; ++p) {
+        rows[p].push_back(p);
+        for (int q : upos[p]) {
+            if (q <= p) return BUILD_EINVAL;  // cannot happen: ancestors sit on higher levels
+            rows[p].push_back(q);
+            rows[q].push_back(p);  // L(q, p)
+        }
+    }
+    P.lu_ptr.assign(n + 1, 0);
+    for (int p = 0; p < n; ++p) {
+        std::sort(rows[p].begin(), rows[p].end());
+        P.lu_ptr[p + 1] = P.lu_ptr[p] + (int)rows[p].size();
+    }
+    const int nnzb = P.lu_ptr[n];
+    P.lu_col.resize(nnzb);
+    P.lu_row.resize(nnzb);
+    P.lu_diag.resize(n);
+    for (int p = 0; p < n; ++p)
+        for (size_t k = 0; k < rows[p].size(); ++k) {
+            int e = P.lu_ptr[p] + (int)k;
+            P.lu_col[e] = rows[p][k];
+            P.lu_row[e] = p;
+            if (rows[p][k] == p) P.lu_diag[p] = e;
+        }
+    P.lu_mirror.resize(nnzb);
+    P.fill_y.resize(nnzb);
+    for (int e = 0; e < nnzb; ++e) {
+        int p = P.lu_row[e], q = P.lu_col[e];
+        P.lu_mirror[e] = find_in_row(P.lu_ptr, P.lu_col, q, p);
+        P.fill_y[e] = find_in_row(P.y_ptr, P.y_idx, P.pos2bus[p], P.pos2bus[q]);
+    }
+
+    // factorisation schedule
+    P.la_ptr.assign(n_levels + 1, 0);
+    P.sch_tptr.assign(n_levels + 1, 0);
+    P.sch_cptr.assign(1, 0);
+    std::vector<std::pair<int, std::pair<int, int>>> contrib;  // (target, (L, U))
+    for (int l = 0; l < n_levels; ++l) {
+        contrib.clear();
+        for (int k = P.lev_ptr[l]; k < P.lev_ptr[l + 1]; ++k) {
+            const int dk = P.lu_diag[k];
+            for (int e = dk + 1; e < P.lu_ptr[k + 1]; ++e) {  // U(k, j), j > k
+                P.la_L.push_back(P.lu_mirror[e]);             // L(j, k)
+                P.la_D.push_back(dk);
+            }
+            for (int ei = dk + 1; ei < P.lu_ptr[k + 1]; ++ei) {
+                int i = P.lu_col[ei];
+                int Lik = P.lu_mirror[ei];
+                for (int ej = dk + 1; ej < P.lu_ptr[k + 1]; ++ej) {
+                    int j = P.lu_col[ej];
+                    int t = find_in_row(P.lu_ptr, P.lu_col, i, j);
+                    if (t < 0) return BUILD_EINVAL;  // clique property violated: bug
+                    contrib.push_back({t, {Lik, ej}});
+                }
+            }
+        }
+        P.la_ptr[l + 1] = (int)P.la_L.size();
+        std::stable_sort(contrib.begin(), contrib.end(),
+                         [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t c = 0; c < contrib.size(); ++c) {
+            if (c == 0 || contrib[c].first != contrib[c - 1].first) {
+                P.sch_tgt.push_back(contrib[c].first);
+                P.sch_cptr.push_back(P.sch_cptr.back());
+            }
+            P.sch_L.push_back(contrib[c].second.first);
+            P.sch_U.push_back(contrib[c].second.second);
+            P.sch_cptr.back()++;
+        }
+        P.sch_tptr[l + 1] = (int)P.sch_tgt.size();
+        P.schur_ops += (long long)contrib.size();
+    }
+
+    // scalar nonzeros of J1 (rows dP_{B\R}, dQ_D; columns theta_{B\R}, Vm_D)
+    long long nnz = 0;
+    for (int i = 0; i < n_bus; ++i) {
+        if (bus_type[i] == 2) continue;
+        int ri = 1 + (bus_type[i] == 0);
+        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+            int j = P.y_idx[k];
+            if (bus_type[j] == 2) continue;
+            nnz += ri * (1 + (bus_type[j] == 0));
+        }
+    }
+    P.nnz_j1 = (int)nnz;
+    return BUILD_OK;
+}
+
+}  // namespace pf

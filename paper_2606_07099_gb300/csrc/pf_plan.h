@@ -1,0 +1,69 @@
+// pf_plan.h -- host-side symbolic plan of one network (internal to libpf).
+//
+// The plan is the "one-time symbolic analysis" of Sec. III-B: everything about
+// the Jacobian J1 of Eq. step1_jacobian that does not depend on the operating
+// point.  It is built once per (Ybus pattern, bus types) and shared by every
+// scenario of every batch.
+//
+// Unknowns and equations are grouped per non-slack bus into 2x2 blocks:
+// unknowns (theta_i, Vm_i), equations (dP_i, dQ_i).  A PV bus has no Vm unknown
+// and no dQ equation; its block row/column is padded with the identity
+// equation dVm_i = 0, which keeps every block 2x2 and leaves the solution of the
+// true unknowns unchanged (the padded row and column stay exactly zero off the
+// diagonal through the elimination).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace pf {
+
+struct Plan {
+    // network
+    int n_bus = 0, n_slack = 0, n_pv = 0, n_pq = 0;
+    std::vector<int> y_ptr, y_idx;       // Ybus CSR, sorted columns, duplicates summed
+    std::vector<double> y_g, y_b;        // Re / Im of Ybus entries
+    std::vector<int> bus_type;           // 0 PQ, 1 PV, 2 slack
+    std::vector<int> yt_ptr, yt_idx;     // transpose of Ybus (CSR of the columns)
+    std::vector<double> yt_g, yt_b;
+
+    // block ordering: position p in [0, n) <-> non-slack bus
+    int n = 0;                           // number of 2x2 pivot blocks = |B \ R|
+    std::vector<int> pos2bus, bus2pos;   // bus2pos = -1 for slack buses
+
+    // elimination-tree levels: positions are sorted by level, so level l holds
+    // the pivot range [lev_ptr[l], lev_ptr[l+1])
+    int n_levels = 0;
+    std::vector<int> lev_ptr;
+
+    // block CSR of the filled L+U pattern in position order
+    std::vector<int> lu_ptr, lu_col, lu_row, lu_diag, lu_mirror;
+    std::vector<int> fill_y;             // Ybus entry of block (row bus, col bus), -1 = fill-in
+
+    // factorisation schedule, per level l:
+    //  phase A: L(i,k) <- A(i,k) * inv(A(k,k)) for the pairs la[la_ptr[l] .. la_ptr[l+1])
+    //           stored as (block position of (i,k), block position of (k,k))
+    //  phase B: A(i,j) -= L(i,k) * U(k,j) gathered per target block
+    std::vector<int> la_ptr, la_L, la_D;
+    std::vector<int> sch_tptr, sch_tgt, sch_cptr, sch_L, sch_U;
+
+    // statistics
+    int nnz_j1 = 0;
+    long long schur_ops = 0;
+    int nnzb() const { return (int)lu_col.size(); }
+};
+
+enum BuildStatus { BUILD_OK = 0, BUILD_EINVAL = 1, BUILD_ESINGULAR = 2 };
+
+// Validates the inputs, sorts/sums the CSR and builds the whole plan.
+BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
+                       const double* y_re, const double* y_im, const int* bus_type,
+                       Plan& plan);
+
+// Minimum-degree elimination order of an undirected graph given by sorted
+// adjacency lists; also returns, for every node, its neighbours at the time it
+// is eliminated (the row pattern of U in elimination terms).
+void minimum_degree(const std::vector<std::vector<int>>& adj,
+                    std::vector<int>& order, std::vector<std::vector<int>>& structs);
+
+}  // namespace pf

@@ -1,0 +1,260 @@
+"""Python face of libpf: one network, many scenarios, on one CUDA device.
+
+Thin marshalling over the C ABI (include/pf.h): PyTorch supplies device memory
+and the current stream; every numerical step runs in libpf's CUDA kernels.
+There is no CPU fallback -- if libpf.so is missing or the device is not a CUDA
+device, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_PREC = {"fp64": L.PF_FP64, "mixed": L.PF_MIXED}
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def build_ybus(n_bus, f, t, r, x, b, tap):
+    """Ybus in CSR from pi-model branches (host; libpf's pf_build_ybus)."""
+    lib = L.load()
+    f = np.ascontiguousarray(f, np.int32)
+    t = np.ascontiguousarray(t, np.int32)
+    r, x, b, tap = (np.ascontiguousarray(v, np.float64) for v in (r, x, b, tap))
+    indptr = np.zeros(n_bus + 1, np.int32)
+    nnz = C.c_int(0)
+    L.check(lib.pf_build_ybus(n_bus, len(f), _iptr(f), _iptr(t), _dptr(r), _dptr(x), _dptr(b),
+                              _dptr(tap), _iptr(indptr), None, None, None, C.byref(nnz)),
+            "pf_build_ybus")
+    idx = np.zeros(nnz.value, np.int32)
+    g = np.zeros(nnz.value)
+    bv = np.zeros(nnz.value)
+    L.check(lib.pf_build_ybus(n_bus, len(f), _iptr(f), _iptr(t), _dptr(r), _dptr(x), _dptr(b),
+                              _dptr(tap), _iptr(indptr), _iptr(idx), _dptr(g), _dptr(bv),
+                              C.byref(nnz)), "pf_build_ybus")
+    return indptr, idx, g, bv
+
+
+def analyze(n_bus, indptr, indices, g, bv, bus_type):
+    """Host-only symbolic analysis: (info dict, pos2bus, lu_ptr, lu_col, lev_ptr)."""
+    lib = L.load()
+    ip, ix = np.ascontiguousarray(indptr, np.int32), np.ascontiguousarray(indices, np.int32)
+    gg, bb = np.ascontiguousarray(g, np.float64), np.ascontiguousarray(bv, np.float64)
+    bt = np.ascontiguousarray(bus_type, np.int32)
+    info = L.PlanInfo()
+    L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
+                           C.byref(info), None, None, None, None), "pf_analyze")
+    pos2bus = np.zeros(info.n_block, np.int32)
+    lu_ptr = np.zeros(info.n_block + 1, np.int32)
+    lu_col = np.zeros(info.nnzb_lu, np.int32)
+    lev_ptr = np.zeros(info.n_levels + 1, np.int32)
+    L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
+                           C.byref(info), _iptr(pos2bus), _iptr(lu_ptr), _iptr(lu_col),
+                           _iptr(lev_ptr)), "pf_analyze")
+    return _info_dict(info), pos2bus, lu_ptr, lu_col, lev_ptr
+
+
+def _info_dict(info: L.PlanInfo) -> dict:
+    return {k: getattr(info, k) for k, _ in L.PlanInfo._fields_}
+
+
+@dataclass
+class SolveResult:
+    Vm: torch.Tensor
+    Va: torch.Tensor
+    Pg: torch.Tensor
+    Qg: torch.Tensor
+    iters: torch.Tensor
+    status: torch.Tensor
+    final_mismatch: torch.Tensor
+
+
+@dataclass
+class Gradients:
+    dPd: torch.Tensor
+    dQd: torch.Tensor
+    dPg: torch.Tensor
+    dVset: torch.Tensor
+    status: torch.Tensor
+
+
+def _check_bus_tensor(x: torch.Tensor, name: str, n_bus: int, batch: int | None = None):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != n_bus:
+        raise ValueError(f"{name} must be float64 [batch, {n_bus}]")
+    if batch is not None and x.shape[0] != batch:
+        raise ValueError(f"{name} has batch {x.shape[0]}, expected {batch}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class PowerFlow:
+    """One network plan (pf_create) on the current CUDA device."""
+
+    def __init__(self, n_bus, y_indptr, y_indices, y_re, y_im, bus_type):
+        lib = L.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpf needs a CUDA device")
+        torch.cuda.init()
+        self.n_bus = int(n_bus)
+        self.bus_type = np.ascontiguousarray(bus_type, np.int32)
+        self._arrays = [np.ascontiguousarray(y_indptr, np.int32),
+                        np.ascontiguousarray(y_indices, np.int32),
+                        np.ascontiguousarray(y_re, np.float64),
+                        np.ascontiguousarray(y_im, np.float64)]
+        h = C.c_void_p()
+        ip, ix, g, bv = self._arrays
+        L.check(lib.pf_create(self.n_bus, _iptr(ip), _iptr(ix), _dptr(g), _dptr(bv),
+                              _iptr(self.bus_type), C.byref(h)), "pf_create")
+        self._h = h
+        self._lib = lib
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._ws = None
+        self._ws_key = None
+        self._solve_id = 0
+        self._last = None
+
+    @classmethod
+    def from_branches(cls, n_bus, f, t, r, x, b, tap, bus_type):
+        ip, ix, g, bv = build_ybus(n_bus, f, t, r, x, b, tap)
+        return cls(n_bus, ip, ix, g, bv, bus_type)
+
+    @classmethod
+    def from_grid(cls, grid):
+        """From a ``synthgrid.Grid`` (branch list + bus types)."""
+        return cls.from_branches(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.b, grid.tap,
+                                 grid.bus_type)
+
+    def info(self) -> dict:
+        info = L.PlanInfo()
+        L.check(self._lib.pf_get_plan_info(self._h, C.byref(info)), "pf_get_plan_info")
+        return _info_dict(info)
+
+    @staticmethod
+    def make_opts(precision="mixed", ir_steps=1, ir_rtol=0.0, group_threads=0, keep_factors=False):
+        if precision not in _PREC:
+            raise ValueError("precision must be 'fp64' or 'mixed'")
+        return L.SolveOpts(_PREC[precision], int(ir_steps), float(ir_rtol), int(group_threads),
+                           1 if keep_factors else 0)
+
+    def workspace_bytes(self, batch: int, opts: L.SolveOpts) -> int:
+        n = C.c_size_t(0)
+        L.check(self._lib.pf_workspace_size(self._h, int(batch), C.byref(opts), C.byref(n)),
+                "pf_workspace_size")
+        return int(n.value)
+
+    def workspace(self, batch: int, opts: L.SolveOpts) -> torch.Tensor:
+        need = self.workspace_bytes(batch, opts)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def solve(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=1,
+              ir_rtol=0.0, group_threads=0, keep_factors=False, out: SolveResult | None = None,
+              workspace: torch.Tensor | None = None) -> SolveResult:
+        """Batched Newton-Raphson (pf_solve) on the current stream; returns device tensors."""
+        batch = Pd.shape[0]
+        for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
+            _check_bus_tensor(v, nm, self.n_bus, batch)
+        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors)
+        ws = self.workspace(batch, opts) if workspace is None else workspace
+        if out is None:
+            e = dict(dtype=torch.float64, device=Pd.device)
+            out = SolveResult(
+                Vm=torch.empty(batch, self.n_bus, **e), Va=torch.empty(batch, self.n_bus, **e),
+                Pg=torch.empty(batch, self.n_bus, **e), Qg=torch.empty(batch, self.n_bus, **e),
+                iters=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                status=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                final_mismatch=torch.empty(batch, dtype=torch.float64, device=Pd.device))
+        stream = torch.cuda.current_stream(Pd.device).cuda_stream
+        L.check(self._lib.pf_solve(
+            self._h, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(), Vset.data_ptr(),
+            float(tol), int(max_iter), C.byref(opts), out.Vm.data_ptr(), out.Va.data_ptr(),
+            out.Pg.data_ptr(), out.Qg.data_ptr(), out.iters.data_ptr(), out.status.data_ptr(),
+            out.final_mismatch.data_ptr(), ws.data_ptr(), ws.numel(), stream), "pf_solve")
+        self._solve_id += 1
+        self._last = (batch, ws, bool(keep_factors))
+        return out
+
+    def adjoint(self, dVm, dVa, dPg=None, dQg=None) -> Gradients:
+        """Implicit-differentiation backward pass (pf_adjoint) of the last solve."""
+        if self._last is None or not self._last[2]:
+            raise RuntimeError("adjoint needs a preceding solve(..., keep_factors=True)")
+        batch, ws, _ = self._last
+        for nm, v in (("dVm", dVm), ("dVa", dVa), ("dPg", dPg), ("dQg", dQg)):
+            if v is not None:
+                _check_bus_tensor(v, nm, self.n_bus, batch)
+        e = dict(dtype=torch.float64, device=dVm.device)
+        g = Gradients(dPd=torch.empty(batch, self.n_bus, **e), dQd=torch.empty(batch, self.n_bus, **e),
+                      dPg=torch.empty(batch, self.n_bus, **e), dVset=torch.empty(batch, self.n_bus, **e),
+                      status=torch.empty(batch, dtype=torch.int32, device=dVm.device))
+        stream = torch.cuda.current_stream(dVm.device).cuda_stream
+        L.check(self._lib.pf_adjoint(
+            self._h, batch, dVm.data_ptr(), dVa.data_ptr(),
+            dPg.data_ptr() if dPg is not None else None,
+            dQg.data_ptr() if dQg is not None else None,
+            g.dPd.data_ptr(), g.dQd.data_ptr(), g.dPg.data_ptr(), g.dVset.data_ptr(),
+            g.status.data_ptr(), ws.data_ptr(), ws.numel(), stream), "pf_adjoint")
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PFLayer(torch.autograd.Function):
+    """Implicit power-flow layer: (Pd, Qd, Pg, Vset) -> (Vm, Va, Pg_out, Qg_out, status).
+
+    Forward runs pf_solve (keeping the factors); backward runs pf_adjoint, which
+    solves J1^T lambda = g_z1 with the reused factors (Sec. II-B.2) instead of
+    differentiating through the Newton iterations.
+    """
+
+    @staticmethod
+    def forward(ctx, pf: PowerFlow, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed",
+                ir_steps=1):
+        res = pf.solve(Pd.contiguous(), Qd.contiguous(), Pg.contiguous(), Vset.contiguous(), tol,
+                       max_iter, precision, ir_steps, keep_factors=True)
+        ctx.pf = pf
+        ctx.solve_id = pf._solve_id
+        ctx.mark_non_differentiable(res.status)
+        return res.Vm, res.Va, res.Pg, res.Qg, res.status
+
+    @staticmethod
+    def backward(ctx, gVm, gVa, gPg, gQg, _gs):
+        pf = ctx.pf
+        if pf._solve_id != ctx.solve_id:
+            raise RuntimeError("PFLayer.backward: the network handle solved again after this "
+                               "forward; run backward first or use one PowerFlow per layer call")
+        z = None
+
+        def dense(v):
+            nonlocal z
+            if v is None:
+                if z is None:
+                    z = torch.zeros(pf._last[0], pf.n_bus, dtype=torch.float64, device=pf.device)
+                return z
+            return v.contiguous()
+
+        g = pf.adjoint(dense(gVm), dense(gVa), None if gPg is None else gPg.contiguous(),
+                       None if gQg is None else gQg.contiguous())
+        return None, g.dPd, g.dQd, g.dPg, g.dVset, None, None, None, None

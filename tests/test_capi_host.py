@@ -1,0 +1,191 @@
+"""Host-side checks of libpf: the library loads, exports what include/pf.h
+declares, and its host-only entry points (Ybus assembly, symbolic analysis) are
+right.  Nothing here launches device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.pf_oracle as O
+from synthgrid import PQ, PV, SLACK, configs, make_grid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_07099_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2606_07099_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+@pytest.fixture(scope="module")
+def pfm(lib):
+    from paper_2606_07099_gb300 import powerflow
+    return powerflow
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "pf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2606_07099_gb300 import _lib
+    names = header_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_error_strings(lib):
+    from paper_2606_07099_gb300 import _lib
+    for code in range(7):
+        assert _lib.error_string(code)
+
+
+@pytest.mark.parametrize("name", ["c0", "c1", "c2"])
+def test_build_ybus_matches_oracle(pfm, name):
+    g = configs.raw_grid(name)
+    ip, ix, gg, bb = pfm.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+    Y = O.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+    assert np.array_equal(Y.indptr, ip) and np.array_equal(Y.indices, ix)
+    assert np.max(np.abs(Y.data - (gg + 1j * bb))) < 1e-12 * np.max(np.abs(Y.data))
+
+
+def test_build_ybus_rejects_bad_branches(pfm):
+    from paper_2606_07099_gb300._lib import PFError
+    with pytest.raises(PFError):
+        pfm.build_ybus(3, [0], [3], [0.1], [0.1], [0.0], [1.0])
+    with pytest.raises(PFError):
+        pfm.build_ybus(3, [0], [1], [0.0], [0.0], [0.0], [1.0])
+    with pytest.raises(PFError):
+        pfm.build_ybus(3, [0], [1], [0.1], [0.1], [0.0], [0.0])
+
+
+def _ybus(pfm, g):
+    return pfm.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+
+
+def dense_block_fill(n, edges):
+    """Boolean block elimination in the given order: the exact filled pattern."""
+    A = np.eye(n, dtype=bool)
+    for a, b in edges:
+        A[a, b] = A[b, a] = True
+    for k in range(n):
+        nz = np.flatnonzero(A[k, k + 1:]) + k + 1
+        for i in nz:
+            A[i, nz] = True
+            A[nz, i] = True
+    return A
+
+
+@pytest.mark.parametrize("name,seed,n_slack", [("c0", None, 1), ("c1", None, 1), ("c4a", None, 1),
+                                               ("rand", 3, 1), ("rand", 4, 3)])
+def test_symbolic_plan_is_a_valid_filled_pattern(pfm, name, seed, n_slack):
+    g = (configs.raw_grid(name) if name != "rand"
+         else make_grid("r", 60, 85, 12, 6, seed, n_slack=n_slack))
+    ip, ix, gg, bb = _ybus(pfm, g)
+    info, pos2bus, lu_ptr, lu_col, lev_ptr = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)
+    nonslack = np.flatnonzero(g.bus_type != SLACK)
+    n = len(nonslack)
+    assert info["n_block"] == n and info["n_slack"] == n_slack
+    assert info["n_unknowns"] == n + int(np.sum(g.bus_type == PQ))
+    # ordering is a permutation of the non-slack buses
+    assert np.array_equal(np.sort(pos2bus), nonslack)
+    bus2pos = -np.ones(g.n_bus, int)
+    bus2pos[pos2bus] = np.arange(n)
+    # the pattern contains the Ybus pattern of the non-slack buses (and every diagonal)
+    pat = np.zeros((n, n), bool)
+    for p in range(n):
+        cols = lu_col[lu_ptr[p]:lu_ptr[p + 1]]
+        assert np.all(np.diff(cols) > 0)
+        pat[p, cols] = True
+    edges = []
+    for i in nonslack:
+        for k in range(ip[i], ip[i + 1]):
+            j = ix[k]
+            if g.bus_type[j] != SLACK:
+                assert pat[bus2pos[i], bus2pos[j]]
+                if i != j:
+                    edges.append((bus2pos[i], bus2pos[j]))
+    # closed under elimination in position order and equal to the exact fill
+    assert np.array_equal(pat, dense_block_fill(n, edges))
+    assert info["nnzb_lu"] == int(pat.sum())
+    # level schedule: L entries of a row lie on lower levels, U entries on higher ones
+    level = np.zeros(n, int)
+    for l in range(len(lev_ptr) - 1):
+        level[lev_ptr[l]:lev_ptr[l + 1]] = l
+    assert lev_ptr[0] == 0 and lev_ptr[-1] == n
+    for p in range(n):
+        for q in lu_col[lu_ptr[p]:lu_ptr[p + 1]]:
+            if q < p:
+                assert level[q] < level[p]
+            elif q > p:
+                assert level[q] > level[p]
+    # the scalar J1 count of Eq. step1_jacobian
+    nnz = 0
+    for i in nonslack:
+        for k in range(ip[i], ip[i + 1]):
+            j = ix[k]
+            if g.bus_type[j] != SLACK:
+                nnz += (1 + (g.bus_type[i] == PQ)) * (1 + (g.bus_type[j] == PQ))
+    assert info["nnz_j1"] == nnz
+
+
+def test_analyze_rejects_bad_networks(pfm):
+    from paper_2606_07099_gb300._lib import PFError, PF_EINVAL, PF_ESINGULAR_PATTERN
+    g = configs.raw_grid("c0")
+    ip, ix, gg, bb = _ybus(pfm, g)
+    bt = g.bus_type.copy()
+    bt[bt == SLACK] = PV  # no slack bus
+    with pytest.raises(PFError) as e:
+        pfm.analyze(g.n_bus, ip, ix, gg, bb, bt)
+    assert e.value.code == PF_EINVAL
+    bt = g.bus_type.copy()
+    bt[3] = 7
+    with pytest.raises(PFError) as e:
+        pfm.analyze(g.n_bus, ip, ix, gg, bb, bt)
+    assert e.value.code == PF_EINVAL
+    # an island: two buses joined to each other but not to the rest
+    f = np.array([0, 1, 3], np.int32)
+    t = np.array([1, 2, 4], np.int32)
+    ip2, ix2, g2, b2 = pfm.build_ybus(5, f, t, [0.01] * 3, [0.1] * 3, [0.0] * 3, [1.0] * 3)
+    with pytest.raises(PFError) as e:
+        pfm.analyze(5, ip2, ix2, g2, b2, np.array([SLACK, PQ, PQ, PQ, PV], np.int32))
+    assert e.value.code == PF_ESINGULAR_PATTERN
+    # column index out of range
+    ix3 = ix.copy()
+    ix3[0] = g.n_bus
+    with pytest.raises(PFError) as e:
+        pfm.analyze(g.n_bus, ip, ix3, gg, bb, g.bus_type)
+    assert e.value.code == PF_EINVAL
+
+
+def test_analyze_sums_duplicates_and_accepts_unsorted(pfm):
+    g = configs.raw_grid("c0")
+    ip, ix, gg, bb = _ybus(pfm, g)
+    info0 = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)[0]
+    # split every entry into two halves and reverse each row
+    ip2 = [0]
+    ix2, g2, b2 = [], [], []
+    for i in range(g.n_bus):
+        for k in reversed(range(ip[i], ip[i + 1])):
+            ix2 += [ix[k], ix[k]]
+            g2 += [gg[k] / 2, gg[k] / 2]
+            b2 += [bb[k] / 2, bb[k] / 2]
+        ip2.append(len(ix2))
+    info1 = pfm.analyze(g.n_bus, np.array(ip2), np.array(ix2), np.array(g2), np.array(b2),
+                        g.bus_type)[0]
+    assert info0 == info1
+
+
+def test_all_slack_network_is_trivial(pfm):
+    ip, ix, gg, bb = pfm.build_ybus(2, [0], [1], [0.01], [0.1], [0.0], [1.0])
+    info = pfm.analyze(2, ip, ix, gg, bb, np.array([SLACK, SLACK], np.int32))[0]
+    assert info["n_block"] == 0 and info["nnzb_lu"] == 0 and info["n_levels"] == 0

@@ -1,0 +1,177 @@
+"""Parity of the CUDA Newton-Raphson path with the FP64 oracle (GPU)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle.pf_oracle as O
+from synthgrid import PQ, PV, SLACK, Scenarios, make_grid, make_scenarios, scale_loads
+
+from gpu_common import (compare, ensure_built, mismatch_checker, regular, run_gpu, run_oracle,
+                        to_dev, workload)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def PowerFlow():
+    ensure_built()
+    from paper_2606_07099_gb300.powerflow import PowerFlow
+    return PowerFlow
+
+
+@pytest.mark.parametrize("precision,ir", [("fp64", 0), ("mixed", 1), ("mixed", 0)])
+def test_c0_all_scenarios_match_stored_oracle(PowerFlow, precision, ir):
+    g, sc = workload("c0")
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c0_oracle.json")))
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=ir)
+    orc = {s: {k: (np.asarray(gold[k][s]) if isinstance(gold[k][s], list) else gold[k][s])
+               for k in ("Vm", "Va", "Pg", "Qg", "iters", "status", "final_mismatch")}
+           for s in range(sc.n)}
+    compare(gpu, orc, iter_slack=0 if precision == "fp64" else 1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c1_full_batch_sampled(PowerFlow, precision):
+    """118-bus, 4096 scenarios in one launch; 48 sampled scenarios against the oracle."""
+    g, sc = workload("c1")
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
+    rng = np.random.default_rng(0)
+    idx = sorted(set([0, sc.n - 1] + rng.choice(sc.n, 46, replace=False).tolist()))
+    compare(gpu, run_oracle(g, sc, idx), iter_slack=0 if precision == "fp64" else 1)
+    # every scenario converged within tol (property checked at full size)
+    assert np.all(gpu["status"] == 0)
+    assert np.all(gpu["final_mismatch"] <= 1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c2_sampled(PowerFlow, precision):
+    g, sc = workload("c2")
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
+    compare(gpu, run_oracle(g, sc, [0, 511, 1023]), iter_slack=0 if precision == "fp64" else 1)
+    assert np.all(gpu["status"] == 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c3_sampled(PowerFlow, precision):
+    g, sc = workload("c3")
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
+    compare(gpu, run_oracle(g, sc, [0, 255]), iter_slack=0 if precision == "fp64" else 1)
+    assert np.all(gpu["status"] == 0)
+
+
+@pytest.mark.parametrize("name,n", [("c4a", 2048), ("c4b", 512), ("c4c", 64)])
+def test_c4_grids_flags_and_values(PowerFlow, name, n):
+    """Uneven loads x U(0.6, 1.4): every flag and every converged value matches."""
+    g, sc = workload(name)
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, sc, precision="fp64")
+    k = {"c4a": 64, "c4b": 48, "c4c": 16}[name]
+    rng = np.random.default_rng(1)
+    idx = sorted(rng.choice(n, k, replace=False).tolist())
+    orc = run_oracle(g, sc, range(n) if name == "c4c" else idx)
+    worst = compare(gpu, orc, check=mismatch_checker(g, sc))
+    # wandering, solution-free scenarios are the minority that the loads x U(0.6, 1.4) create
+    assert worst["irregular"] <= 0.2 * len(orc)
+
+
+def test_thread_mapping_does_not_change_results(PowerFlow):
+    g, sc = workload("c1", 256)
+    pf = PowerFlow.from_grid(g)
+    ref = run_gpu(pf, sc, precision="fp64", group_threads=32)
+    for th in (64, 96, 128, 256):
+        out = run_gpu(pf, sc, precision="fp64", group_threads=th)
+        for k in ref:
+            assert np.array_equal(ref[k], out[k]), (th, k)
+    refm = run_gpu(pf, sc, precision="mixed", group_threads=32)
+    outm = run_gpu(pf, sc, precision="mixed", group_threads=160)
+    for k in refm:
+        assert np.array_equal(refm[k], outm[k]), k
+
+
+def test_two_bus_closed_form_on_gpu(PowerFlow):
+    P, Q, r, x, V1 = 1.2, 0.4, 0.05, 0.2, 1.06
+    g = make_grid("two", 2, 1, 0, 0, 0)
+    g.f[:] = [0]
+    g.t[:] = [1]
+    g.r[:] = [r]
+    g.x[:] = [x]
+    g.b[:] = [0.0]
+    g.tap[:] = [1.0]
+    g.bus_type[:] = [SLACK, PQ]
+    g.Vset[:] = [V1, 0.0]
+    sc = Scenarios(Pd=np.array([[0.0, P]]), Qd=np.array([[0.0, Q]]), Pg=np.zeros((1, 2)),
+                   Vset=np.array([[V1, 0.0]]))
+    pf = PowerFlow.from_grid(g)
+    a, b = r * P + x * Q, x * P - r * Q
+    c1 = 2 * a - V1 * V1
+    v2sq = (-c1 + np.sqrt(c1 * c1 - 4 * (r * r + x * x) * (P * P + Q * Q))) / 2
+    for prec in ("fp64", "mixed"):
+        out = run_gpu(pf, sc, tol=1e-12, precision=prec, ir_steps=2)
+        assert out["status"][0] == 0
+        assert abs(out["Vm"][0, 1] - np.sqrt(v2sq)) < 1e-10
+        assert abs(out["Va"][0, 1] + np.arctan2(b, v2sq + a)) < 1e-10
+
+
+def test_status_edge_cases(PowerFlow):
+    g, sc = workload("c0", 5)
+    pf = PowerFlow.from_grid(g)
+    for prec in ("fp64", "mixed"):
+        out = run_gpu(pf, sc, max_iter=0, precision=prec)
+        assert np.all(out["status"] == O.MAXITER) and np.all(out["iters"] == 0)
+        out = run_gpu(pf, sc, max_iter=1, precision=prec)
+        assert np.all(out["status"] == O.MAXITER) and np.all(out["iters"] == 1)
+        bad = Scenarios(Pd=sc.Pd.copy(), Qd=sc.Qd.copy(), Pg=sc.Pg.copy(), Vset=sc.Vset.copy())
+        bad.Pd[2, np.flatnonzero(g.bus_type == PQ)[0]] = np.nan
+        bad.Qd[4, np.flatnonzero(g.bus_type == PQ)[1]] = np.inf
+        out = run_gpu(pf, bad, precision=prec)
+        assert out["status"][2] == O.DIVERGED and out["status"][4] == O.DIVERGED
+        assert out["iters"][2] == 0
+        assert np.all(out["status"][[0, 1, 3]] == O.CONVERGED)
+        # a single scenario
+        one = Scenarios(Pd=sc.Pd[:1], Qd=sc.Qd[:1], Pg=sc.Pg[:1], Vset=sc.Vset[:1])
+        out = run_gpu(pf, one, precision=prec)
+        assert out["status"][0] == 0
+
+
+def test_infeasible_load_flags_match_oracle(PowerFlow):
+    g, sc = workload("c0", 6)
+    f = np.array([1, 3, 1e5, 1e7, 1e8, 1e9])[:, None]  # two solvable, four far past collapse
+    heavy = Scenarios(Pd=sc.Pd * f, Qd=sc.Qd * f, Pg=sc.Pg, Vset=sc.Vset)
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, heavy, precision="fp64", max_iter=15)
+    orc = run_oracle(g, heavy, range(6), max_iter=15)
+    assert all(regular(o) for o in orc.values())
+    assert [orc[s]["status"] for s in range(6)] == [0, 0, 2, 2, 2, 2]
+    compare(gpu, orc, max_iter=15, check=mismatch_checker(g, heavy))
+
+
+def test_multi_slack_grid(PowerFlow):
+    g = scale_loads(make_grid("ms", 80, 110, 15, 8, 17, n_slack=3), 0.5)
+    sc = make_scenarios(g, 40, 0.9, 1.1, 3)
+    pf = PowerFlow.from_grid(g)
+    for prec in ("fp64", "mixed"):
+        gpu = run_gpu(pf, sc, precision=prec, ir_steps=1)
+        compare(gpu, run_oracle(g, sc, range(0, 40, 5)), iter_slack=0 if prec == "fp64" else 1)
+
+
+def test_bad_arguments_raise(PowerFlow):
+    import torch
+    from paper_2606_07099_gb300._lib import PFError
+    g, sc = workload("c0", 4)
+    pf = PowerFlow.from_grid(g)
+    Pd, Qd, Pg, Vset = to_dev(sc)
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(PFError):
+        pf.solve(Pd, Qd, Pg, Vset, workspace=small)
+    with pytest.raises(PFError):
+        pf.solve(Pd, Qd, Pg, Vset, tol=0.0)
+    with pytest.raises(ValueError):
+        pf.solve(Pd.float(), Qd, Pg, Vset)
+    with pytest.raises(RuntimeError):
+        pf.adjoint(Pd, Pd)  # no preceding solve with keep_factors
