@@ -43,6 +43,24 @@ FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 
 
+def profiled_traffic(kernel_json="nr_solve_c1_mixed.json"):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel source is
+    unchanged since the capture (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", kernel_json)) as fh:
+            prof = json.load(fh)
+        src = b""
+        for f in ("pf_kernels.cu", "pf_device.cuh"):
+            with open(os.path.join(ROOT, "paper_2606_07099_gb300", "csrc", f), "rb") as fh:
+                src += fh.read()
+        if hashlib.sha256(src).hexdigest()[:16] != prof["source_sha256_16"]:
+            return None
+        return prof["dram_bytes_read_per_launch"] + prof["dram_bytes_write_per_launch"]
+    except Exception:
+        return None
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -67,22 +85,39 @@ def _oracle_chunk(args):
     return conv
 
 
+class OraclePool:
+    """A spawn-started process pool (one BLAS thread per worker) running the oracle."""
+
+    def __init__(self, n_sample_hint: int):
+        cores = os.cpu_count() or 1
+        self.procs = max(1, min(cores, n_sample_hint))
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        self.pool.map(_oracle_chunk, [(WORKLOAD, 0, 1)] * self.procs)  # warm: imports, grid
+
+    def rate(self, n_sample: int):
+        """Converged solves/s on the first n_sample scenarios of the workload."""
+        bounds = np.linspace(0, n_sample, self.procs + 1).astype(int)
+        chunks = [(WORKLOAD, int(bounds[i]), int(bounds[i + 1])) for i in range(self.procs)]
+        t0 = time.perf_counter()
+        conv = sum(self.pool.map(_oracle_chunk, chunks))
+        dt = time.perf_counter() - t0
+        return conv / dt, dt, conv
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def oracle_rate(n_sample: int):
     """Converged solves/s of the CPU oracle on the first n_sample scenarios, all cores."""
-    cores = os.cpu_count() or 1
-    procs = max(1, min(cores, n_sample))
-    bounds = np.linspace(0, n_sample, procs + 1).astype(int)
-    chunks = [(WORKLOAD, int(bounds[i]), int(bounds[i + 1])) for i in range(procs)]
-    # one BLAS thread per worker process: the workers are the parallelism
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
-        pool.map(_oracle_chunk, [(WORKLOAD, 0, 1)] * procs)  # warm the workers (imports)
-        t0 = time.perf_counter()
-        conv = sum(pool.map(_oracle_chunk, chunks))
-        dt = time.perf_counter() - t0
-    return conv / dt, procs, dt, conv
+    pool = OraclePool(n_sample)
+    try:
+        r, dt, conv = pool.rate(n_sample)
+    finally:
+        pool.close()
+    return r, pool.procs, dt, conv
 
 
 def cpu_model():
@@ -153,7 +188,7 @@ def alg_counts(info: dict, n_bus: int, iters: np.ndarray, ir_steps: int, precisi
 
     Per Newton iteration of one scenario: the FP64 mismatch (complex SpMV, 8
     flop per Ybus entry, plus ~20 flop per bus for V, S and F), the Jacobian
-    fill (~12 flop per 2x2 block, FP64), the block LU (16 flop per Schur block
+    fill (~12 flop per 2x2 block; FP32 in the mixed form), the block LU (16 flop per Schur block
     update, ~24 per L-column scaling), the triangular solves (8 flop per stored
     block per sweep pair member), and per refinement sweep a matrix-free FP64
     residual (another complex SpMV + ~30 flop per bus) and one more solve.  One
@@ -169,9 +204,10 @@ def alg_counts(info: dict, n_bus: int, iters: np.ndarray, ir_steps: int, precisi
     solve = 8 * nnzb
     resid = 8 * nnzY + 30 * n_bus
     mixed = precision == "mixed"
-    f64 = (it + n_sc) * mism + it * fill + (it * ir_steps * resid if mixed else 0)
+    # the mixed form fills the Jacobian in FP32 (it feeds the FP32 factor)
+    f64 = (it + n_sc) * mism + (it * ir_steps * resid if mixed else it * fill)
     fsolve = it * (lu + solve * (1 + (ir_steps if mixed else 0)))
-    f32 = fsolve if mixed else 0.0
+    f32 = fsolve + it * fill if mixed else 0.0
     if not mixed:
         f64 += fsolve
     hbm = n_sc * (8 * 4 * n_bus + 8 * 4 * n_bus + 16 + 16 * n_bus + 16)
@@ -187,8 +223,8 @@ def gpu_leg(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    g = configs.grid(WORKLOAD)
-    sc = configs.scenarios(WORKLOAD, g=g)
+    g = configs.grid(args.workload)
+    sc = configs.scenarios(args.workload, g=g)
     N, nb = sc.n, g.n_bus
     pf = PowerFlow.from_grid(g)
     info = pf.info()
@@ -217,14 +253,17 @@ def gpu_leg(args, rank, world):
         return [e0.elapsed_time(e1) for e0, e1 in evs]
 
     opts = dict(precision="mixed", ir_steps=args.ir_steps, ir_rtol=args.ir_rtol)
+    secs = set(args.sections.split(","))
     res = pf.solve(Pd, Qd, Pg, Vset, **opts)
     mixed_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **opts)  # noqa: E731
-    res64 = pf.solve(Pd, Qd, Pg, Vset, precision="fp64")
-    fp64_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64)  # noqa: E731
+    if "fp64" in secs:
+        res64 = pf.solve(Pd, Qd, Pg, Vset, precision="fp64")
+        fp64_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64)  # noqa: E731
 
     # forward + backward of the implicit layer with the config-2 style loss cotangents
     slack = torch.as_tensor(g.bus_type == 2, device=dev)
-    resk = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, **opts)
+    if "fwdbwd" in secs:
+        resk = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, **opts)
 
     def fwd_bwd():
         r = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, out=resk, **opts)
@@ -237,7 +276,8 @@ def gpu_leg(args, rank, world):
     out_host = [torch.empty(N, nb, dtype=torch.float64).pin_memory() for _ in range(2)]
     st_host = torch.empty(N, dtype=torch.int32).pin_memory()
     dev_in = [torch.empty_like(Pd) for _ in range(4)]
-    rese = pf.solve(Pd, Qd, Pg, Vset, **opts)
+    if "e2e" in secs:
+        rese = pf.solve(Pd, Qd, Pg, Vset, **opts)
 
     def e2e():
         for d, h in zip(dev_in, host):
@@ -247,18 +287,19 @@ def gpu_leg(args, rank, world):
         out_host[1].copy_(rese.Va, non_blocking=True)
         st_host.copy_(rese.status, non_blocking=True)
 
+    none = [float("nan")]
     with ClockSampler(dev.index) as clk:
         t_mixed = timed(mixed_fn, args.steps, args.warmup)
-        t_fp64 = timed(fp64_fn, args.steps, args.warmup)
-        t_fb = timed(fwd_bwd, args.steps, args.warmup)
-        t_e2e = timed(e2e, args.steps, args.warmup)
+        t_fp64 = timed(fp64_fn, args.steps, args.warmup) if "fp64" in secs else none
+        t_fb = timed(fwd_bwd, args.steps, args.warmup) if "fwdbwd" in secs else none
+        t_e2e = timed(e2e, args.steps, args.warmup) if "e2e" in secs else none
     clocks = clk.summary()
     torch.cuda.synchronize(dev)
     st = res.status.cpu().numpy()
     its = res.iters.cpu().numpy()
     conv = int((st == 0).sum())
-    conv64 = int((res64.status.cpu().numpy() == 0).sum())
-    conve = int((rese.status.cpu().numpy() == 0).sum())
+    conv64 = int((res64.status.cpu().numpy() == 0).sum()) if "fp64" in secs else 0
+    conve = int((rese.status.cpu().numpy() == 0).sum()) if "e2e" in secs else 0
     fmax = float(res.final_mismatch.max().item())
 
     def agg(ts):
@@ -282,7 +323,8 @@ def gpu_leg(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": T_mixed / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "n_bus": nb, "batch_per_gpu": N,
+        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD
+                   else f"synthgrid workload {args.workload}", "n_bus": nb, "batch_per_gpu": N,
                    "global_batch": N * world, "precision": "mixed (FP32 LU + FP64 mismatch/refinement)",
                    "ir_steps": args.ir_steps, "ir_rtol": args.ir_rtol,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
@@ -296,7 +338,8 @@ def gpu_leg(args, rank, world):
                 "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N},
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved_eq, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_eq / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_eq / FP64_PEAK_TFLOPS,
+                     "traffic": profiled_traffic() if args.workload == WORKLOAD else None,
                      "kernel": "nr_solve_kernel<float>",
                      "note": ("FP64-equivalent rate: F64 + F32*(peak64/peak32) flops per launch over "
                               "the launch time; peaks derived from unit counts (FP32 "
@@ -318,7 +361,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ir-steps", type=int, default=1)
     ap.add_argument("--ir-rtol", type=float, default=0.0)
-    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--cpu-sample", type=int, default=4096,
+                    help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
+    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,e2e",
+                    help="timed sections to run (the first one, mixed, always runs)")
+    ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -328,11 +375,13 @@ def main():
         if rank != 0:
             return
         # the CPU oracle on a bounded sample of the workload, per step
-        per_step = max(16, args.cpu_sample // 4)
-        rates = []
-        for _ in range(args.steps):
-            r, procs, dt, conv = oracle_rate(per_step)
-            rates.append(r)
+        per_step = max(64, args.cpu_sample // 4)
+        pool = OraclePool(per_step)
+        procs = pool.procs
+        for _ in range(args.warmup):
+            pool.rate(per_step)
+        rates = [pool.rate(per_step)[0] for _ in range(args.steps)]
+        pool.close()
         v = statistics.median(rates)
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -352,7 +401,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     line = gpu_leg(args, rank, world)
-    if rank == 0:
+    if rank == 0 and args.cpu_sample > 0:
         r, procs, dt, conv = oracle_rate(args.cpu_sample)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
                                 "sample": f"first {args.cpu_sample} of the 4096 scenarios "

@@ -49,7 +49,8 @@ struct DeviceGuard {
 
 int auto_threads(int n) {
     if (n <= 48) return 32;
-    if (n <= 400) return 64;
+    if (n <= 160) return 128;
+    if (n <= 400) return 128;
     if (n <= 1600) return 128;
     if (n <= 6000) return 256;
     return 512;
@@ -58,28 +59,35 @@ int auto_threads(int n) {
 // Shared memory reserved for the kernels' static arrays and the runtime.
 constexpr size_t kStaticSmemReserve = 1024;
 
+// Shared-memory placement of one kernel: vectors and factor in shared memory if both
+// fit, else the vectors only, else neither (everything streams from the global slot).
+pf::KernelSmem place(size_t vec_bytes, size_t fac_bytes, size_t budget) {
+    pf::KernelSmem k{};
+    k.vec_bytes = vec_bytes;
+    if (vec_bytes + fac_bytes <= budget) {
+        k.vec_in_smem = 1;
+        k.fac_in_smem = 1;
+        k.smem_fac_off = vec_bytes;
+        k.smem_bytes = vec_bytes + fac_bytes;
+    } else if (vec_bytes <= budget) {
+        k.vec_in_smem = 1;
+        k.smem_bytes = vec_bytes;
+    }
+    return k;
+}
+
 pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep) {
     const pf::Plan& P = h->plan;
     pf::SlotLayout L{};
-    L.vec_bytes = pf::carve(nullptr, P.n_bus, P.n, ft_bytes, nullptr);
     L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
     const size_t budget = (size_t)h->smem_optin > kStaticSmemReserve
                               ? (size_t)h->smem_optin - kStaticSmemReserve : 0;
-    if (L.vec_bytes + L.fac_bytes <= budget) {
-        L.vec_in_smem = 1;
-        L.fac_in_smem = 1;
-        L.smem_fac_off = L.vec_bytes;
-        L.smem_bytes = L.vec_bytes + L.fac_bytes;
-    } else if (L.vec_bytes <= budget) {
-        L.vec_in_smem = 1;
-        L.fac_in_smem = 0;
-        L.smem_bytes = L.vec_bytes;
-    } else {
-        L.vec_in_smem = 0;
-        L.fac_in_smem = 0;
-        L.smem_bytes = 0;
-    }
-    L.fac_global = (!L.fac_in_smem || keep) ? 1 : 0;
+    L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes, budget);
+    L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes, budget);
+    L.fac_global = (!L.fwd.fac_in_smem || keep) ? 1 : 0;
+    size_t vec_global = 0;
+    if (!L.fwd.vec_in_smem) vec_global = std::max(vec_global, L.fwd.vec_bytes);
+    if (keep && !L.adj.vec_in_smem) vec_global = std::max(vec_global, L.adj.vec_bytes);
     size_t o = 0;
     L.off_state = o;
     o = pf::align_up(o + sizeof(double) * 2 * (size_t)P.n_bus, 256);
@@ -89,9 +97,9 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep) {
         L.off_fac = o;
         o = pf::align_up(o + L.fac_bytes, 256);
     }
-    if (!L.vec_in_smem) {
+    if (vec_global) {
         L.off_vec = o;
-        o = pf::align_up(o + L.vec_bytes, 256);
+        o = pf::align_up(o + vec_global, 256);
     }
     L.slot_bytes = o;
     return L;
@@ -201,12 +209,18 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     // pack every plan array into one device buffer
     std::vector<unsigned char> buf;
     std::vector<double2> ygb(P.y_g.size()), ytgb(P.yt_g.size());
-    for (size_t k = 0; k < P.y_g.size(); ++k) ygb[k] = make_double2(P.y_g[k], P.y_b[k]);
+    std::vector<float2> ygb32(P.y_g.size());
+    for (size_t k = 0; k < P.y_g.size(); ++k) {
+        ygb[k] = make_double2(P.y_g[k], P.y_b[k]);
+        ygb32[k] = make_float2((float)P.y_g[k], (float)P.y_b[k]);
+    }
     for (size_t k = 0; k < P.yt_g.size(); ++k) ytgb[k] = make_double2(P.yt_g[k], P.yt_b[k]);
     std::vector<int2> la(P.la_L.size()), sch(P.sch_L.size());
+    std::vector<int4> levg(P.n_levels);
+    for (int l = 0; l < P.n_levels; ++l) levg[l] = make_int4(P.lev_gL[l], P.lev_gU[l], P.lev_gS[l], 0);
     for (size_t k = 0; k < la.size(); ++k) la[k] = make_int2(P.la_L[k], P.la_D[k]);
     for (size_t k = 0; k < sch.size(); ++k) sch[k] = make_int2(P.sch_L[k], P.sch_U[k]);
-    size_t o_ygb = push(buf, ygb), o_ytgb = push(buf, ytgb);
+    size_t o_ygb = push(buf, ygb), o_ytgb = push(buf, ytgb), o_ygb32 = push(buf, ygb32);
     size_t o_yptr = push(buf, P.y_ptr), o_yidx = push(buf, P.y_idx);
     size_t o_ytptr = push(buf, P.yt_ptr), o_ytidx = push(buf, P.yt_idx);
     size_t o_bt = push(buf, P.bus_type), o_p2b = push(buf, P.pos2bus), o_b2p = push(buf, P.bus2pos);
@@ -214,7 +228,7 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     size_t o_luc = push(buf, P.lu_col), o_lud = push(buf, P.lu_diag), o_lum = push(buf, P.lu_mirror);
     size_t o_fy = push(buf, P.fill_y), o_lap = push(buf, P.la_ptr), o_la = push(buf, la);
     size_t o_stp = push(buf, P.sch_tptr), o_stg = push(buf, P.sch_tgt), o_scp = push(buf, P.sch_cptr);
-    size_t o_sch = push(buf, sch);
+    size_t o_sch = push(buf, sch), o_levg = push(buf, levg);
     if (buf.empty()) buf.resize(16);
     if (cudaMalloc(&h->d_buf, buf.size()) != cudaSuccess) {
         delete h;
@@ -235,6 +249,7 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     d.y_ptr = I(o_yptr);
     d.y_idx = I(o_yidx);
     d.y_gb = reinterpret_cast<const double2*>(base + o_ygb);
+    d.y_gb32 = reinterpret_cast<const float2*>(base + o_ygb32);
     d.yt_ptr = I(o_ytptr);
     d.yt_idx = I(o_ytidx);
     d.yt_gb = reinterpret_cast<const double2*>(base + o_ytgb);
@@ -242,6 +257,7 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     d.pos2bus = I(o_p2b);
     d.bus2pos = I(o_b2p);
     d.lev_ptr = I(o_lev);
+    d.lev_g = reinterpret_cast<const int4*>(base + o_levg);
     d.lu_ptr = I(o_lup);
     d.lu_row = I(o_lur);
     d.lu_col = I(o_luc);

@@ -6,7 +6,7 @@
 // scenario's state staged in shared memory when it fits:
 //
 //   mismatch  I = Y V, S = V conj(I), F1 = spec - S           (Sec. II-A, FP64)
-//   fill      polar 2x2 Jacobian blocks on the fixed pattern  (Alg. 1 values)
+//   fill      polar 2x2 Jacobian blocks on the fixed pattern  (Alg. 1 values, FT)
 //   factor    level-scheduled right-looking 2x2-block LU      (FT = float | double)
 //   solve     level-scheduled block triangular sweeps         (FT)
 //   refine    FP64 residual r = -F1 - J1 dz (matrix-free)     (Table I + refinement)
@@ -97,37 +97,55 @@ __device__ double group_max(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- FP64 network kernels
-// V = Vm e^{j theta}
+// u = e^{j theta}, V = Vm u
 __device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
         double s, c;
         sincos(a.Va[i], &s, &c);
+        a.Uc[i] = c;
+        a.Us[i] = s;
         a.Vre[i] = a.Vm[i] * c;
         a.Vim[i] = a.Vm[i] * s;
     }
 }
 
-// I = Y V, S = V conj(I), F1 at pivot positions; returns ||F1||_inf (inf if non-finite)
+// FP32 copies of the per-bus quantities the FP32 Jacobian fill reads:
+// V, u, Vm and (pu, qu) = u conj(I), so that S = Vm (pu + j qu).
+__device__ __forceinline__ void store_bus_f32(const Arrays& a, int i, double ir, double ii) {
+    const double c = a.Uc[i], s = a.Us[i];
+    a.fvr[i] = float(a.Vre[i]);
+    a.fvi[i] = float(a.Vim[i]);
+    a.fur[i] = float(c);
+    a.fui[i] = float(s);
+    a.fvm[i] = float(a.Vm[i]);
+    a.fpu[i] = float(c * ir + s * ii);
+    a.fqu[i] = float(s * ir - c * ii);
+}
+
+// I = Y V, S = V conj(I), F1 at pivot positions; returns ||F1||_inf (inf if non-finite).
+// With F32COPY the FP32 per-bus copies for the FP32 Jacobian fill are written too.
+template <bool F32COPY>
 __device__ double phase_mismatch(const DevPlan& P, const Arrays& a, double* red) {
     double lmax = 0.0;
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
         double ir = 0.0, ii = 0.0;
-        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
-            const int j = P.y_idx[k];
-            const double2 y = P.y_gb[k];
+        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
+            const int j = __ldg(P.y_idx + k);
+            const double2 y = __ldg(P.y_gb + k);
             const double vr = a.Vre[j], vi = a.Vim[j];
             ir = fma(y.x, vr, fma(-y.y, vi, ir));
             ii = fma(y.x, vi, fma(y.y, vr, ii));
         }
         a.Ire[i] = ir;
         a.Iim[i] = ii;
-        const int p = P.bus2pos[i];
+        if (F32COPY) store_bus_f32(a, i, ir, ii);
+        const int p = __ldg(P.bus2pos + i);
         if (p >= 0) {
             const double vr = a.Vre[i], vi = a.Vim[i];
             const double Pi = vr * ir + vi * ii;
             const double Qi = vi * ir - vr * ii;
             const double fP = a.Psp[i] - Pi;
-            const double fQ = (P.bus_type[i] == 0) ? a.Qsp[i] - Qi : 0.0;
+            const double fQ = (__ldg(P.bus_type + i) == 0) ? a.Qsp[i] - Qi : 0.0;
             a.F[2 * p] = fP;
             a.F[2 * p + 1] = fQ;
             lmax = fmax(lmax, fmax(absinf(fP), absinf(fQ)));
@@ -149,9 +167,9 @@ __device__ void phase_jvt(const DevPlan& P, const Arrays& a) {
     gsync();
     for (int j = threadIdx.x; j < P.n_bus; j += blockDim.x) {
         double gr = 0.0, gi = 0.0;
-        for (int k = P.yt_ptr[j]; k < P.yt_ptr[j + 1]; ++k) {
-            const int i = P.yt_idx[k];
-            const double2 y = P.yt_gb[k];  // Y_ij
+        for (int k = __ldg(P.yt_ptr + j); k < __ldg(P.yt_ptr + (j + 1)); ++k) {
+            const int i = __ldg(P.yt_idx + k);
+            const double2 y = __ldg(P.yt_gb + k);  // Y_ij
             const double hr = a.dVre[i], hi = a.dVim[i];
             gr = fma(hr, y.x, fma(-hi, y.y, gr));
             gi = fma(hr, y.y, fma(hi, y.x, gi));
@@ -160,93 +178,140 @@ __device__ void phase_jvt(const DevPlan& P, const Arrays& a) {
         const double Ir = a.Ire[j], Ii = a.Iim[j];
         gr += mr * Ir - mi * Ii;      // conj(m I) = (mr Ir - mi Ii) - j(mr Ii + mi Ir)
         gi -= mr * Ii + mi * Ir;
-        const double vm = a.Vm[j];
         const double vr = a.Vre[j], vi = a.Vim[j];
-        const double inv = 1.0 / vm;
-        a.w0[j] = (gr * vr - gi * vi) * inv;
+        a.w0[j] = gr * a.Uc[j] - gi * a.Us[j];
         a.w1[j] = -(gr * vi + gi * vr);
     }
 }
 
 // ---------------------------------------------------------------- Jacobian fill (Alg. 1)
-// J1 = dF1/dz1 in 2x2 blocks; F = spec - S, so every entry is minus the derivative
-// of the calculated injection.  With W = V_i conj(Y_ij V_j) (i != j):
-//   dP_i/dtheta_j = Im W, dQ_i/dtheta_j = -Re W, dP_i/dVm_j = Re W / Vm_j,
-//   dQ_i/dVm_j = Im W / Vm_j;
-// on the diagonal: dP_i/dtheta_i = -Q_i - B_ii Vm_i^2, dQ_i/dtheta_i = P_i - G_ii Vm_i^2,
-//   dP_i/dVm_i = (P_i + G_ii Vm_i^2) / Vm_i, dQ_i/dVm_i = (Q_i - B_ii Vm_i^2) / Vm_i.
-template <typename FT>
-__device__ void phase_fill(const DevPlan& P, const Arrays& a, FT* fac) {
+// J1 = dF1/dz1 in 2x2 blocks; F = spec - S, so every entry is minus the derivative of
+// the calculated injection.  With u = e^{j theta}, W = V_i conj(Y_ij V_j) and
+// W' = V_i conj(Y_ij u_j) = W / Vm_j (i != j):
+//   dP_i/dtheta_j = Im W, dQ_i/dtheta_j = -Re W, dP_i/dVm_j = Re W', dQ_i/dVm_j = Im W';
+// on the diagonal, with pu + j qu = u_i conj(I_i) (so P_i + j Q_i = Vm_i (pu + j qu)):
+//   dP_i/dtheta_i = -Q_i - B_ii Vm_i^2, dQ_i/dtheta_i = P_i - G_ii Vm_i^2,
+//   dP_i/dVm_i = pu + G_ii Vm_i,        dQ_i/dVm_i = qu - B_ii Vm_i.
+// The values are the same as Alg. 1's; they are computed in the precision of the
+// factor they feed (FP32 from FP32 copies of the bus quantities, or FP64).
+template <typename T>
+__device__ __forceinline__ Blk<T> jac_block(bool diag, T gij, T bij, T vri, T vii, T urj, T uij,
+                                            T vmj, T vmi, T pui, T qui) {
+    if (diag) {
+        const T vm2 = vmi * vmi;
+        return {vmi * qui + bij * vm2, -(pui + gij * vmi), -vmi * pui + gij * vm2,
+                -(qui - bij * vmi)};
+    }
+    const T yur = gij * urj - bij * uij, yui = gij * uij + bij * urj;  // Y_ij u_j
+    const T wr = vri * yur + vii * yui;                                 // W' = V_i conj(Y_ij u_j)
+    const T wi = vii * yur - vri * yui;
+    return {-wi * vmj, -wr, wr * vmj, -wi};
+}
+
+template <typename T>
+__device__ __forceinline__ Blk<T> pad_pv(Blk<T> m, bool diag, int ti, int tj) {
+    // PV buses: no dQ row and no Vm column; padded with the identity equation dVm_i = 0
+    if (ti == 1) { m.c = T(0); m.d = T(0); }
+    if (tj == 1) { m.b = T(0); m.d = T(0); }
+    if (diag && ti == 1) m.d = T(1);
+    return m;
+}
+
+__device__ void phase_fill(const DevPlan& P, const Arrays& a, float* fac) {
     for (int e = threadIdx.x; e < P.nnzb; e += blockDim.x) {
-        const int p = P.lu_row[e], q = P.lu_col[e];
-        const int yi = P.fill_y[e];
-        const int i = P.pos2bus[p], j = P.pos2bus[q];
-        double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+        const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
+        const int yi = __ldg(P.fill_y + e);
+        const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
+        Blk<float> m{0.f, 0.f, 0.f, 0.f};
         if (yi >= 0) {
-            const double2 y = P.y_gb[yi];
-            if (p == q) {
-                const double vr = a.Vre[i], vi = a.Vim[i], ir = a.Ire[i], ii = a.Iim[i];
-                const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
-                const double vm = a.Vm[i], vm2 = vm * vm, ivm = 1.0 / vm;
-                a00 = Qi + y.y * vm2;
-                a01 = -(Pi + y.x * vm2) * ivm;
-                a10 = -Pi + y.x * vm2;
-                a11 = -(Qi - y.y * vm2) * ivm;
-            } else {
-                const double vr = a.Vre[j], vi = a.Vim[j];
-                const double yvr = y.x * vr - y.y * vi, yvi = y.x * vi + y.y * vr;
-                const double Wr = a.Vre[i] * yvr + a.Vim[i] * yvi;
-                const double Wi = a.Vim[i] * yvr - a.Vre[i] * yvi;
-                const double ivm = 1.0 / a.Vm[j];
-                a00 = -Wi;
-                a10 = Wr;
-                a01 = -Wr * ivm;
-                a11 = -Wi * ivm;
-            }
+            const float2 y = __ldg(P.y_gb32 + yi);
+            m = jac_block<float>(p == q, y.x, y.y, a.fvr[i], a.fvi[i], a.fur[j], a.fui[j],
+                                 a.fvm[j], a.fvm[i], a.fpu[i], a.fqu[i]);
         }
-        // PV buses: no dQ row and no Vm column; padded with the identity equation
-        if (P.bus_type[i] == 1) { a10 = 0.0; a11 = 0.0; }
-        if (P.bus_type[j] == 1) { a01 = 0.0; a11 = 0.0; }
-        if (p == q && P.bus_type[i] == 1) a11 = 1.0;
-        stb(fac, e, Blk<FT>{FT(a00), FT(a01), FT(a10), FT(a11)});
+        stb(fac, e, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
+    }
+}
+
+__device__ void phase_fill(const DevPlan& P, const Arrays& a, double* fac) {
+    for (int e = threadIdx.x; e < P.nnzb; e += blockDim.x) {
+        const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
+        const int yi = __ldg(P.fill_y + e);
+        const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
+        Blk<double> m{0.0, 0.0, 0.0, 0.0};
+        if (yi >= 0) {
+            const double2 y = __ldg(P.y_gb + yi);
+            const double c = a.Uc[i], s = a.Us[i], ir = a.Ire[i], ii = a.Iim[i];
+            m = jac_block<double>(p == q, y.x, y.y, a.Vre[i], a.Vim[i], a.Uc[j], a.Us[j],
+                                  a.Vm[j], a.Vm[i], c * ir + s * ii, s * ir - c * ii);
+        }
+        stb(fac, e, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
     }
 }
 
 // ---------------------------------------------------------------- block LU
-// Right-looking, one elimination-tree level at a time.  Phase A scales the L
-// columns of the level's pivots; phase B gathers every Schur update of the level
-// into its target block (no two threads write the same block) and replaces the
-// level's pivot blocks by their inverses.  Returns nonzero if a pivot was singular.
+// Gathers (one row of a triangular sweep, or the Schur updates of one target block) run
+// on one thread; their indices and operands are loaded kBatch at a time before any
+// arithmetic, so the loads of a gather overlap instead of forming one long chain (four
+// FP32 blocks, or two FP64 blocks to stay within the register budget).  The summation
+// order depends only on the plan, so results do not depend on blockDim.
+template <typename FT>
+constexpr int kBatch = sizeof(FT) == 4 ? 4 : 2;
+
+// Right-looking, one elimination-tree level at a time.  Phase A scales the L columns of
+// the level's pivots; phase B gathers every Schur update of the level into its target
+// block (no two threads write the same block) and replaces the level's pivot blocks by
+// their inverses.  Returns nonzero if a pivot was singular.
 template <typename FT>
 __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
     int bad = 0;
     if (threadIdx.x == 0) *s_bad = 0;
     for (int l = 0; l < P.n_levels; ++l) {
-        const int a0 = P.la_ptr[l], a1 = P.la_ptr[l + 1];
+        const int a0 = __ldg(P.la_ptr + l), a1 = __ldg(P.la_ptr + l + 1);
         for (int c = a0 + threadIdx.x; c < a1; c += blockDim.x) {
-            const int2 ld = P.la[c];
+            const int2 ld = __ldg(P.la + c);
             int dummy = 0;
             Blk<FT> dinv = inv2(ldb(fac, ld.y), &dummy);
             stb(fac, ld.x, mul(ldb(fac, ld.x), dinv));
         }
         gsync();
-        const int t0 = P.sch_tptr[l], t1 = P.sch_tptr[l + 1];
-        const int p0 = P.lev_ptr[l], p1 = P.lev_ptr[l + 1];
-        const int nt = t1 - t0, nw = nt + (p1 - p0);
-        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
-            if (w < nt) {
-                const int t = t0 + w;
-                const int tg = P.sch_tgt[t];
-                Blk<FT> acc = ldb(fac, tg);
-                for (int c = P.sch_cptr[t]; c < P.sch_cptr[t + 1]; ++c) {
-                    const int2 lu = P.sch[c];
-                    acc = msub(acc, ldb(fac, lu.x), ldb(fac, lu.y));
+        const int t0 = __ldg(P.sch_tptr + l), t1 = __ldg(P.sch_tptr + l + 1);
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int c0 = __ldg(P.sch_cptr + t), c1 = __ldg(P.sch_cptr + t + 1);
+            Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+            constexpr int W = kBatch<FT>;
+            for (int c = c0; c < c1; c += W) {
+                int2 lu[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) lu[k] = (c + k < c1) ? __ldg(P.sch + c + k) : make_int2(-1, -1);
+                Blk<FT> xl[W], yu[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    if (lu[k].x >= 0) {
+                        xl[k] = ldb(fac, lu[k].x);
+                        yu[k] = ldb(fac, lu[k].y);
+                    } else {
+                        xl[k] = yu[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
+                    }
                 }
-                stb(fac, tg, acc);
-            } else {
-                const int dk = P.lu_diag[p0 + (w - nt)];
-                stb(fac, dk, inv2(ldb(fac, dk), &bad));
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    acc.a += xl[k].a * yu[k].a + xl[k].b * yu[k].c;
+                    acc.b += xl[k].a * yu[k].b + xl[k].b * yu[k].d;
+                    acc.c += xl[k].c * yu[k].a + xl[k].d * yu[k].c;
+                    acc.d += xl[k].c * yu[k].b + xl[k].d * yu[k].d;
+                }
             }
+            const int tg = __ldg(P.sch_tgt + t);
+            Blk<FT> m = ldb(fac, tg);
+            m.a -= acc.a;
+            m.b -= acc.b;
+            m.c -= acc.c;
+            m.d -= acc.d;
+            stb(fac, tg, m);
+        }
+        for (int p = __ldg(P.lev_ptr + l) + threadIdx.x; p < __ldg(P.lev_ptr + l + 1); p += blockDim.x) {
+            const int dk = __ldg(P.lu_diag + p);
+            stb(fac, dk, inv2(ldb(fac, dk), &bad));
         }
         gsync();
     }
@@ -255,76 +320,94 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
     return *s_bad;
 }
 
-// x <- (LU)^{-1} x, in place, x holds 2 values per pivot
-template <typename FT>
-__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x) {
-    for (int l = 0; l < P.n_levels; ++l) {
-        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
-            FT x0 = x[2 * p], x1 = x[2 * p + 1];
-            for (int e = P.lu_ptr[p]; e < P.lu_diag[p]; ++e) {
-                const int q = P.lu_col[e];
-                const Blk<FT> m = ldb(fac, e);
-                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
-                x0 -= m.a * y0 + m.b * y1;
-                x1 -= m.c * y0 + m.d * y1;
+// One level of a block triangular sweep: x_p <- op(x_p - sum_e M_e x_q(e)) for the rows p
+// of the level, where the gathered entries e of row p are the L part (lower sweeps) or
+// the U part (upper sweeps) of row p in the L+U pattern.  TRANS sweeps read the block at
+// the mirrored position, transposed (row p of U^T / L^T).  The stored pivot inverse (or
+// its transpose) is applied by the upper sweep of LU and by the first sweep of (LU)^T.
+template <typename FT, bool UPPER, bool TRANS>
+__device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT* x, int l) {
+    constexpr bool DIAG = UPPER != TRANS;
+    const int r1 = __ldg(P.lev_ptr + l + 1);
+    for (int p = __ldg(P.lev_ptr + l) + threadIdx.x; p < r1; p += blockDim.x) {
+        const int dg = __ldg(P.lu_diag + p);
+        const int e0 = UPPER ? dg + 1 : __ldg(P.lu_ptr + p);
+        const int e1 = UPPER ? __ldg(P.lu_ptr + p + 1) : dg;
+        FT s0 = FT(0), s1 = FT(0);
+        constexpr int W = kBatch<FT>;
+        for (int e = e0; e < e1; e += W) {
+            int q[W], pos[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const bool ok = e + k < e1;
+                q[k] = ok ? __ldg(P.lu_col + e + k) : -1;
+                pos[k] = ok ? (TRANS ? __ldg(P.lu_mirror + e + k) : e + k) : 0;
             }
+            Blk<FT> m[W];
+            FT y0[W], y1[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (q[k] >= 0) {
+                    m[k] = ldb(fac, pos[k]);
+                    y0[k] = x[2 * q[k]];
+                    y1[k] = x[2 * q[k] + 1];
+                } else {
+                    m[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
+                    y0[k] = y1[k] = FT(0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (TRANS) {
+                    s0 += m[k].a * y0[k] + m[k].c * y1[k];
+                    s1 += m[k].b * y0[k] + m[k].d * y1[k];
+                } else {
+                    s0 += m[k].a * y0[k] + m[k].b * y1[k];
+                    s1 += m[k].c * y0[k] + m[k].d * y1[k];
+                }
+            }
+        }
+        const FT x0 = x[2 * p] - s0, x1 = x[2 * p + 1] - s1;
+        if (DIAG) {
+            const Blk<FT> d = ldb(fac, dg);
+            if (TRANS) {
+                x[2 * p] = d.a * x0 + d.c * x1;
+                x[2 * p + 1] = d.b * x0 + d.d * x1;
+            } else {
+                x[2 * p] = d.a * x0 + d.b * x1;
+                x[2 * p + 1] = d.c * x0 + d.d * x1;
+            }
+        } else {
             x[2 * p] = x0;
             x[2 * p + 1] = x1;
         }
+    }
+}
+
+// x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
+// then U x = y by descending levels.
+template <typename FT>
+__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x) {
+    for (int l = 0; l < P.n_levels; ++l) {
+        sweep_level<FT, false, false>(P, fac, x, l);
         gsync();
     }
     for (int l = P.n_levels - 1; l >= 0; --l) {
-        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
-            FT x0 = x[2 * p], x1 = x[2 * p + 1];
-            const int dg = P.lu_diag[p];
-            for (int e = dg + 1; e < P.lu_ptr[p + 1]; ++e) {
-                const int q = P.lu_col[e];
-                const Blk<FT> m = ldb(fac, e);
-                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
-                x0 -= m.a * y0 + m.b * y1;
-                x1 -= m.c * y0 + m.d * y1;
-            }
-            const Blk<FT> d = ldb(fac, dg);
-            x[2 * p] = d.a * x0 + d.b * x1;
-            x[2 * p + 1] = d.c * x0 + d.d * x1;
-        }
+        sweep_level<FT, true, false>(P, fac, x, l);
         gsync();
     }
 }
 
-// x <- (LU)^{-T} x: U^T y = x forward (U^T rows are mirrored L-part positions), then
-// L^T x = y backward (mirrored U-part positions).
+// x <- (LU)^{-T} x: U^T y = x by ascending levels (row p of U^T = mirrored L-part
+// positions of row p), then L^T x = y by descending levels (mirrored U-part positions).
 template <typename FT>
 __device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
     for (int l = 0; l < P.n_levels; ++l) {
-        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
-            FT x0 = x[2 * p], x1 = x[2 * p + 1];
-            for (int e = P.lu_ptr[p]; e < P.lu_diag[p]; ++e) {
-                const int q = P.lu_col[e];
-                const Blk<FT> m = ldb(fac, P.lu_mirror[e]);  // U(q, p), used transposed
-                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
-                x0 -= m.a * y0 + m.c * y1;
-                x1 -= m.b * y0 + m.d * y1;
-            }
-            const Blk<FT> d = ldb(fac, P.lu_diag[p]);     // inverse of U(p,p); use its transpose
-            x[2 * p] = d.a * x0 + d.c * x1;
-            x[2 * p + 1] = d.b * x0 + d.d * x1;
-        }
+        sweep_level<FT, false, true>(P, fac, x, l);
         gsync();
     }
     for (int l = P.n_levels - 1; l >= 0; --l) {
-        for (int p = P.lev_ptr[l] + threadIdx.x; p < P.lev_ptr[l + 1]; p += blockDim.x) {
-            FT x0 = x[2 * p], x1 = x[2 * p + 1];
-            for (int e = P.lu_diag[p] + 1; e < P.lu_ptr[p + 1]; ++e) {
-                const int q = P.lu_col[e];
-                const Blk<FT> m = ldb(fac, P.lu_mirror[e]);  // L(q, p), used transposed
-                const FT y0 = x[2 * q], y1 = x[2 * q + 1];
-                x0 -= m.a * y0 + m.c * y1;
-                x1 -= m.b * y0 + m.d * y1;
-            }
-            x[2 * p] = x0;
-            x[2 * p + 1] = x1;
-        }
+        sweep_level<FT, true, true>(P, fac, x, l);
         gsync();
     }
 }
@@ -334,15 +417,13 @@ __device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
 // Returns ||r||_inf over the true (unpadded) rows.
 __device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red) {
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int p = P.bus2pos[i];
+        const int p = __ldg(P.bus2pos + i);
         double dr = 0.0, di = 0.0;
         if (p >= 0) {
             const double dth = a.dz[2 * p];
-            const double dvm = (P.bus_type[i] == 0) ? a.dz[2 * p + 1] : 0.0;
-            const double vr = a.Vre[i], vi = a.Vim[i];
-            const double s = dvm / a.Vm[i];
-            dr = vr * s - vi * dth;
-            di = vi * s + vr * dth;
+            const double dvm = (__ldg(P.bus_type + i) == 0) ? a.dz[2 * p + 1] : 0.0;
+            dr = a.Uc[i] * dvm - a.Vim[i] * dth;  // dV = u dVm + j V dtheta
+            di = a.Us[i] * dvm + a.Vre[i] * dth;
         }
         a.dVre[i] = dr;
         a.dVim[i] = di;
@@ -350,12 +431,12 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red)
     gsync();
     double lmax = 0.0;
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int p = P.bus2pos[i];
+        const int p = __ldg(P.bus2pos + i);
         if (p < 0) continue;
         double ir = 0.0, ii = 0.0;
-        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
-            const int j = P.y_idx[k];
-            const double2 y = P.y_gb[k];
+        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
+            const int j = __ldg(P.y_idx + k);
+            const double2 y = __ldg(P.y_gb + k);
             const double vr = a.dVre[j], vi = a.dVim[j];
             ir = fma(y.x, vr, fma(-y.y, vi, ir));
             ii = fma(y.x, vi, fma(y.y, vr, ii));
@@ -366,7 +447,7 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red)
         const double dSr = dvr * Ir + dvi * Ii + vr * ir + vi * ii;
         const double dSi = dvi * Ir - dvr * Ii + vi * ir - vr * ii;
         const double rP = -a.F[2 * p] + dSr;
-        const double rQ = (P.bus_type[i] == 0) ? -a.F[2 * p + 1] + dSi : 0.0;
+        const double rQ = (__ldg(P.bus_type + i) == 0) ? -a.F[2 * p + 1] + dSi : 0.0;
         a.r[2 * p] = rP;
         a.r[2 * p + 1] = rQ;
         lmax = fmax(lmax, fmax(absinf(rP), absinf(rQ)));
@@ -375,7 +456,7 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red)
 }
 
 // ---------------------------------------------------------------- forward kernel
-template <typename FT>
+template <typename FT, bool VSM, bool FSM>
 __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
@@ -383,19 +464,22 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
     const int b = blockIdx.x;
     if (b >= A.batch) return;
     const SlotLayout& L = A.L;
+    const KernelSmem& K = L.fwd;
     unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
-    unsigned char* vbase = L.vec_in_smem ? smem : slot + L.off_vec;
-    FT* fac = L.fac_in_smem ? reinterpret_cast<FT*>(smem + L.smem_fac_off)
-                            : reinterpret_cast<FT*>(slot + L.off_fac);
+    // VSM / FSM are compile-time so that the compiler sees which pointers address
+    // shared memory (plain shared loads instead of generic ones)
+    unsigned char* vbase = VSM ? smem : slot + L.off_vec;
+    FT* fac = FSM ? reinterpret_cast<FT*>(smem + K.smem_fac_off)
+                  : reinterpret_cast<FT*>(slot + L.off_fac);
     Arrays a;
-    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), &a);
+    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), false, &a);
     FT* x = ftptr<FT>(a.x);
-    const bool mixed = sizeof(FT) == 4;
+    constexpr bool mixed = sizeof(FT) == 4;
     const size_t row = (size_t)b * P.n_bus;
 
     // flat start and specified injections (Sec. II-A, Sec. IV-A)
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = P.bus_type[i];
+        const int t = __ldg(P.bus_type + i);
         a.Vm[i] = (t == 0) ? 1.0 : A.Vset[row + i];
         a.Va[i] = 0.0;
         a.Psp[i] = ((t == 1) ? A.Pg[row + i] : 0.0) - A.Pd[row + i];
@@ -410,11 +494,11 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
     for (;;) {
         phase_voltage(P, a);
         gsync();
-        norm = phase_mismatch(P, a, red);  // ends with a group barrier
+        norm = phase_mismatch<mixed>(P, a, red);  // ends with a group barrier
         if (!(norm <= 1e10)) { status = 2; break; }
         if (norm <= A.tol) { status = 0; break; }
         if (it >= A.max_iter) { status = 1; break; }
-        phase_fill<FT>(P, a, fac);
+        phase_fill(P, a, fac);
         gsync();
         if (phase_lu<FT>(P, fac, &s_bad)) { status = 3; factored = false; break; }
         factored = true;
@@ -437,11 +521,11 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
         }
         // update (FP64)
         for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
-            const int i = P.pos2bus[p];
+            const int i = __ldg(P.pos2bus + p);
             const double dth = mixed ? a.dz[2 * p] : double(x[2 * p]);
             const double dvm = mixed ? a.dz[2 * p + 1] : double(x[2 * p + 1]);
             a.Va[i] += dth;
-            if (P.bus_type[i] == 0) a.Vm[i] += dvm;
+            if (__ldg(P.bus_type + i) == 0) a.Vm[i] += dvm;
         }
         ++it;
         gsync();
@@ -450,7 +534,7 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
     // Step 2 and outputs
     double* st = reinterpret_cast<double*>(slot + L.off_state);
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = P.bus_type[i];
+        const int t = __ldg(P.bus_type + i);
         const double vr = a.Vre[i], vi = a.Vim[i], ir = a.Ire[i], ii = a.Iim[i];
         const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
         A.Vm[row + i] = a.Vm[i];
@@ -460,7 +544,7 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
         if (A.Pg_out) A.Pg_out[row + i] = (t == 1) ? A.Pg[row + i] : (t == 2 ? Pi + A.Pd[row + i] : 0.0);
         if (A.Qg_out) A.Qg_out[row + i] = (t == 0) ? 0.0 : Qi + A.Qd[row + i];
     }
-    if (A.keep_factors && factored && L.fac_in_smem) {
+    if (A.keep_factors && factored && FSM) {
         FT* dst = reinterpret_cast<FT*>(slot + L.off_fac);
         const int nv = P.nnzb * 4;
         for (int k = threadIdx.x; k < nv; k += blockDim.x) dst[k] = fac[k];
@@ -482,7 +566,7 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
 // All Jacobian-transpose products are taken matrix-free through Ybus^T (phase_jvt);
 // the transposed solve uses the stored factor of the last Newton step and refines
 // with the FP64 residual of J1 at the solution.
-template <typename FT>
+template <typename FT, bool VSM, bool FSM>
 __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
@@ -490,12 +574,13 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     const int b = blockIdx.x;
     if (b >= A.batch) return;
     const SlotLayout& L = A.L;
+    const KernelSmem& K = L.adj;
     unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
-    unsigned char* vbase = L.vec_in_smem ? smem : slot + L.off_vec;
+    unsigned char* vbase = VSM ? smem : slot + L.off_vec;
     FT* gfac = reinterpret_cast<FT*>(slot + L.off_fac);
-    FT* fac = L.fac_in_smem ? reinterpret_cast<FT*>(smem + L.smem_fac_off) : gfac;
+    FT* fac = FSM ? reinterpret_cast<FT*>(smem + K.smem_fac_off) : gfac;
     Arrays a;
-    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), &a);
+    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), true, &a);
     FT* x = ftptr<FT>(a.x);
     const size_t row = (size_t)b * P.n_bus;
     const int* fl = reinterpret_cast<const int*>(slot + L.off_flags);
@@ -523,18 +608,19 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     gsync();
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {  // I = Y V
         double ir = 0.0, ii = 0.0;
-        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
-            const int j = P.y_idx[k];
-            const double2 y = P.y_gb[k];
+        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
+            const int j = __ldg(P.y_idx + k);
+            const double2 y = __ldg(P.y_gb + k);
             ir = fma(y.x, a.Vre[j], fma(-y.y, a.Vim[j], ir));
             ii = fma(y.x, a.Vim[j], fma(y.y, a.Vre[j], ii));
         }
         a.Ire[i] = ir;
         a.Iim[i] = ii;
+        store_bus_f32(a, i, ir, ii);
     }
     // Step-2 weights: c_P on R (dL/dpg_R), c_Q on B\D (dL/dqg)
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = P.bus_type[i];
+        const int t = __ldg(P.bus_type + i);
         a.Psp[i] = (t == 2 && A.dPg) ? A.dPg[row + i] : 0.0;
         a.Qsp[i] = (t != 0 && A.dQg) ? A.dQg[row + i] : 0.0;
     }
@@ -546,10 +632,10 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         const double gvm = A.dVm[row + i] + a.w0[i];
         const double gva = A.dVa[row + i] + a.w1[i];
         a.gV[i] = gvm;
-        const int p = P.bus2pos[i];
+        const int p = __ldg(P.bus2pos + i);
         if (p >= 0) {
             a.F[2 * p] = gva;                                   // theta component of g_z1
-            a.F[2 * p + 1] = (P.bus_type[i] == 0) ? gvm : 0.0;  // Vm component (PQ only)
+            a.F[2 * p + 1] = (__ldg(P.bus_type + i) == 0) ? gvm : 0.0;  // Vm component (PQ only)
             lg = fmax(lg, fmax(absinf(gva), absinf(a.F[2 * p + 1])));
         }
     }
@@ -557,7 +643,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
 
     // stage the stored factor
     bool have = has_factor != 0;
-    if (have && L.fac_in_smem) {
+    if (have && FSM) {
         const int nv = P.nnzb * 4;
         for (int k = threadIdx.x; k < nv; k += blockDim.x) fac[k] = gfac[k];
         gsync();
@@ -566,7 +652,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     bool refactored = false;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (!have) {
-            phase_fill<FT>(P, a, fac);
+            phase_fill(P, a, fac);
             gsync();
             if (phase_lu<FT>(P, fac, &s_bad)) { astat = 3; break; }
             have = true;
@@ -581,18 +667,18 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         for (int s = 0;; ++s) {
             // m1 = lambda on the F1 rows; r = g_z1 - J1^T lambda = g_z1 + (Jv^T m1)[z1]
             for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-                const int p = P.bus2pos[i];
+                const int p = __ldg(P.bus2pos + i);
                 a.Psp[i] = (p >= 0) ? a.dz[2 * p] : 0.0;
-                a.Qsp[i] = (p >= 0 && P.bus_type[i] == 0) ? a.dz[2 * p + 1] : 0.0;
+                a.Qsp[i] = (p >= 0 && __ldg(P.bus_type + i) == 0) ? a.dz[2 * p + 1] : 0.0;
             }
             gsync();
             phase_jvt(P, a);
             gsync();
             double lr = 0.0;
             for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
-                const int i = P.pos2bus[p];
+                const int i = __ldg(P.pos2bus + p);
                 const double r0 = a.F[2 * p] + a.w1[i];
-                const double r1 = (P.bus_type[i] == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
+                const double r1 = (__ldg(P.bus_type + i) == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
                 a.r[2 * p] = r0;
                 a.r[2 * p + 1] = r1;
                 lr = fmax(lr, fmax(absinf(r0), absinf(r1)));
@@ -612,8 +698,8 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     }
     // gradients; w0 holds (Jv^T m1)_Vm for the final lambda
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = P.bus_type[i];
-        const int p = P.bus2pos[i];
+        const int t = __ldg(P.bus_type + i);
+        const int p = __ldg(P.bus2pos + i);
         const double lP = (p >= 0) ? a.dz[2 * p] : 0.0;
         const double lQ = (p >= 0 && t == 0) ? a.dz[2 * p + 1] : 0.0;
         const double cP = A.dPg ? A.dPg[row + i] : 0.0;
@@ -627,24 +713,32 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename FT>
-cudaError_t launch_solve(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s) {
-    auto k = nr_solve_kernel<FT>;
+template <typename KernelT, typename ArgT>
+cudaError_t launch_one(KernelT k, const DevPlan& P, const ArgT& A, const KernelSmem& K,
+                       int threads, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)A.L.smem_bytes);
+                                         (int)K.smem_bytes);
     if (e != cudaSuccess) return e;
-    k<<<A.batch, threads, A.L.smem_bytes, s>>>(P, A);
+    k<<<A.batch, threads, K.smem_bytes, s>>>(P, A);
     return cudaGetLastError();
 }
 
 template <typename FT>
+cudaError_t launch_solve(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s) {
+    const KernelSmem& K = A.L.fwd;
+    if (K.vec_in_smem && K.fac_in_smem)
+        return launch_one(nr_solve_kernel<FT, true, true>, P, A, K, threads, s);
+    if (K.vec_in_smem) return launch_one(nr_solve_kernel<FT, true, false>, P, A, K, threads, s);
+    return launch_one(nr_solve_kernel<FT, false, false>, P, A, K, threads, s);
+}
+
+template <typename FT>
 cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s) {
-    auto k = adjoint_kernel<FT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)A.L.smem_bytes);
-    if (e != cudaSuccess) return e;
-    k<<<A.batch, threads, A.L.smem_bytes, s>>>(P, A);
-    return cudaGetLastError();
+    const KernelSmem& K = A.L.adj;
+    if (K.vec_in_smem && K.fac_in_smem)
+        return launch_one(adjoint_kernel<FT, true, true>, P, A, K, threads, s);
+    if (K.vec_in_smem) return launch_one(adjoint_kernel<FT, true, false>, P, A, K, threads, s);
+    return launch_one(adjoint_kernel<FT, false, false>, P, A, K, threads, s);
 }
 
 template cudaError_t launch_solve<float>(const DevPlan&, const SolveArgs&, int, cudaStream_t);

@@ -296,6 +296,29 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         P.schur_ops += (long long)contrib.size();
     }
 
+    // lanes per gathered row: the smallest power of two covering the level's longest
+    // gather, capped at one warp
+    auto lanes = [](int len) {
+        int g = 1;
+        while (g < len && g < 32) g <<= 1;
+        return g;
+    };
+    P.lev_gL.assign(n_levels, 1);
+    P.lev_gU.assign(n_levels, 1);
+    P.lev_gS.assign(n_levels, 1);
+    for (int l = 0; l < n_levels; ++l) {
+        int mL = 0, mU = 0, mS = 0;
+        for (int p = P.lev_ptr[l]; p < P.lev_ptr[l + 1]; ++p) {
+            mL = std::max(mL, P.lu_diag[p] - P.lu_ptr[p]);
+            mU = std::max(mU, P.lu_ptr[p + 1] - P.lu_diag[p] - 1);
+        }
+        for (int t = P.sch_tptr[l]; t < P.sch_tptr[l + 1]; ++t)
+            mS = std::max(mS, P.sch_cptr[t + 1] - P.sch_cptr[t]);
+        P.lev_gL[l] = lanes(mL);
+        P.lev_gU[l] = lanes(mU);
+        P.lev_gS[l] = lanes(mS);
+    }
+
     // scalar nonzeros of J1 (rows dP_{B\R}, dQ_D; columns theta_{B\R}, Vm_D)
     long long nnz = 0;
     for (int i = 0; i < n_bus; ++i) {

@@ -35,6 +35,9 @@ struct Plan {
     // the pivot range [lev_ptr[l], lev_ptr[l+1])
     int n_levels = 0;
     std::vector<int> lev_ptr;
+    // lanes per gathered row (a power of two <= 32) for each level: forward (L part),
+    // backward (U part) and Schur-target gathers
+    std::vector<int> lev_gL, lev_gU, lev_gS;
 
     // block CSR of the filled L+U pattern in position order
     std::vector<int> lu_ptr, lu_col, lu_row, lu_diag, lu_mirror;

@@ -49,7 +49,7 @@ def regular(o):
     Newton iterates of the two implementations differ only by rounding, which the
     iteration damps inside the quadratic basin and amplifies elsewhere.  A scenario
     is regular if it converges with ||F1|| decreasing monotonically after the first
-    three iterates, diverges within the first six, or is non-finite from the start.
+    three iterates, or diverges within two Newton steps (or is non-finite from the start).
     Elsewhere -- scenarios that wander for many iterations without a solution -- the
     MAXITER / DIVERGED split (and a late convergence) depends on rounding.
     """
@@ -60,7 +60,7 @@ def regular(o):
         tail = h[2:]
         return all(b < a for a, b in zip(tail, tail[1:]))
     if o["status"] == O.DIVERGED:
-        return o["iters"] <= 6
+        return o["iters"] <= 2
     return False
 
 
