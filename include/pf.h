@@ -192,6 +192,31 @@ pf_err pf_adjoint(pf_handle* h, int batch,
                   double* dPd, double* dQd, double* dPg_in, double* dVset, int* adj_status,
                   void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * pf_solve_noalloc -- pf_solve for callers that cannot allocate device memory.
+ * The paper has no counterpart: this entry point exists for callers that may not
+ * call cudaMalloc (code running while another part of the process captures a CUDA
+ * graph, plug-ins whose host application owns the device allocator, real-time
+ * loops with a memory budget fixed at start-up).  It takes the same arguments as
+ * pf_solve minus the workspace: the per-scenario scratch lives in a static device
+ * array of PF_NOALLOC_SCRATCH_BYTES that the library holds on every device it is
+ * loaded on until the process exits.  No allocation of any kind happens inside.
+ *   - The first call on a device looks up that array's address (once per device);
+ *     make that first call before any stream capture that it should join.
+ *   - All calls share the array: calls whose kernels overlap on the GPU race and
+ *     corrupt each other; order them on one stream.  Nothing in it needs clearing.
+ *   - keep_factors must be 0 (pf_adjoint needs a caller-owned workspace).
+ * Errors: PF_EINVAL when keep_factors is set or when the batch needs more scratch
+ * than PF_NOALLOC_SCRATCH_BYTES (pf_workspace_size tells the need), plus every
+ * error of pf_solve.
+ */
+#define PF_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+pf_err pf_solve_noalloc(pf_handle* h, int batch,
+                        const double* Pd, const double* Qd, const double* Pg, const double* Vset,
+                        double tol, int max_iter, const pf_solve_opts* opts,
+                        double* Vm, double* Va, double* Pg_out, double* Qg_out,
+                        int* iters, int* status, double* final_mismatch, void* stream);
+
 /* pf_destroy -- frees the handle's host and device memory (waits for the device). */
 void pf_destroy(pf_handle* h);
 

@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(_HERE, "libpf.so")
 PF_OK, PF_EINVAL, PF_ESINGULAR_PATTERN, PF_ENOMEM, PF_ECUDA, PF_ESTATE, PF_ENOTSUP = range(7)
 PF_CONVERGED, PF_MAXITER, PF_DIVERGED, PF_SINGULAR = range(4)
 PF_FP64, PF_MIXED = 0, 1
+PF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 # every function and its (restype, argtypes); the CPU tests check this list against pf.h
 _p = C.c_void_p
@@ -41,6 +42,8 @@ SIGNATURES = {
     "pf_solve": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
                       _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "pf_adjoint": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_solve_noalloc": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
+                              _p, _p, _p, _p, _p, _p, _p, _p]),
     "pf_destroy": (None, [_p]),
     "pf_error_string": (C.c_char_p, [_i]),
 }

@@ -2,7 +2,7 @@
 
     python -m paper_2606_07099_gb300.build
 
-The three translation units compile in parallel; the library links the CUDA
+The translation units compile in parallel; the library links the CUDA
 runtime statically so that it needs nothing but the driver at run time.
 """
 from __future__ import annotations
@@ -54,6 +54,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     cxx_flags = ["-O2", "-std=c++17", "-fPIC", "-I", os.path.join(_cuda_home(), "include")] + inc
     jobs = [
         [nvcc, "-c", os.path.join(CSRC, "pf_kernels.cu"), "-o", os.path.join(BUILD, "pf_kernels.o")] + cu_flags,
+        [nvcc, "-c", os.path.join(CSRC, "pf_noalloc.cu"), "-o", os.path.join(BUILD, "pf_noalloc.o")] + cu_flags,
         [cxx, "-c", os.path.join(CSRC, "pf_api.cpp"), "-o", os.path.join(BUILD, "pf_api.o")] + cxx_flags,
         [cxx, "-c", os.path.join(CSRC, "pf_plan.cpp"), "-o", os.path.join(BUILD, "pf_plan.o")] + cxx_flags,
     ]
@@ -61,6 +62,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         outs = list(ex.map(_run, jobs))
     tmp = LIB + ".tmp"
     _run([nvcc, "-shared"] + ARCH + ["-o", tmp, os.path.join(BUILD, "pf_kernels.o"),
+                                     os.path.join(BUILD, "pf_noalloc.o"),
                                      os.path.join(BUILD, "pf_api.o"), os.path.join(BUILD, "pf_plan.o"),
                                      "-cudart", "static", "-lpthread", "-ldl", "-lrt"])
     os.replace(tmp, LIB)

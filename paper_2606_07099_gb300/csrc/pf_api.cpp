@@ -125,6 +125,10 @@ size_t push(std::vector<unsigned char>& buf, const std::vector<T>& v) {
 
 }  // namespace
 
+namespace pf {
+int handle_device(const pf_handle* h) { return h->device; }
+}  // namespace pf
+
 extern "C" {
 
 const char* pf_error_string(pf_err e) {
