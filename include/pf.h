@@ -92,7 +92,28 @@ typedef struct {
     int group_threads; /* threads per scenario (32..1024, multiple of 32; 0 = auto) */
     int keep_factors;  /* nonzero: store each scenario's last LU factor in the workspace
                           so that pf_adjoint can reuse it (required before pf_adjoint) */
+    int placement;     /* pf_placement: where a scenario's vectors and factor live while
+                          it is solved (0 = auto: the autotuned choice, else a heuristic) */
+    int instances_per_cta; /* 0 = auto; 1 = one scenario per CTA of group_threads threads;
+                          2..8 = that many scenarios per CTA, one warp each (group_threads
+                          must then be 0 or 32) */
 } pf_solve_opts;
+
+typedef enum {
+    PF_PLACE_AUTO = 0,
+    PF_PLACE_ONCHIP = 1,   /* vectors and factor in shared memory (if they fit) */
+    PF_PLACE_VECTORS = 2,  /* vectors in shared memory, factor in the global workspace */
+    PF_PLACE_GLOBAL = 3,   /* everything in the global workspace (most scenarios per SM) */
+    PF_PLACE_FACTOR = 4    /* factor in shared memory, vectors in the global workspace */
+} pf_placement;
+
+/* Result of pf_autotune: the fastest launch configuration found for one precision. */
+typedef struct {
+    int group_threads;
+    int placement;
+    int instances_per_cta;
+    float ms;              /* measured time of one pf_solve with that configuration */
+} pf_tune_result;
 
 /*
  * pf_build_ybus -- host helper: Ybus of pi-model branches (Sec. II-A's Ybus).
@@ -143,9 +164,10 @@ pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info);
 
 /*
  * pf_workspace_size -- device bytes pf_solve / pf_adjoint need for `batch`
- * scenarios with these options.  The caller allocates the workspace (any device
- * allocator, 256-byte alignment) and passes the same buffer to pf_adjoint after
- * pf_solve.  Errors: PF_EINVAL.
+ * scenarios with these options (placement PF_PLACE_AUTO: the placement pf_solve would
+ * pick now; PF_PLACE_GLOBAL needs the most and serves every placement).  The caller
+ * allocates the workspace (any device allocator, 256-byte alignment) and passes the
+ * same buffer to pf_adjoint after pf_solve.  Errors: PF_EINVAL.
  */
 pf_err pf_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts,
                          size_t* bytes);
@@ -170,6 +192,24 @@ pf_err pf_solve(pf_handle* h, int batch,
                 double* Vm, double* Va, double* Pg_out, double* Qg_out,
                 int* iters, int* status, double* final_mismatch,
                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * pf_autotune -- picks the launch configuration (threads per scenario and placement
+ * of the scenario data) for this handle, `batch` and opts->precision by timing
+ * pf_solve on the given inputs (device, as pf_solve) for every candidate: 32..512
+ * threads per scenario, or 2, 4 or 8 one-warp scenarios per CTA, times every placement
+ * that fits.  The fastest one is kept in
+ * the handle and used by later pf_solve calls with group_threads = 0 and placement =
+ * PF_PLACE_AUTO at the same precision; *out (nullable) receives it.  The workspace
+ * must hold pf_workspace_size for PF_PLACE_GLOBAL; the call allocates small temporary
+ * output buffers of its own.  Not the hot path: it launches every
+ * candidate several times and waits for the device (stream-synchronous).
+ * Errors: as pf_solve.
+ */
+pf_err pf_autotune(pf_handle* h, int batch,
+                   const double* Pd, const double* Qd, const double* Pg, const double* Vset,
+                   double tol, int max_iter, const pf_solve_opts* opts,
+                   void* workspace, size_t workspace_bytes, void* stream, pf_tune_result* out);
 
 /*
  * pf_adjoint -- implicit-differentiation backward pass of Sec. II-B.2 at the

@@ -30,7 +30,16 @@ class PlanInfo(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("ir_steps", C.c_int), ("ir_rtol", C.c_double),
-                ("group_threads", C.c_int), ("keep_factors", C.c_int)]
+                ("group_threads", C.c_int), ("keep_factors", C.c_int), ("placement", C.c_int),
+                ("instances_per_cta", C.c_int)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("group_threads", C.c_int), ("placement", C.c_int),
+                ("instances_per_cta", C.c_int), ("ms", C.c_float)]
+
+
+PF_PLACE_AUTO, PF_PLACE_ONCHIP, PF_PLACE_VECTORS, PF_PLACE_GLOBAL, PF_PLACE_FACTOR = range(5)
 
 
 SIGNATURES = {
@@ -41,6 +50,8 @@ SIGNATURES = {
     "pf_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
     "pf_solve": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
                       _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_autotune": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts), _p, _sz, _p,
+                         C.POINTER(TuneResult)]),
     "pf_adjoint": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "pf_solve_noalloc": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
                               _p, _p, _p, _p, _p, _p, _p, _p]),

@@ -23,6 +23,8 @@ struct pf_handle {
     int num_sms = 0;
     void* d_buf = nullptr;
     pf::DevPlan dp{};
+    // autotuned launch configuration per precision (index 0 = FP64, 1 = mixed)
+    pf_tune_result tuned[2] = {{0, 0, 0, 0.f}, {0, 0, 0, 0.f}};
     // state of the last pf_solve (for pf_adjoint)
     int last_batch = -1;
     int last_ft = 0;
@@ -59,31 +61,73 @@ int auto_threads(int n) {
 // Shared memory reserved for the kernels' static arrays and the runtime.
 constexpr size_t kStaticSmemReserve = 1024;
 
-// Shared-memory placement of one kernel: vectors and factor in shared memory if both
-// fit, else the vectors only, else neither (everything streams from the global slot).
-pf::KernelSmem place(size_t vec_bytes, size_t fac_bytes, size_t budget) {
+// Shared-memory placement of one kernel (pf_placement): vectors and factor in shared
+// memory, vectors only, or neither (everything streams from the global slot).  A
+// placement that does not fit falls back to the next one down.
+// The triangular-solve vector is the only vector every level of a sweep reads right
+// after an earlier level wrote it; when the vectors live in the global workspace it
+// still goes to shared memory if it is small (<= 8 KB).
+constexpr size_t kXSmemMax = 8 * 1024;
+
+void add_x(pf::KernelSmem& k, size_t x_bytes, size_t budget) {
+    if (k.vec_in_smem || x_bytes > kXSmemMax || k.smem_bytes + x_bytes > budget) return;
+    k.x_in_smem = 1;
+    k.smem_x_off = k.smem_bytes;
+    k.smem_bytes += pf::align_up(x_bytes, 16);
+}
+
+pf::KernelSmem place(size_t vec_bytes, size_t fac_bytes, size_t budget, int placement,
+                     size_t x_bytes = kXSmemMax + 1) {
     pf::KernelSmem k{};
     k.vec_bytes = vec_bytes;
-    if (vec_bytes + fac_bytes <= budget) {
+    if (placement == PF_PLACE_FACTOR) {
+        if (fac_bytes <= budget) {
+            k.fac_in_smem = 1;
+            k.smem_fac_off = 0;
+            k.smem_bytes = fac_bytes;
+        }
+        add_x(k, x_bytes, budget);
+        return k;
+    }
+    if (placement <= PF_PLACE_ONCHIP && vec_bytes + fac_bytes <= budget) {
         k.vec_in_smem = 1;
         k.fac_in_smem = 1;
         k.smem_fac_off = vec_bytes;
         k.smem_bytes = vec_bytes + fac_bytes;
-    } else if (vec_bytes <= budget) {
+    } else if (placement <= PF_PLACE_VECTORS && vec_bytes <= budget) {
         k.vec_in_smem = 1;
         k.smem_bytes = vec_bytes;
     }
+    add_x(k, x_bytes, budget);
     return k;
 }
 
-pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep) {
+size_t smem_budget(const pf_handle* h) {
+    return (size_t)h->smem_optin > kStaticSmemReserve ? (size_t)h->smem_optin - kStaticSmemReserve : 0;
+}
+
+// Default placement without tuning data: keep a scenario on chip only while at least
+// three of them fit on one SM (76 KB each); past that, more scenarios in flight from
+// the global workspace beat fewer scenarios in shared memory.
+int heuristic_placement(const pf_handle* h, int ft_bytes) {
+    const pf::Plan& P = h->plan;
+    const size_t vec = pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr);
+    const size_t fac = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
+    const size_t lim = std::min<size_t>(smem_budget(h), 76 * 1024);
+    if (vec + fac <= lim) return PF_PLACE_ONCHIP;
+    if (vec <= lim) return PF_PLACE_VECTORS;
+    return PF_PLACE_GLOBAL;
+}
+
+pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int placement) {
     const pf::Plan& P = h->plan;
     pf::SlotLayout L{};
     L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
-    const size_t budget = (size_t)h->smem_optin > kStaticSmemReserve
-                              ? (size_t)h->smem_optin - kStaticSmemReserve : 0;
-    L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes, budget);
-    L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes, budget);
+    const size_t budget = smem_budget(h);
+    L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes, budget,
+                  placement, (size_t)ft_bytes * 2 * (size_t)P.n);
+    L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes, budget,
+                  placement);
     L.fac_global = (!L.fwd.fac_in_smem || keep) ? 1 : 0;
     size_t vec_global = 0;
     if (!L.fwd.vec_in_smem) vec_global = std::max(vec_global, L.fwd.vec_bytes);
@@ -105,6 +149,27 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep) {
     return L;
 }
 
+struct LaunchCfg {
+    int threads;
+    int placement;
+    int ipc;
+};
+
+LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o) {
+    const int ft = o->precision == PF_MIXED ? 4 : 8;
+    const pf_tune_result& t = h->tuned[o->precision == PF_MIXED ? 1 : 0];
+    const bool use_tuned = o->group_threads == 0 && o->instances_per_cta == 0 && t.group_threads;
+    LaunchCfg c;
+    c.threads = o->group_threads ? o->group_threads
+                                 : (use_tuned ? t.group_threads : auto_threads(h->plan.n));
+    c.ipc = o->instances_per_cta ? o->instances_per_cta
+                                 : (use_tuned ? t.instances_per_cta : 1);
+    if (c.ipc > 1) c.threads = 32;
+    c.placement = o->placement ? o->placement
+                               : (t.placement ? t.placement : heuristic_placement(h, ft));
+    return c;
+}
+
 bool opts_ok(const pf_solve_opts* o) {
     if (!o) return false;
     if (o->precision != PF_FP64 && o->precision != PF_MIXED) return false;
@@ -112,6 +177,9 @@ bool opts_ok(const pf_solve_opts* o) {
     if (!(o->ir_rtol >= 0.0)) return false;
     if (o->group_threads != 0 &&
         (o->group_threads < 32 || o->group_threads > 1024 || o->group_threads % 32)) return false;
+    if (o->placement < PF_PLACE_AUTO || o->placement > PF_PLACE_FACTOR) return false;
+    if (o->instances_per_cta < 0 || o->instances_per_cta > 8) return false;
+    if (o->instances_per_cta > 1 && o->group_threads != 0 && o->group_threads != 32) return false;
     return true;
 }
 
@@ -316,8 +384,8 @@ pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices, const do
 pf_err pf_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts, size_t* bytes) {
     if (!h || !bytes || batch < 1 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors);
-    *bytes = L.slot_bytes * (size_t)batch;
+    const size_t slot = make_layout(h, ft, opts->keep_factors, resolve(h, opts).placement).slot_bytes;
+    *bytes = slot * (size_t)batch;
     return PF_OK;
 }
 
@@ -329,13 +397,16 @@ pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, con
         return PF_EINVAL;
     if (!(tol > 0.0) || max_iter < 0 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors);
+    const LaunchCfg cfg = resolve(h, opts);
+    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, cfg.placement);
     if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
     if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
-    const int threads = opts->group_threads ? opts->group_threads : auto_threads(h->plan.n);
+    const int threads = cfg.threads;
+    if (cfg.ipc > 1 && L.fwd.smem_bytes * (size_t)cfg.ipc > smem_budget(h)) return PF_EINVAL;
     DeviceGuard guard(h->device);
     pf::SolveArgs A{};
     A.batch = batch;
+    A.ipc = cfg.ipc;
     A.tol = tol;
     A.max_iter = max_iter;
     A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
@@ -398,6 +469,76 @@ pf_err pf_adjoint(pf_handle* h, int batch, const double* dVm, const double* dVa,
     cudaError_t e = h->last_ft == 4 ? pf::launch_adjoint<float>(h->dp, A, h->last_threads, s)
                                     : pf::launch_adjoint<double>(h->dp, A, h->last_threads, s);
     return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
+                   const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
+                   void* workspace, size_t workspace_bytes, void* stream, pf_tune_result* out) {
+    if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !workspace || !opts_ok(opts)) return PF_EINVAL;
+    {
+        pf_solve_opts g = *opts;
+        g.placement = PF_PLACE_GLOBAL;  // the largest slot of all placements
+        size_t need = 0;
+        if (pf_workspace_size(h, batch, &g, &need) != PF_OK || workspace_bytes < need) return PF_EINVAL;
+    }
+    DeviceGuard guard(h->device);
+    const int nb = h->plan.n_bus;
+    // temporary outputs of the trial solves
+    double* dbuf = nullptr;
+    int* ibuf = nullptr;
+    const size_t nd = (size_t)batch * nb;
+    if (cudaMalloc(&dbuf, sizeof(double) * (2 * nd + (size_t)batch)) != cudaSuccess) return PF_ENOMEM;
+    if (cudaMalloc(&ibuf, sizeof(int) * 2 * (size_t)batch) != cudaSuccess) {
+        cudaFree(dbuf);
+        return PF_ENOMEM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    pf_tune_result best{0, 0, 0, 0.f};
+    pf_err err = PF_OK;
+    // (threads per scenario, scenarios per CTA)
+    const int cands[][2] = {{32, 1}, {64, 1}, {128, 1}, {256, 1}, {512, 1}, {32, 2}, {32, 4}, {32, 8}};
+    for (int pl = PF_PLACE_ONCHIP; pl <= PF_PLACE_FACTOR && err == PF_OK; ++pl) {
+        // skip placements that fall back to another one (they would time a duplicate)
+        const int ft = opts->precision == PF_MIXED ? 4 : 8;
+        const pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, pl);
+        const int eff = (L.fwd.fac_in_smem && L.fwd.vec_in_smem) ? PF_PLACE_ONCHIP
+                        : L.fwd.vec_in_smem ? PF_PLACE_VECTORS
+                        : L.fwd.fac_in_smem ? PF_PLACE_FACTOR : PF_PLACE_GLOBAL;
+        if (eff != pl) continue;
+        for (const auto& cand : cands) {
+            const int th = cand[0], ipc = cand[1];
+            if (ipc > 1 && L.fwd.smem_bytes * (size_t)ipc > smem_budget(h)) continue;
+            pf_solve_opts o = *opts;
+            o.group_threads = th;
+            o.instances_per_cta = ipc;
+            o.placement = pl;
+            float ms_best = 0.f;
+            for (int rep = 0; rep < 3 && err == PF_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                err = pf_solve(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, &o, dbuf, dbuf + nd,
+                               nullptr, nullptr, ibuf, ibuf + batch, dbuf + 2 * nd, workspace,
+                               workspace_bytes, stream);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) err = PF_ECUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && (ms_best == 0.f || ms < ms_best)) ms_best = ms;  // rep 0 warms up
+            }
+            if (err == PF_OK && (best.group_threads == 0 || ms_best < best.ms)) best = {th, pl, ipc, ms_best};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dbuf);
+    cudaFree(ibuf);
+    h->last_batch = -1;  // the trial solves invalidate the adjoint state
+    if (err != PF_OK) return err;
+    h->tuned[opts->precision == PF_MIXED ? 1 : 0] = best;
+    if (out) *out = best;
+    return PF_OK;
 }
 
 void pf_destroy(pf_handle* h) {

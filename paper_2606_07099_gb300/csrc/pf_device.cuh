@@ -41,6 +41,8 @@ struct KernelSmem {
     int fac_in_smem;      // factor staged in shared memory
     size_t smem_bytes;    // dynamic shared memory per CTA
     size_t smem_fac_off;  // factor offset inside the dynamic shared memory
+    int x_in_smem;        // the solve vector in shared memory although the vectors are not
+    size_t smem_x_off;    // its offset inside the dynamic shared memory
     size_t vec_bytes;     // size of this kernel's vector arena
 };
 
@@ -58,6 +60,7 @@ struct SlotLayout {
 
 struct SolveArgs {
     int batch;
+    int ipc;         // scenarios per CTA: 1 = the whole CTA per scenario, >1 = one warp each
     double tol;
     int max_iter;
     int ir_steps;
@@ -99,10 +102,11 @@ struct AdjArgs {
 // Vector arena carved from one base pointer (shared or global memory).
 struct Arrays {
     // FP64, one entry per bus; (Uc, Us) = (cos theta, sin theta) is the unit phasor u
-    double *Vm, *Va, *Psp, *Qsp, *Uc, *Us, *Vre, *Vim, *Ire, *Iim, *dVre, *dVim;
-    double *w0, *w1, *gV;  // adjoint only (null in the forward layout)
+    double *Vm, *Va, *Uc, *Us, *Vre, *Vim, *Ire, *Iim, *dVre, *dVim;
+    double *Psp, *Qsp, *w0, *w1, *gV;  // adjoint only (null in the forward layout)
     // FP64, two entries per pivot block
-    double *F, *dz, *r;
+    double *F, *dz;
+    double* r;                          // adjoint only
     // FP32 copies per bus feeding the FP32 Jacobian fill: V, u, Vm and u conj(I)
     float *fvr, *fvi, *fur, *fui, *fvm, *fpu, *fqu;
     void* x;  // FT[2n], the triangular-solve vector
@@ -110,37 +114,45 @@ struct Arrays {
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Arena layout shared by host (sizing) and device (carving).
+// Arena layout shared by host (sizing) and device (carving).  In the forward layout the
+// refinement's dV (FP64, two per bus) shares its bytes with the first four FP32 fill
+// copies: the copies are written by the mismatch and read by the fill, dV is written and
+// read by the refinement residual, later in the same Newton iteration.
 __host__ __device__ inline size_t carve(unsigned char* base, int n_bus, int n, int ft_bytes,
                                         bool adjoint, Arrays* out) {
     size_t o = 0;
-    auto d_bus = [&](double** dst) {
-        if (out) *dst = reinterpret_cast<double*>(base + o);
-        o = align_up(o + sizeof(double) * (size_t)n_bus, 16);
+    auto take = [&](size_t bytes) {
+        unsigned char* p = base + o;
+        o = align_up(o + bytes, 16);
+        return p;
     };
-    auto d_pos = [&](double** dst) {
-        if (out) *dst = reinterpret_cast<double*>(base + o);
-        o = align_up(o + sizeof(double) * 2 * (size_t)n, 16);
-    };
-    auto f_bus = [&](float** dst) {
-        if (out) *dst = reinterpret_cast<float*>(base + o);
-        o = align_up(o + sizeof(float) * (size_t)n_bus, 16);
-    };
+    const size_t db = sizeof(double) * (size_t)n_bus, fb = sizeof(float) * (size_t)n_bus;
+    const size_t pb = sizeof(double) * 2 * (size_t)n;
     Arrays dummy;
     Arrays* a = out ? out : &dummy;
-    d_bus(&a->Vm); d_bus(&a->Va); d_bus(&a->Psp); d_bus(&a->Qsp); d_bus(&a->Uc); d_bus(&a->Us);
-    d_bus(&a->Vre); d_bus(&a->Vim); d_bus(&a->Ire); d_bus(&a->Iim); d_bus(&a->dVre);
-    d_bus(&a->dVim);
+    double** bus_fwd[8] = {&a->Vm, &a->Va, &a->Uc, &a->Us, &a->Vre, &a->Vim, &a->Ire, &a->Iim};
+    for (double** d : bus_fwd) *d = reinterpret_cast<double*>(take(db));
+    a->F = reinterpret_cast<double*>(take(pb));
+    a->dz = reinterpret_cast<double*>(take(pb));
     if (adjoint) {
-        d_bus(&a->w0); d_bus(&a->w1); d_bus(&a->gV);
-    } else if (out) {
-        out->w0 = out->w1 = out->gV = nullptr;
+        double** bus_adj[7] = {&a->dVre, &a->dVim, &a->Psp, &a->Qsp, &a->w0, &a->w1, &a->gV};
+        for (double** d : bus_adj) *d = reinterpret_cast<double*>(take(db));
+        a->r = reinterpret_cast<double*>(take(pb));
+        float** f32[7] = {&a->fvr, &a->fvi, &a->fur, &a->fui, &a->fvm, &a->fpu, &a->fqu};
+        for (float** f : f32) *f = reinterpret_cast<float*>(take(fb));
+    } else {
+        unsigned char* shared = take(2 * db);  // dV (2 x FP64) == fvr, fvi, fur, fui (4 x FP32)
+        a->dVre = reinterpret_cast<double*>(shared);
+        a->dVim = reinterpret_cast<double*>(shared + db);
+        a->fvr = reinterpret_cast<float*>(shared);
+        a->fvi = reinterpret_cast<float*>(shared + fb);
+        a->fur = reinterpret_cast<float*>(shared + 2 * fb);
+        a->fui = reinterpret_cast<float*>(shared + 3 * fb);
+        float** f32[3] = {&a->fvm, &a->fpu, &a->fqu};
+        for (float** f : f32) *f = reinterpret_cast<float*>(take(fb));
+        a->Psp = a->Qsp = a->w0 = a->w1 = a->gV = a->r = nullptr;
     }
-    d_pos(&a->F); d_pos(&a->dz); d_pos(&a->r);
-    f_bus(&a->fvr); f_bus(&a->fvi); f_bus(&a->fur); f_bus(&a->fui); f_bus(&a->fvm);
-    f_bus(&a->fpu); f_bus(&a->fqu);
-    if (out) out->x = base + o;
-    o = align_up(o + (size_t)ft_bytes * 2 * n, 16);
+    a->x = take((size_t)ft_bytes * 2 * n);
     return o;
 }
 

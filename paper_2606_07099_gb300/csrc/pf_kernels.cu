@@ -10,13 +10,16 @@
 //   factor    level-scheduled right-looking 2x2-block LU      (FT = float | double)
 //   solve     level-scheduled block triangular sweeps         (FT)
 //   refine    FP64 residual r = -F1 - J1 dz (matrix-free)     (Table I + refinement)
-//   update    theta_{B\R} += dtheta, Vm_D += dVm              (FP64)
+//   update    theta_{B\R} += dtheta, Vm_D += dVm, u and V     (FP64)
 //
 // until ||F1||_inf <= tol; then Step 2 (Eq. F2_completion) writes the recovered
 // generation.  The convergence decision is taken on the device per scenario;
 // the host never waits inside the loop.
 #include <cfloat>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "pf_device.cuh"
 
@@ -69,8 +72,15 @@ __device__ __forceinline__ Blk<T> inv2(Blk<T> m, int* bad) {
 template <typename T>
 __device__ __forceinline__ T* ftptr(void* p) { return reinterpret_cast<T*>(p); }
 
+// A "group" solves one scenario: either the whole CTA (W = false) or one warp of it
+// (W = true: several independent scenarios per CTA, one per warp).  GTID / GSZ are the
+// thread's rank and the size of its group; gsync<W> is the group barrier.
+#define GTID (W ? (int)(threadIdx.x & 31u) : (int)threadIdx.x)
+#define GSZ (W ? 32 : (int)blockDim.x)
+
+template <bool W>
 __device__ __forceinline__ void gsync() {
-    if (blockDim.x == 32) __syncwarp();
+    if (W || blockDim.x == 32) __syncwarp();
     else __syncthreads();
 }
 
@@ -81,9 +91,10 @@ __device__ __forceinline__ double absinf(double v) {
 }
 
 // Group-wide max; every thread gets the result.  `red` holds one double per warp.
+template <bool W>
 __device__ double group_max(double v, double* red) {
     for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (blockDim.x == 32) {
+    if (W || blockDim.x == 32) {
         __syncwarp();  // also orders the shared-memory writes of the phase that reduced
         return v;
     }
@@ -98,8 +109,9 @@ __device__ double group_max(double v, double* red) {
 
 // ---------------------------------------------------------------- FP64 network kernels
 // u = e^{j theta}, V = Vm u
+template <bool W>
 __device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {
         double s, c;
         sincos(a.Va[i], &s, &c);
         a.Uc[i] = c;
@@ -107,6 +119,42 @@ __device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
         a.Vre[i] = a.Vm[i] * c;
         a.Vim[i] = a.Vm[i] * s;
     }
+}
+
+// e^{j d} for a Newton angle step |d| <= 1/8 from the Maclaurin series of sin and cos,
+// truncated after d^9 and d^10: the first omitted terms are below 3e-18 relative.
+// (Horner form; the factors are 1/(k(k+1)) of consecutive terms, as products so that no
+// division is emitted.)
+__device__ __forceinline__ void small_angle_phasor(double d, double* c, double* s) {
+    const double d2 = d * d;
+    *s = d * (1.0 - d2 * (1.0 / 6.0) *
+                        (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
+    *c = 1.0 - d2 * 0.5 *
+                   (1.0 - d2 * (1.0 / 12.0) *
+                              (1.0 - d2 * (1.0 / 30.0) * (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
+}
+
+// Newton update of one bus (FP64) that also advances u = e^{j theta} and V = Vm u: small
+// angle steps rotate u by e^{j dth}; larger ones recompute it from theta.
+__device__ __forceinline__ void update_bus(const Arrays& a, int i, double dth, double dvm, bool pq) {
+    const double th = a.Va[i] + dth;
+    a.Va[i] = th;
+    const double vm = pq ? a.Vm[i] + dvm : a.Vm[i];
+    a.Vm[i] = vm;
+    double c, s;
+    if (fabs(dth) <= 0.125) {
+        double rc, rs;
+        small_angle_phasor(dth, &rc, &rs);
+        const double uc = a.Uc[i], us = a.Us[i];
+        c = uc * rc - us * rs;
+        s = us * rc + uc * rs;
+    } else {
+        sincos(th, &s, &c);
+    }
+    a.Uc[i] = c;
+    a.Us[i] = s;
+    a.Vre[i] = vm * c;
+    a.Vim[i] = vm * s;
 }
 
 // FP32 copies of the per-bus quantities the FP32 Jacobian fill reads:
@@ -123,11 +171,14 @@ __device__ __forceinline__ void store_bus_f32(const Arrays& a, int i, double ir,
 }
 
 // I = Y V, S = V conj(I), F1 at pivot positions; returns ||F1||_inf (inf if non-finite).
-// With F32COPY the FP32 per-bus copies for the FP32 Jacobian fill are written too.
-template <bool F32COPY>
-__device__ double phase_mismatch(const DevPlan& P, const Arrays& a, double* red) {
+// The specified injections P_spec = pg - pd (pg on PV buses only) and Q_spec = -qd are
+// read from the scenario's input rows.  With F32COPY the FP32 per-bus copies for the
+// FP32 Jacobian fill are written too.
+template <bool F32COPY, bool W>
+__device__ double phase_mismatch(const DevPlan& P, const Arrays& a, const double* Pd,
+                                 const double* Qd, const double* Pg, double* red) {
     double lmax = 0.0;
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {
         double ir = 0.0, ii = 0.0;
         for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
             const int j = __ldg(P.y_idx + k);
@@ -144,28 +195,31 @@ __device__ double phase_mismatch(const DevPlan& P, const Arrays& a, double* red)
             const double vr = a.Vre[i], vi = a.Vim[i];
             const double Pi = vr * ir + vi * ii;
             const double Qi = vi * ir - vr * ii;
-            const double fP = a.Psp[i] - Pi;
-            const double fQ = (__ldg(P.bus_type + i) == 0) ? a.Qsp[i] - Qi : 0.0;
+            const int t = __ldg(P.bus_type + i);
+            const double psp = (t == 1 ? __ldg(Pg + i) : 0.0) - __ldg(Pd + i);
+            const double fP = psp - Pi;
+            const double fQ = (t == 0) ? -__ldg(Qd + i) - Qi : 0.0;
             a.F[2 * p] = fP;
             a.F[2 * p + 1] = fQ;
             lmax = fmax(lmax, fmax(absinf(fP), absinf(fQ)));
         }
     }
-    return group_max(lmax, red);
+    return group_max<W>(lmax, red);
 }
 
 // G_j = conj(m_j I_j) + sum_i m_i conj(V_i) Y_ij;  w0_j = Re(G_j u_j) = d(m.S)/dVm_j,
 // w1_j = -Im(G_j V_j) = d(m.S)/dtheta_j, for the injection weights m = mP + j mQ held in
 // (Psp, Qsp).  This is (d[P;Q]/d[Vm;theta])^T [mP; mQ] without forming the Jacobian.
+template <bool W>
 __device__ void phase_jvt(const DevPlan& P, const Arrays& a) {
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {
         const double mr = a.Psp[i], mi = a.Qsp[i];
         // h = m conj(V)
         a.dVre[i] = mr * a.Vre[i] + mi * a.Vim[i];
         a.dVim[i] = mi * a.Vre[i] - mr * a.Vim[i];
     }
-    gsync();
-    for (int j = threadIdx.x; j < P.n_bus; j += blockDim.x) {
+    gsync<W>();
+    for (int j = GTID; j < P.n_bus; j += GSZ) {
         double gr = 0.0, gi = 0.0;
         for (int k = __ldg(P.yt_ptr + j); k < __ldg(P.yt_ptr + (j + 1)); ++k) {
             const int i = __ldg(P.yt_idx + k);
@@ -217,8 +271,9 @@ __device__ __forceinline__ Blk<T> pad_pv(Blk<T> m, bool diag, int ti, int tj) {
     return m;
 }
 
+template <bool W>
 __device__ void phase_fill(const DevPlan& P, const Arrays& a, float* fac) {
-    for (int e = threadIdx.x; e < P.nnzb; e += blockDim.x) {
+    for (int e = GTID; e < P.nnzb; e += GSZ) {
         const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
         const int yi = __ldg(P.fill_y + e);
         const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
@@ -232,8 +287,9 @@ __device__ void phase_fill(const DevPlan& P, const Arrays& a, float* fac) {
     }
 }
 
+template <bool W>
 __device__ void phase_fill(const DevPlan& P, const Arrays& a, double* fac) {
-    for (int e = threadIdx.x; e < P.nnzb; e += blockDim.x) {
+    for (int e = GTID; e < P.nnzb; e += GSZ) {
         const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
         const int yi = __ldg(P.fill_y + e);
         const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
@@ -260,32 +316,33 @@ constexpr int kBatch = sizeof(FT) == 4 ? 4 : 2;
 // Right-looking, one elimination-tree level at a time.  Phase A scales the L columns of
 // the level's pivots; phase B gathers every Schur update of the level into its target
 // block (no two threads write the same block) and replaces the level's pivot blocks by
-// their inverses.  Returns nonzero if a pivot was singular.
-template <typename FT>
+// their inverses.  (A variant with one barrier per level, recomputing L(i,k) inside each
+// Schur update, measured slower: the extra 2x2 inverse per update costs more than the
+// barrier it saves.)  Returns nonzero if a pivot was singular.
+template <typename FT, bool W>
 __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
     int bad = 0;
-    if (threadIdx.x == 0) *s_bad = 0;
+    if (!W && threadIdx.x == 0) *s_bad = 0;
     for (int l = 0; l < P.n_levels; ++l) {
         const int a0 = __ldg(P.la_ptr + l), a1 = __ldg(P.la_ptr + l + 1);
-        for (int c = a0 + threadIdx.x; c < a1; c += blockDim.x) {
+        for (int c = a0 + GTID; c < a1; c += GSZ) {
             const int2 ld = __ldg(P.la + c);
             int dummy = 0;
-            Blk<FT> dinv = inv2(ldb(fac, ld.y), &dummy);
-            stb(fac, ld.x, mul(ldb(fac, ld.x), dinv));
+            stb(fac, ld.x, mul(ldb(fac, ld.x), inv2(ldb(fac, ld.y), &dummy)));
         }
-        gsync();
+        gsync<W>();
         const int t0 = __ldg(P.sch_tptr + l), t1 = __ldg(P.sch_tptr + l + 1);
-        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        for (int t = t0 + GTID; t < t1; t += GSZ) {
             const int c0 = __ldg(P.sch_cptr + t), c1 = __ldg(P.sch_cptr + t + 1);
             Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
-            constexpr int W = kBatch<FT>;
-            for (int c = c0; c < c1; c += W) {
-                int2 lu[W];
+            constexpr int NB = kBatch<FT>;
+            for (int c = c0; c < c1; c += NB) {
+                int2 lu[NB];
 #pragma unroll
-                for (int k = 0; k < W; ++k) lu[k] = (c + k < c1) ? __ldg(P.sch + c + k) : make_int2(-1, -1);
-                Blk<FT> xl[W], yu[W];
+                for (int k = 0; k < NB; ++k) lu[k] = (c + k < c1) ? __ldg(P.sch + c + k) : make_int2(-1, -1);
+                Blk<FT> xl[NB], yu[NB];
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
+                for (int k = 0; k < NB; ++k) {
                     if (lu[k].x >= 0) {
                         xl[k] = ldb(fac, lu[k].x);
                         yu[k] = ldb(fac, lu[k].y);
@@ -294,7 +351,7 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
+                for (int k = 0; k < NB; ++k) {
                     acc.a += xl[k].a * yu[k].a + xl[k].b * yu[k].c;
                     acc.b += xl[k].a * yu[k].b + xl[k].b * yu[k].d;
                     acc.c += xl[k].c * yu[k].a + xl[k].d * yu[k].c;
@@ -309,14 +366,15 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
             m.d -= acc.d;
             stb(fac, tg, m);
         }
-        for (int p = __ldg(P.lev_ptr + l) + threadIdx.x; p < __ldg(P.lev_ptr + l + 1); p += blockDim.x) {
+        for (int p = __ldg(P.lev_ptr + l) + GTID; p < __ldg(P.lev_ptr + l + 1); p += GSZ) {
             const int dk = __ldg(P.lu_diag + p);
             stb(fac, dk, inv2(ldb(fac, dk), &bad));
         }
-        gsync();
+        gsync<W>();
     }
+    if (W) return __any_sync(0xffffffffu, bad);
     if (bad) *s_bad = 1;
-    gsync();
+    gsync<W>();
     return *s_bad;
 }
 
@@ -325,28 +383,28 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
 // the U part (upper sweeps) of row p in the L+U pattern.  TRANS sweeps read the block at
 // the mirrored position, transposed (row p of U^T / L^T).  The stored pivot inverse (or
 // its transpose) is applied by the upper sweep of LU and by the first sweep of (LU)^T.
-template <typename FT, bool UPPER, bool TRANS>
+template <typename FT, bool UPPER, bool TRANS, bool W>
 __device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT* x, int l) {
     constexpr bool DIAG = UPPER != TRANS;
     const int r1 = __ldg(P.lev_ptr + l + 1);
-    for (int p = __ldg(P.lev_ptr + l) + threadIdx.x; p < r1; p += blockDim.x) {
+    for (int p = __ldg(P.lev_ptr + l) + GTID; p < r1; p += GSZ) {
         const int dg = __ldg(P.lu_diag + p);
         const int e0 = UPPER ? dg + 1 : __ldg(P.lu_ptr + p);
         const int e1 = UPPER ? __ldg(P.lu_ptr + p + 1) : dg;
         FT s0 = FT(0), s1 = FT(0);
-        constexpr int W = kBatch<FT>;
-        for (int e = e0; e < e1; e += W) {
-            int q[W], pos[W];
+        constexpr int NB = kBatch<FT>;
+        for (int e = e0; e < e1; e += NB) {
+            int q[NB], pos[NB];
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
+            for (int k = 0; k < NB; ++k) {
                 const bool ok = e + k < e1;
                 q[k] = ok ? __ldg(P.lu_col + e + k) : -1;
                 pos[k] = ok ? (TRANS ? __ldg(P.lu_mirror + e + k) : e + k) : 0;
             }
-            Blk<FT> m[W];
-            FT y0[W], y1[W];
+            Blk<FT> m[NB];
+            FT y0[NB], y1[NB];
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
+            for (int k = 0; k < NB; ++k) {
                 if (q[k] >= 0) {
                     m[k] = ldb(fac, pos[k]);
                     y0[k] = x[2 * q[k]];
@@ -357,7 +415,7 @@ __device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT*
                 }
             }
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
+            for (int k = 0; k < NB; ++k) {
                 if (TRANS) {
                     s0 += m[k].a * y0[k] + m[k].c * y1[k];
                     s1 += m[k].b * y0[k] + m[k].d * y1[k];
@@ -386,37 +444,39 @@ __device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT*
 
 // x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
 // then U x = y by descending levels.
-template <typename FT>
+template <typename FT, bool W>
 __device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x) {
     for (int l = 0; l < P.n_levels; ++l) {
-        sweep_level<FT, false, false>(P, fac, x, l);
-        gsync();
+        sweep_level<FT, false, false, W>(P, fac, x, l);
+        gsync<W>();
     }
     for (int l = P.n_levels - 1; l >= 0; --l) {
-        sweep_level<FT, true, false>(P, fac, x, l);
-        gsync();
+        sweep_level<FT, true, false, W>(P, fac, x, l);
+        gsync<W>();
     }
 }
 
 // x <- (LU)^{-T} x: U^T y = x by ascending levels (row p of U^T = mirrored L-part
 // positions of row p), then L^T x = y by descending levels (mirrored U-part positions).
-template <typename FT>
+template <typename FT, bool W>
 __device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
     for (int l = 0; l < P.n_levels; ++l) {
-        sweep_level<FT, false, true>(P, fac, x, l);
-        gsync();
+        sweep_level<FT, false, true, W>(P, fac, x, l);
+        gsync<W>();
     }
     for (int l = P.n_levels - 1; l >= 0; --l) {
-        sweep_level<FT, true, true>(P, fac, x, l);
-        gsync();
+        sweep_level<FT, true, true, W>(P, fac, x, l);
+        gsync<W>();
     }
 }
 
 // r = -F1 - J1 dz with J1 dz = -[Re dS; Im dS] linearised through Ybus (FP64):
 // dV_i = u_i dVm_i + j V_i dtheta_i, dS_i = dV_i conj(I_i) + V_i conj(sum_k Y_ik dV_k).
-// Returns ||r||_inf over the true (unpadded) rows.
-__device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red) {
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+// r is rounded straight into the solve vector x (the next right-hand side).  Returns
+// ||r||_inf over the true (unpadded) rows.
+template <typename FT, bool W>
+__device__ double phase_residual(const DevPlan& P, const Arrays& a, FT* x, double* red) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {
         const int p = __ldg(P.bus2pos + i);
         double dr = 0.0, di = 0.0;
         if (p >= 0) {
@@ -428,9 +488,9 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red)
         a.dVre[i] = dr;
         a.dVim[i] = di;
     }
-    gsync();
+    gsync<W>();
     double lmax = 0.0;
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {
         const int p = __ldg(P.bus2pos + i);
         if (p < 0) continue;
         double ir = 0.0, ii = 0.0;
@@ -448,92 +508,91 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, double* red)
         const double dSi = dvi * Ir - dvr * Ii + vi * ir - vr * ii;
         const double rP = -a.F[2 * p] + dSr;
         const double rQ = (__ldg(P.bus_type + i) == 0) ? -a.F[2 * p + 1] + dSi : 0.0;
-        a.r[2 * p] = rP;
-        a.r[2 * p + 1] = rQ;
+        x[2 * p] = FT(rP);
+        x[2 * p + 1] = FT(rQ);
         lmax = fmax(lmax, fmax(absinf(rP), absinf(rQ)));
     }
-    return group_max(lmax, red);
+    return group_max<W>(lmax, red);
 }
 
 // ---------------------------------------------------------------- forward kernel
-template <typename FT, bool VSM, bool FSM>
-__global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    __shared__ int s_bad;
-    const int b = blockIdx.x;
+// The Newton loop of one scenario, run by one group (see GTID / GSZ).
+template <typename FT, bool VSM, bool FSM, bool XSM, bool W>
+__device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
+                                           unsigned char* smem, double* red, int* s_bad_ptr) {
+    int& s_bad = *s_bad_ptr;
+    const int b = W ? (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) : (int)blockIdx.x;
     if (b >= A.batch) return;
     const SlotLayout& L = A.L;
     const KernelSmem& K = L.fwd;
     unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
     // VSM / FSM are compile-time so that the compiler sees which pointers address
     // shared memory (plain shared loads instead of generic ones)
+    if (W) smem += (threadIdx.x >> 5) * K.smem_bytes;  // this warp's own arena
     unsigned char* vbase = VSM ? smem : slot + L.off_vec;
     FT* fac = FSM ? reinterpret_cast<FT*>(smem + K.smem_fac_off)
                   : reinterpret_cast<FT*>(slot + L.off_fac);
     Arrays a;
     carve(vbase, P.n_bus, P.n, (int)sizeof(FT), false, &a);
-    FT* x = ftptr<FT>(a.x);
+    FT* x = XSM ? reinterpret_cast<FT*>(smem + K.smem_x_off) : ftptr<FT>(a.x);
     constexpr bool mixed = sizeof(FT) == 4;
     const size_t row = (size_t)b * P.n_bus;
 
     // flat start and specified injections (Sec. II-A, Sec. IV-A)
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {  // theta = 0: u = 1, V = Vm
         const int t = __ldg(P.bus_type + i);
-        a.Vm[i] = (t == 0) ? 1.0 : A.Vset[row + i];
+        const double vm = (t == 0) ? 1.0 : A.Vset[row + i];
+        a.Vm[i] = vm;
         a.Va[i] = 0.0;
-        a.Psp[i] = ((t == 1) ? A.Pg[row + i] : 0.0) - A.Pd[row + i];
-        a.Qsp[i] = -A.Qd[row + i];
+        a.Uc[i] = 1.0;
+        a.Us[i] = 0.0;
+        a.Vre[i] = vm;
+        a.Vim[i] = 0.0;
     }
-    if (threadIdx.x == 0) s_bad = 0;
-    gsync();
+    if (!W && GTID == 0) s_bad = 0;
+    gsync<W>();
 
     int it = 0, status = 1;
     double norm = 0.0;
     bool factored = false;
     for (;;) {
-        phase_voltage(P, a);
-        gsync();
-        norm = phase_mismatch<mixed>(P, a, red);  // ends with a group barrier
+        norm = phase_mismatch<mixed, W>(P, a, A.Pd + row, A.Qd + row, A.Pg + row, red);
         if (!(norm <= 1e10)) { status = 2; break; }
         if (norm <= A.tol) { status = 0; break; }
         if (it >= A.max_iter) { status = 1; break; }
-        phase_fill(P, a, fac);
-        gsync();
-        if (phase_lu<FT>(P, fac, &s_bad)) { status = 3; factored = false; break; }
+        phase_fill<W>(P, a, fac);
+        gsync<W>();
+        if (phase_lu<FT, W>(P, fac, &s_bad)) { status = 3; factored = false; break; }
         factored = true;
         // first solve with the FT factor
-        for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(-a.F[k]);
-        gsync();
-        phase_solve<FT>(P, fac, x);
+        for (int k = GTID; k < 2 * P.n; k += GSZ) x[k] = FT(-a.F[k]);
+        gsync<W>();
+        phase_solve<FT, W>(P, fac, x);
         if (mixed) {
-            for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] = double(x[k]);
-            gsync();
+            for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] = double(x[k]);
+            gsync<W>();
             for (int s = 0; s < A.ir_steps; ++s) {
-                const double rmax = phase_residual(P, a, red);
+                const double rmax = phase_residual<FT, W>(P, a, x, red);  // ends with a barrier
                 if (A.ir_rtol > 0.0 && rmax <= A.ir_rtol * norm) break;
-                for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
-                gsync();
-                phase_solve<FT>(P, fac, x);
-                for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] += double(x[k]);
-                gsync();
+                phase_solve<FT, W>(P, fac, x);
+                for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] += double(x[k]);
+                gsync<W>();
             }
         }
         // update (FP64)
-        for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
+        for (int p = GTID; p < P.n; p += GSZ) {
             const int i = __ldg(P.pos2bus + p);
             const double dth = mixed ? a.dz[2 * p] : double(x[2 * p]);
             const double dvm = mixed ? a.dz[2 * p + 1] : double(x[2 * p + 1]);
-            a.Va[i] += dth;
-            if (__ldg(P.bus_type + i) == 0) a.Vm[i] += dvm;
+            update_bus(a, i, dth, dvm, __ldg(P.bus_type + i) == 0);
         }
         ++it;
-        gsync();
+        gsync<W>();
     }
 
     // Step 2 and outputs
     double* st = reinterpret_cast<double*>(slot + L.off_state);
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+    for (int i = GTID; i < P.n_bus; i += GSZ) {
         const int t = __ldg(P.bus_type + i);
         const double vr = a.Vre[i], vi = a.Vim[i], ir = a.Ire[i], ii = a.Iim[i];
         const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
@@ -547,9 +606,9 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
     if (A.keep_factors && factored && FSM) {
         FT* dst = reinterpret_cast<FT*>(slot + L.off_fac);
         const int nv = P.nnzb * 4;
-        for (int k = threadIdx.x; k < nv; k += blockDim.x) dst[k] = fac[k];
+        for (int k = GTID; k < nv; k += GSZ) dst[k] = fac[k];
     }
-    if (threadIdx.x == 0) {
+    if (GTID == 0) {
         A.status[b] = status;
         if (A.iters) A.iters[b] = it;
         if (A.fmis) A.fmis[b] = norm;
@@ -558,6 +617,23 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
         fl[1] = it;
         fl[2] = (A.keep_factors && factored) ? 1 : 0;
     }
+}
+
+template <typename FT, bool VSM, bool FSM, bool XSM>
+__global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_bad;
+    solve_body<FT, VSM, FSM, XSM, false>(P, A, smem, red, &s_bad);
+}
+
+// Several scenarios per CTA, one per warp; the tighter register budget (42 per thread)
+// lets more warps -- more scenarios in flight -- share an SM.
+template <typename FT, bool VSM, bool FSM, bool XSM>
+__global__ void __launch_bounds__(256, 6) nr_solve_warps_kernel(DevPlan P, SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int unused = 0;  // the warp groups vote instead of sharing a flag
+    solve_body<FT, VSM, FSM, XSM, true>(P, A, smem, nullptr, &unused);
 }
 
 // ---------------------------------------------------------------- adjoint kernel
@@ -603,9 +679,9 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         a.Va[i] = st[P.n_bus + i];
     }
     if (threadIdx.x == 0) s_bad = 0;
-    gsync();
-    phase_voltage(P, a);
-    gsync();
+    gsync<false>();
+    phase_voltage<false>(P, a);
+    gsync<false>();
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {  // I = Y V
         double ir = 0.0, ii = 0.0;
         for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
@@ -624,9 +700,9 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         a.Psp[i] = (t == 2 && A.dPg) ? A.dPg[row + i] : 0.0;
         a.Qsp[i] = (t != 0 && A.dQg) ? A.dQg[row + i] : 0.0;
     }
-    gsync();
-    phase_jvt(P, a);  // v_bar2 = -J2^T c = (d[P_R; Q_{B\D}]/dv)^T c
-    gsync();
+    gsync<false>();
+    phase_jvt<false>(P, a);  // v_bar2 = -J2^T c = (d[P_R; Q_{B\D}]/dv)^T c
+    gsync<false>();
     double lg = 0.0;
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
         const double gvm = A.dVm[row + i] + a.w0[i];
@@ -639,30 +715,30 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             lg = fmax(lg, fmax(absinf(gva), absinf(a.F[2 * p + 1])));
         }
     }
-    const double gnorm = group_max(lg, red);
+    const double gnorm = group_max<false>(lg, red);
 
     // stage the stored factor
     bool have = has_factor != 0;
     if (have && FSM) {
         const int nv = P.nnzb * 4;
         for (int k = threadIdx.x; k < nv; k += blockDim.x) fac[k] = gfac[k];
-        gsync();
+        gsync<false>();
     }
     int astat = 0;
     bool refactored = false;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (!have) {
-            phase_fill(P, a, fac);
-            gsync();
-            if (phase_lu<FT>(P, fac, &s_bad)) { astat = 3; break; }
+            phase_fill<false>(P, a, fac);
+            gsync<false>();
+            if (phase_lu<FT, false>(P, fac, &s_bad)) { astat = 3; break; }
             have = true;
             refactored = true;
         }
         for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.F[k]);
-        gsync();
-        phase_solve_t<FT>(P, fac, x);
+        gsync<false>();
+        phase_solve_t<FT, false>(P, fac, x);
         for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] = double(x[k]);
-        gsync();
+        gsync<false>();
         bool conv = false;
         for (int s = 0;; ++s) {
             // m1 = lambda on the F1 rows; r = g_z1 - J1^T lambda = g_z1 + (Jv^T m1)[z1]
@@ -671,9 +747,9 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
                 a.Psp[i] = (p >= 0) ? a.dz[2 * p] : 0.0;
                 a.Qsp[i] = (p >= 0 && __ldg(P.bus_type + i) == 0) ? a.dz[2 * p + 1] : 0.0;
             }
-            gsync();
-            phase_jvt(P, a);
-            gsync();
+            gsync<false>();
+            phase_jvt<false>(P, a);
+            gsync<false>();
             double lr = 0.0;
             for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
                 const int i = __ldg(P.pos2bus + p);
@@ -683,14 +759,14 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
                 a.r[2 * p + 1] = r1;
                 lr = fmax(lr, fmax(absinf(r0), absinf(r1)));
             }
-            const double rmax = group_max(lr, red);
+            const double rmax = group_max<false>(lr, red);
             if (rmax <= A.ir_rtol * gnorm) { conv = true; break; }
             if (s >= A.ir_max || !(rmax <= 1e300)) break;
             for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
-            gsync();
-            phase_solve_t<FT>(P, fac, x);
+            gsync<false>();
+            phase_solve_t<FT, false>(P, fac, x);
             for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] += double(x[k]);
-            gsync();
+            gsync<false>();
         }
         if (conv) break;
         if (refactored) { astat = 1; break; }
@@ -713,23 +789,54 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
 }
 
 // ---------------------------------------------------------------- launchers
+// The dynamic shared-memory limit of a kernel is raised once per (device, kernel) to the
+// largest size requested so far, so that launches after the first make no attribute
+// call (a launch can then be recorded into a CUDA graph).
+cudaError_t ensure_smem_limit(const void* k, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = done[{dev, k}];
+    if (bytes <= cur && cur > 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 template <typename KernelT, typename ArgT>
 cudaError_t launch_one(KernelT k, const DevPlan& P, const ArgT& A, const KernelSmem& K,
                        int threads, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)K.smem_bytes);
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k), K.smem_bytes);
     if (e != cudaSuccess) return e;
     k<<<A.batch, threads, K.smem_bytes, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+template <typename FT, bool VSM, bool FSM, bool XSM>
+cudaError_t launch_solve_cfg(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s) {
+    if (A.ipc <= 1) return launch_one(nr_solve_kernel<FT, VSM, FSM, XSM>, P, A, A.L.fwd, threads, s);
+    auto k = nr_solve_warps_kernel<FT, VSM, FSM, XSM>;
+    const size_t smem = A.L.fwd.smem_bytes * (size_t)A.ipc;
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (A.batch + A.ipc - 1) / A.ipc;
+    k<<<grid, 32 * A.ipc, smem, s>>>(P, A);
     return cudaGetLastError();
 }
 
 template <typename FT>
 cudaError_t launch_solve(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s) {
     const KernelSmem& K = A.L.fwd;
-    if (K.vec_in_smem && K.fac_in_smem)
-        return launch_one(nr_solve_kernel<FT, true, true>, P, A, K, threads, s);
-    if (K.vec_in_smem) return launch_one(nr_solve_kernel<FT, true, false>, P, A, K, threads, s);
-    return launch_one(nr_solve_kernel<FT, false, false>, P, A, K, threads, s);
+    if (K.vec_in_smem && K.fac_in_smem) return launch_solve_cfg<FT, true, true, false>(P, A, threads, s);
+    if (K.vec_in_smem) return launch_solve_cfg<FT, true, false, false>(P, A, threads, s);
+    if (K.fac_in_smem)
+        return K.x_in_smem ? launch_solve_cfg<FT, false, true, true>(P, A, threads, s)
+                           : launch_solve_cfg<FT, false, true, false>(P, A, threads, s);
+    return K.x_in_smem ? launch_solve_cfg<FT, false, false, true>(P, A, threads, s)
+                       : launch_solve_cfg<FT, false, false, false>(P, A, threads, s);
 }
 
 template <typename FT>
@@ -738,6 +845,7 @@ cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cuda
     if (K.vec_in_smem && K.fac_in_smem)
         return launch_one(adjoint_kernel<FT, true, true>, P, A, K, threads, s);
     if (K.vec_in_smem) return launch_one(adjoint_kernel<FT, true, false>, P, A, K, threads, s);
+    if (K.fac_in_smem) return launch_one(adjoint_kernel<FT, false, true>, P, A, K, threads, s);
     return launch_one(adjoint_kernel<FT, false, false>, P, A, K, threads, s);
 }
 

@@ -260,7 +260,10 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
     P.la_ptr.assign(n_levels + 1, 0);
     P.sch_tptr.assign(n_levels + 1, 0);
     P.sch_cptr.assign(1, 0);
-    std::vector<std::pair<int, std::pair<int, int>>> contrib;  // (target, (L, U))
+    struct Contrib {
+        int t, L, U;
+    };
+    std::vector<Contrib> contrib;
     for (int l = 0; l < n_levels; ++l) {
         contrib.clear();
         for (int k = P.lev_ptr[l]; k < P.lev_ptr[l + 1]; ++k) {
@@ -276,20 +279,20 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
                     int j = P.lu_col[ej];
                     int t = find_in_row(P.lu_ptr, P.lu_col, i, j);
                     if (t < 0) return BUILD_EINVAL;  // clique property violated: bug
-                    contrib.push_back({t, {Lik, ej}});
+                    contrib.push_back({t, Lik, ej});
                 }
             }
         }
         P.la_ptr[l + 1] = (int)P.la_L.size();
         std::stable_sort(contrib.begin(), contrib.end(),
-                         [](const auto& a, const auto& b) { return a.first < b.first; });
+                         [](const Contrib& a, const Contrib& b) { return a.t < b.t; });
         for (size_t c = 0; c < contrib.size(); ++c) {
-            if (c == 0 || contrib[c].first != contrib[c - 1].first) {
-                P.sch_tgt.push_back(contrib[c].first);
+            if (c == 0 || contrib[c].t != contrib[c - 1].t) {
+                P.sch_tgt.push_back(contrib[c].t);
                 P.sch_cptr.push_back(P.sch_cptr.back());
             }
-            P.sch_L.push_back(contrib[c].second.first);
-            P.sch_U.push_back(contrib[c].second.second);
+            P.sch_L.push_back(contrib[c].L);
+            P.sch_U.push_back(contrib[c].U);
             P.sch_cptr.back()++;
         }
         P.sch_tptr[l + 1] = (int)P.sch_tgt.size();

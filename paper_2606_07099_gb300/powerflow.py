@@ -143,11 +143,15 @@ class PowerFlow:
         return _info_dict(info)
 
     @staticmethod
-    def make_opts(precision="mixed", ir_steps=1, ir_rtol=0.0, group_threads=0, keep_factors=False):
+    def make_opts(precision="mixed", ir_steps=2, ir_rtol=1e-3, group_threads=0, keep_factors=False,
+                  placement=0, instances_per_cta=0):
+        """Solve options.  Mixed precision refines with the FP64 residual until
+        ||r|| <= ir_rtol * ||F1|| (at most ir_steps sweeps; ir_rtol = 0 runs every sweep,
+        ir_steps = 0 is the unrefined FP32 step)."""
         if precision not in _PREC:
             raise ValueError("precision must be 'fp64' or 'mixed'")
         return L.SolveOpts(_PREC[precision], int(ir_steps), float(ir_rtol), int(group_threads),
-                           1 if keep_factors else 0)
+                           1 if keep_factors else 0, int(placement), int(instances_per_cta))
 
     def workspace_bytes(self, batch: int, opts: L.SolveOpts) -> int:
         n = C.c_size_t(0)
@@ -161,14 +165,16 @@ class PowerFlow:
             self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
         return self._ws
 
-    def solve(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=1,
-              ir_rtol=0.0, group_threads=0, keep_factors=False, out: SolveResult | None = None,
-              workspace: torch.Tensor | None = None) -> SolveResult:
+    def solve(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
+              ir_rtol=1e-3, group_threads=0, keep_factors=False, out: SolveResult | None = None,
+              workspace: torch.Tensor | None = None, placement=0,
+              instances_per_cta=0) -> SolveResult:
         """Batched Newton-Raphson (pf_solve) on the current stream; returns device tensors."""
         batch = Pd.shape[0]
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
             _check_bus_tensor(v, nm, self.n_bus, batch)
-        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors)
+        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
+                              instances_per_cta)
         ws = self.workspace(batch, opts) if workspace is None else workspace
         if out is None:
             e = dict(dtype=torch.float64, device=Pd.device)
@@ -187,6 +193,26 @@ class PowerFlow:
         self._solve_id += 1
         self._last = (batch, ws, bool(keep_factors))
         return out
+
+    def autotune(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
+                 ir_rtol=1e-3, keep_factors=False) -> dict:
+        """Time every launch configuration on these inputs (pf_autotune) and keep the
+        fastest for later solves at this precision.  Stream-synchronous."""
+        batch = Pd.shape[0]
+        for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
+            _check_bus_tensor(v, nm, self.n_bus, batch)
+        opts = self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, 0)
+        ws = self.workspace(batch, self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors,
+                                                  L.PF_PLACE_GLOBAL))
+        res = L.TuneResult()
+        stream = torch.cuda.current_stream(Pd.device).cuda_stream
+        L.check(self._lib.pf_autotune(self._h, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(),
+                                      Vset.data_ptr(), float(tol), int(max_iter), C.byref(opts),
+                                      ws.data_ptr(), ws.numel(), stream, C.byref(res)),
+                "pf_autotune")
+        self._last = None
+        return {"group_threads": res.group_threads, "placement": res.placement,
+                "instances_per_cta": res.instances_per_cta, "ms": res.ms}
 
     def adjoint(self, dVm, dVa, dPg=None, dQg=None) -> Gradients:
         """Implicit-differentiation backward pass (pf_adjoint) of the last solve."""
@@ -231,7 +257,7 @@ class PFLayer(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, pf: PowerFlow, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed",
-                ir_steps=1):
+                ir_steps=2):
         res = pf.solve(Pd.contiguous(), Qd.contiguous(), Pg.contiguous(), Vset.contiguous(), tol,
                        max_iter, precision, ir_steps, keep_factors=True)
         ctx.pf = pf

@@ -97,6 +97,8 @@ def compare(gpu, orc, tol=1e-8, iter_slack=0, max_iter=20, check=None):
             continue
         assert abs(int(gpu["iters"][s]) - o["iters"]) <= iter_slack, (s, gpu["iters"][s], o["iters"])
         assert gpu["final_mismatch"][s] <= tol
+        if check is not None:  # the oracle's own mismatch at the returned (Vm, theta)
+            assert check(s, gpu["Vm"][s], gpu["Va"][s]) <= 1.01 * tol + 1e-13, s
         dv = np.max(np.abs(gpu["Vm"][s] - o["Vm"]))
         dt = np.max(np.abs(gpu["Va"][s] - o["Va"]))
         dp = max(np.max(np.abs(gpu["Pg"][s] - o["Pg"])), np.max(np.abs(gpu["Qg"][s] - o["Qg"])))

@@ -33,15 +33,19 @@ def test_c0_all_scenarios_match_stored_oracle(PowerFlow, precision, ir):
     compare(gpu, orc, iter_slack=0 if precision == "fp64" else 1)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_c1_full_batch_sampled(PowerFlow, precision):
-    """118-bus, 4096 scenarios in one launch; 48 sampled scenarios against the oracle."""
+@pytest.mark.parametrize("precision,ir,rtol", [("fp64", 0, 0.0), ("mixed", 1, 0.0),
+                                               ("mixed", 2, 1e-3), ("mixed", 0, 0.0)])
+def test_c1_full_batch_sampled(PowerFlow, precision, ir, rtol):
+    """118-bus, 4096 scenarios in one launch; 48 sampled scenarios against the oracle.
+    Mixed forms: unconditional refinement, residual-checked refinement (the default),
+    and the unrefined FP32 step."""
     g, sc = workload("c1")
     pf = PowerFlow.from_grid(g)
-    gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=ir, ir_rtol=rtol)
     rng = np.random.default_rng(0)
     idx = sorted(set([0, sc.n - 1] + rng.choice(sc.n, 46, replace=False).tolist()))
-    compare(gpu, run_oracle(g, sc, idx), iter_slack=0 if precision == "fp64" else 1)
+    compare(gpu, run_oracle(g, sc, idx), iter_slack=0 if precision == "fp64" else 1,
+            check=mismatch_checker(g, sc))
     # every scenario converged within tol (property checked at full size)
     assert np.all(gpu["status"] == 0)
     assert np.all(gpu["final_mismatch"] <= 1e-8)
@@ -52,7 +56,8 @@ def test_c2_sampled(PowerFlow, precision):
     g, sc = workload("c2")
     pf = PowerFlow.from_grid(g)
     gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
-    compare(gpu, run_oracle(g, sc, [0, 511, 1023]), iter_slack=0 if precision == "fp64" else 1)
+    compare(gpu, run_oracle(g, sc, [0, 511, 1023]), iter_slack=0 if precision == "fp64" else 1,
+            check=mismatch_checker(g, sc))
     assert np.all(gpu["status"] == 0)
 
 
@@ -78,6 +83,64 @@ def test_c4_grids_flags_and_values(PowerFlow, name, n):
     worst = compare(gpu, orc, check=mismatch_checker(g, sc))
     # wandering, solution-free scenarios are the minority that the loads x U(0.6, 1.4) create
     assert worst["irregular"] <= 0.2 * len(orc)
+
+
+@pytest.mark.parametrize("name,n", [("c1", 256), ("c2", 64)])
+def test_placement_does_not_change_results(PowerFlow, name, n):
+    """Shared-memory or global placement of the scenario data is bit-identical."""
+    g, sc = workload(name, n)
+    pf = PowerFlow.from_grid(g)
+    for prec in ("mixed", "fp64"):
+        outs = [run_gpu(pf, sc, precision=prec, placement=pl) for pl in (1, 2, 3, 4)]
+        # several one-warp scenarios per CTA, from the global workspace or with the factor
+        # in shared memory
+        multi = ((3, 2), (3, 4), (4, 2)) if name == "c1" else ((3, 2), (3, 4))
+        outs += [run_gpu(pf, sc, precision=prec, placement=pl, instances_per_cta=ipc)
+                 for pl, ipc in multi]
+        for o in outs[1:]:
+            for k in o:
+                assert np.array_equal(outs[0][k], o[k]), (prec, k)
+
+
+def test_autotune_keeps_results(PowerFlow):
+    import torch
+    g, sc = workload("c1", 512)
+    pf = PowerFlow.from_grid(g)
+    ref = run_gpu(pf, sc, precision="mixed", group_threads=128, placement=1)
+    best = pf.autotune(*to_dev(sc), precision="mixed")
+    assert best["group_threads"] in (32, 64, 128, 256, 512)
+    assert best["placement"] in (1, 2, 3, 4) and best["ms"] > 0
+    assert best["instances_per_cta"] in (1, 2, 4, 8)
+    out = run_gpu(pf, sc, precision="mixed")  # now uses the tuned configuration
+    torch.cuda.synchronize()
+    for k in ref:
+        assert np.array_equal(ref[k], out[k]), k
+
+
+def test_solve_captured_in_cuda_graph(PowerFlow):
+    """The whole Newton loop is one kernel: pf_solve records into a CUDA graph and
+    replays with new inputs written into the captured input buffers."""
+    import torch
+    g, sc = workload("c1", 1024)
+    pf = PowerFlow.from_grid(g)
+    Pd, Qd, Pg, Vset = to_dev(sc)
+    pf.solve(Pd, Qd, Pg, Vset)  # warm-up outside capture (workspace, launch attributes)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        res = pf.solve(Pd, Qd, Pg, Vset)
+    g2, sc2 = workload("c1")
+    for lo in (0, 1024, 3072):
+        Pd.copy_(torch.as_tensor(sc2.Pd[lo:lo + 1024]))
+        Qd.copy_(torch.as_tensor(sc2.Qd[lo:lo + 1024]))
+        graph.replay()
+        torch.cuda.synchronize()
+        from synthgrid import Scenarios
+        part = Scenarios(Pd=sc2.Pd[lo:lo + 1024], Qd=sc2.Qd[lo:lo + 1024], Pg=sc2.Pg[:1024],
+                         Vset=sc2.Vset[:1024])
+        eager = run_gpu(pf, part)
+        assert np.array_equal(res.Vm.cpu().numpy(), eager["Vm"])
+        assert np.array_equal(res.status.cpu().numpy(), eager["status"])
 
 
 def test_thread_mapping_does_not_change_results(PowerFlow):
