@@ -34,6 +34,7 @@ WORKLOAD = "c1"
 WORKLOAD_DESC = ("synthetic 118-bus meshed grid (186 branches, 9 transformers, 1 slack, 53 PV, "
                  "64 PQ), 4096 load scenarios x U(0.7, 1.3), flat start, tol 1e-8 pu, max 20 iterations")
 METRIC = "PF solves/s at <=1e-8 pu mismatch (mixed precision form)"
+
 UNIT = "solves/s"
 L2_FLUSH_BYTES = 256 << 20
 # Peaks for the roofline.  HBM: measured copy bandwidth of this GPU family.
@@ -239,39 +240,74 @@ def gpu_leg(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, name):
         for _ in range(warmup):
             fn()
         barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
+        torch.cuda.nvtx.range_push(f"timed_{name}")  # lets a profiler select the timed steps
         for e0, e1 in evs:
             flush.fill_(1)  # evict the previous step's data from L2 (outside the timed events)
             e0.record(stream)
             fn()
             e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         barrier()
         return [e0.elapsed_time(e1) for e0, e1 in evs]
 
     opts = dict(precision="mixed", ir_steps=args.ir_steps, ir_rtol=args.ir_rtol)
     secs = set(args.sections.split(","))
+    # the largest workspace any section needs, allocated once (captured graphs keep its address)
+    pf.workspace(N, pf.make_opts("fp64", keep_factors=True, placement=3))
+    tuned = {}
+    if args.autotune:  # launch shape per precision, picked on these inputs (setup, not timed)
+        tuned["mixed"] = pf.autotune(Pd, Qd, Pg, Vset, **opts)
+        if "fp64" in secs:
+            tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
+
+    def graphed(fn):
+        """Record one step into a CUDA graph (the whole Newton loop is one kernel)."""
+        fn()
+        torch.cuda.synchronize(dev)
+        if not args.graph:
+            return fn
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            fn()
+        return gr.replay
+
     res = pf.solve(Pd, Qd, Pg, Vset, **opts)
-    mixed_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **opts)  # noqa: E731
+    mixed_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **opts))
     if "fp64" in secs:
         res64 = pf.solve(Pd, Qd, Pg, Vset, precision="fp64")
-        fp64_fn = lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64)  # noqa: E731
+        fp64_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64))
 
     # forward + backward of the implicit layer with the config-2 style loss cotangents
     slack = torch.as_tensor(g.bus_type == 2, device=dev)
+
+    def make_fwd_bwd(pfx, inputs, slack_mask, resx):
+        def step():
+            r = pfx.solve(*inputs, keep_factors=True, out=resx, **opts)
+            Vm = r.Vm
+            dVm = 2 * torch.relu(Vm - 1.06) - 2 * torch.relu(0.94 - Vm)
+            dPg = 2 * r.Pg * slack_mask
+            pfx.adjoint(dVm, torch.zeros_like(Vm), dPg, None)
+        return step
+
     if "fwdbwd" in secs:
         resk = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, **opts)
-
-    def fwd_bwd():
-        r = pf.solve(Pd, Qd, Pg, Vset, keep_factors=True, out=resk, **opts)
-        Vm = r.Vm
-        dVm = 2 * torch.relu(Vm - 1.06) - 2 * torch.relu(0.94 - Vm)
-        dPg = 2 * r.Pg * slack
-        pf.adjoint(dVm, torch.zeros_like(Vm), dPg, None)
+        fwd_bwd = graphed(make_fwd_bwd(pf, (Pd, Qd, Pg, Vset), slack, resk))
+    if "layer_c2" in secs:  # the implicit layer on the 1354-bus workload, batch 1024
+        g2 = configs.grid("c2")
+        sc2 = configs.scenarios("c2", g=g2)
+        pf2 = PowerFlow.from_grid(g2)
+        in2 = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (sc2.Pd, sc2.Qd, sc2.Pg, sc2.Vset)]
+        pf2.workspace(sc2.n, pf2.make_opts("mixed", keep_factors=True, placement=3))
+        if args.autotune:
+            tuned["layer_c2"] = pf2.autotune(*in2, keep_factors=True, **opts)
+        res2 = pf2.solve(*in2, keep_factors=True, **opts)
+        fb2 = graphed(make_fwd_bwd(pf2, in2, torch.as_tensor(g2.bus_type == 2, device=dev), res2))
 
     # end to end through the public API with host buffers
     out_host = [torch.empty(N, nb, dtype=torch.float64).pin_memory() for _ in range(2)]
@@ -290,10 +326,11 @@ def gpu_leg(args, rank, world):
 
     none = [float("nan")]
     with ClockSampler(dev.index) as clk:
-        t_mixed = timed(mixed_fn, args.steps, args.warmup)
-        t_fp64 = timed(fp64_fn, args.steps, args.warmup) if "fp64" in secs else none
-        t_fb = timed(fwd_bwd, args.steps, args.warmup) if "fwdbwd" in secs else none
-        t_e2e = timed(e2e, args.steps, args.warmup) if "e2e" in secs else none
+        t_mixed = timed(mixed_fn, args.steps, args.warmup, "mixed")
+        t_fp64 = timed(fp64_fn, args.steps, args.warmup, "fp64") if "fp64" in secs else none
+        t_fb = timed(fwd_bwd, args.steps, args.warmup, "fwdbwd") if "fwdbwd" in secs else none
+        t_fb2 = timed(fb2, args.steps, args.warmup, "layer_c2") if "layer_c2" in secs else none
+        t_e2e = timed(e2e, args.steps, args.warmup, "e2e") if "e2e" in secs else none
     clocks = clk.summary()
     torch.cuda.synchronize(dev)
     st = res.status.cpu().numpy()
@@ -311,7 +348,7 @@ def gpu_leg(args, rank, world):
             tot = float(t.item())
         return tot
 
-    T_mixed, T_fp64, T_fb, T_e2e = (agg(t) for t in (t_mixed, t_fp64, t_fb, t_e2e))
+    T_mixed, T_fp64, T_fb, T_fb2, T_e2e = (agg(t) for t in (t_mixed, t_fp64, t_fb, t_fb2, t_e2e))
     K = args.steps
     value = world * conv * K / (T_mixed / 1e3)
     ms_launch = statistics.mean(t_mixed)
@@ -328,6 +365,8 @@ def gpu_leg(args, rank, world):
                    else f"synthgrid workload {args.workload}", "n_bus": nb, "batch_per_gpu": N,
                    "global_batch": N * world, "precision": "mixed (FP32 LU + FP64 mismatch/refinement)",
                    "ir_steps": args.ir_steps, "ir_rtol": args.ir_rtol,
+                   "launch": "CUDA-graph replay of one pf_solve" if args.graph else "direct",
+                   "tuned": tuned,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
                    "parallelism": f"replicas x{world} (scenarios sharded, no collective)"},
         "converged": conv, "max_final_mismatch": fmax, "mean_iters": float(its.mean()),
@@ -335,6 +374,9 @@ def gpu_leg(args, rank, world):
                       "ms_per_step": T_fp64 / K, "mixed_speedup": T_fp64 / T_mixed},
         "fwd_bwd": {"value": world * N * K / (T_fb / 1e3), "unit": "fwd+bwd/s",
                     "ms_per_step": T_fb / K},
+        "fwd_bwd_c2": {"value": world * 1024 * K / (T_fb2 / 1e3), "unit": "fwd+bwd/s",
+                       "ms_per_step": T_fb2 / K,
+                       "workload": "1354-bus grid, 1024 scenarios, config-2 loss cotangents"},
         "e2e": {"value": world * conve * K / (T_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N},
         "gpu_launches": K,
@@ -360,11 +402,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--ir-steps", type=int, default=1)
-    ap.add_argument("--ir-rtol", type=float, default=0.0)
+    ap.add_argument("--ir-steps", type=int, default=2)
+    ap.add_argument("--ir-rtol", type=float, default=1e-3,
+                    help="refine while the FP64 residual exceeds this fraction of ||F1||")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
-    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,e2e",
+    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e",
                     help="timed sections to run (the first one, mixed, always runs)")
     ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
     args = ap.parse_args()
