@@ -256,7 +256,7 @@ def gpu_leg(args, rank, world):
         barrier()
         return [e0.elapsed_time(e1) for e0, e1 in evs]
 
-    opts = dict(precision="mixed", ir_steps=args.ir_steps, ir_rtol=args.ir_rtol)
+    opts = dict(precision="mixed", ir_steps=args.ir_steps, ir_rtol=args.ir_rtol, ir_gate=args.ir_gate)
     secs = set(args.sections.split(","))
     # the largest workspace any section needs, allocated once (captured graphs keep its address)
     pf.workspace(N, pf.make_opts("fp64", keep_factors=True, placement=3))
@@ -364,7 +364,7 @@ def gpu_leg(args, rank, world):
         "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD
                    else f"synthgrid workload {args.workload}", "n_bus": nb, "batch_per_gpu": N,
                    "global_batch": N * world, "precision": "mixed (FP32 LU + FP64 mismatch/refinement)",
-                   "ir_steps": args.ir_steps, "ir_rtol": args.ir_rtol,
+                   "ir_steps": args.ir_steps, "ir_rtol": args.ir_rtol, "ir_gate": args.ir_gate,
                    "launch": "CUDA-graph replay of one pf_solve" if args.graph else "direct",
                    "tuned": tuned,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
@@ -405,6 +405,8 @@ def main():
     ap.add_argument("--ir-steps", type=int, default=2)
     ap.add_argument("--ir-rtol", type=float, default=1e-3,
                     help="refine while the FP64 residual exceeds this fraction of ||F1||")
+    ap.add_argument("--ir-gate", type=float, default=1e-2,
+                    help="check/refine Newton steps only once ||F1||_inf <= this (0 = all)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,

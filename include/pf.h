@@ -87,8 +87,9 @@ typedef struct {
     int precision;     /* pf_precision */
     int ir_steps;      /* PF_MIXED: max refinement sweeps per Newton step (0 = the paper's
                           scheme without refinement); ignored for PF_FP64 */
-    double ir_rtol;    /* PF_MIXED: stop refining once ||r||_inf <= ir_rtol * ||F1||_inf
-                          (0 = always run ir_steps sweeps) */
+    double ir_rtol;    /* PF_MIXED: stop refining once ||r||_inf <= eta ||F1||_inf with the
+                          forcing term eta = min(ir_rtol, ||F1||_inf) (loose far from the
+                          solution, quadratic near it); 0 = always run ir_steps sweeps */
     int group_threads; /* threads per scenario (32..1024, multiple of 32; 0 = auto) */
     int keep_factors;  /* nonzero: store each scenario's last LU factor in the workspace
                           so that pf_adjoint can reuse it (required before pf_adjoint) */
@@ -97,6 +98,9 @@ typedef struct {
     int instances_per_cta; /* 0 = auto; 1 = one scenario per CTA of group_threads threads;
                           2..8 = that many scenarios per CTA, one warp each (group_threads
                           must then be 0 or 32) */
+    double ir_gate;    /* PF_MIXED: check and refine a Newton step only once ||F1||_inf <=
+                          ir_gate (far from the solution the Newton model error dwarfs the
+                          FP32 solve error); 0 = every step */
 } pf_solve_opts;
 
 typedef enum {
@@ -210,6 +214,45 @@ pf_err pf_autotune(pf_handle* h, int batch,
                    const double* Pd, const double* Qd, const double* Pg, const double* Vset,
                    double tol, int max_iter, const pf_solve_opts* opts,
                    void* workspace, size_t workspace_bytes, void* stream, pf_tune_result* out);
+
+/*
+ * One network's part of a pf_solve_multi call: the handle, its batch and the same
+ * device arrays pf_solve takes ([batch][n_bus of h]; Pg_out, Qg_out, iters and
+ * final_mismatch may be NULL).
+ */
+typedef struct {
+    pf_handle* h;
+    int batch;
+    const double *Pd, *Qd, *Pg, *Vset;
+    double *Vm, *Va, *Pg_out, *Qg_out;
+    int *iters, *status;
+    double* final_mismatch;
+} pf_job;
+
+#define PF_MAX_JOBS 8
+
+/*
+ * pf_multi_workspace_size -- workspace bytes for pf_solve_multi over these jobs, and
+ * (job_offsets, nullable, n_jobs entries) where each job's part starts inside it.
+ * Errors: PF_EINVAL (n_jobs outside 1..PF_MAX_JOBS, a NULL handle, batch < 1, bad opts).
+ */
+pf_err pf_multi_workspace_size(int n_jobs, const pf_job* jobs, const pf_solve_opts* opts,
+                               size_t* bytes, size_t* job_offsets);
+
+/*
+ * pf_solve_multi -- the scenarios of several networks (grids of different sizes, uneven
+ * batches) in ONE persistent launch.  CTAs take scenarios from a device work counter,
+ * the most expensive network's scenarios first, and run each with its own plan: same
+ * Newton iteration, outputs and status as pf_solve per job.  All data lives in the
+ * global workspace (placement PF_PLACE_GLOBAL; opts->placement must be 0 or that),
+ * group_threads threads per scenario (0 = 128), instances_per_cta must be 0 or 1.
+ * With keep_factors, each job's handle remembers its part of the workspace, so
+ * pf_adjoint(job.h, job.batch, ..., workspace + job_offsets[j], ...) differentiates it.
+ * All handles must live on the current device.  Errors: PF_EINVAL, PF_ECUDA.
+ */
+pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
+                      const pf_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                      void* stream);
 
 /*
  * pf_adjoint -- implicit-differentiation backward pass of Sec. II-B.2 at the

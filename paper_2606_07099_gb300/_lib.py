@@ -31,7 +31,7 @@ class PlanInfo(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("ir_steps", C.c_int), ("ir_rtol", C.c_double),
                 ("group_threads", C.c_int), ("keep_factors", C.c_int), ("placement", C.c_int),
-                ("instances_per_cta", C.c_int)]
+                ("instances_per_cta", C.c_int), ("ir_gate", C.c_double)]
 
 
 class TuneResult(C.Structure):
@@ -40,6 +40,14 @@ class TuneResult(C.Structure):
 
 
 PF_PLACE_AUTO, PF_PLACE_ONCHIP, PF_PLACE_VECTORS, PF_PLACE_GLOBAL, PF_PLACE_FACTOR = range(5)
+PF_MAX_JOBS = 8
+
+
+class Job(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("batch", C.c_int),
+                ("Pd", C.c_void_p), ("Qd", C.c_void_p), ("Pg", C.c_void_p), ("Vset", C.c_void_p),
+                ("Vm", C.c_void_p), ("Va", C.c_void_p), ("Pg_out", C.c_void_p), ("Qg_out", C.c_void_p),
+                ("iters", C.c_void_p), ("status", C.c_void_p), ("final_mismatch", C.c_void_p)]
 
 
 SIGNATURES = {
@@ -55,6 +63,9 @@ SIGNATURES = {
     "pf_adjoint": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "pf_solve_noalloc": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
                               _p, _p, _p, _p, _p, _p, _p, _p]),
+    "pf_multi_workspace_size": (_i, [_i, C.POINTER(Job), C.POINTER(SolveOpts), C.POINTER(_sz),
+                                     C.POINTER(_sz)]),
+    "pf_solve_multi": (_i, [_i, C.POINTER(Job), _d, _i, C.POINTER(SolveOpts), _p, _sz, _p]),
     "pf_destroy": (None, [_p]),
     "pf_error_string": (C.c_char_p, [_i]),
 }

@@ -174,7 +174,7 @@ bool opts_ok(const pf_solve_opts* o) {
     if (!o) return false;
     if (o->precision != PF_FP64 && o->precision != PF_MIXED) return false;
     if (o->ir_steps < 0 || o->ir_steps > 64) return false;
-    if (!(o->ir_rtol >= 0.0)) return false;
+    if (!(o->ir_rtol >= 0.0) || !(o->ir_gate >= 0.0)) return false;
     if (o->group_threads != 0 &&
         (o->group_threads < 32 || o->group_threads > 1024 || o->group_threads % 32)) return false;
     if (o->placement < PF_PLACE_AUTO || o->placement > PF_PLACE_FACTOR) return false;
@@ -411,6 +411,7 @@ pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, con
     A.max_iter = max_iter;
     A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
     A.ir_rtol = opts->ir_rtol;
+    A.ir_gate = opts->ir_gate;
     A.keep_factors = opts->keep_factors ? 1 : 0;
     A.Pd = Pd;
     A.Qd = Qd;
@@ -538,6 +539,128 @@ pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, 
     if (err != PF_OK) return err;
     h->tuned[opts->precision == PF_MIXED ? 1 : 0] = best;
     if (out) *out = best;
+    return PF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+bool multi_ok(int n_jobs, const pf_job* jobs, const pf_solve_opts* opts) {
+    if (n_jobs < 1 || n_jobs > pf::kMaxJobs || !jobs || !opts_ok(opts)) return false;
+    if (opts->placement != PF_PLACE_AUTO && opts->placement != PF_PLACE_GLOBAL) return false;
+    if (opts->instances_per_cta > 1) return false;
+    for (int j = 0; j < n_jobs; ++j)
+        if (!jobs[j].h || jobs[j].batch < 1) return false;
+    return true;
+}
+
+// the multi path keeps every job in the global workspace
+pf::SlotLayout multi_layout(const pf_handle* h, const pf_solve_opts* opts) {
+    return make_layout(h, opts->precision == PF_MIXED ? 4 : 8, opts->keep_factors, PF_PLACE_GLOBAL);
+}
+
+// Workspace: a 256-byte header (the work counter), then one region per job.
+size_t multi_layout_offsets(int n_jobs, const pf_job* jobs, const pf_solve_opts* opts,
+                            size_t* offsets) {
+    size_t o = 256;
+    for (int j = 0; j < n_jobs; ++j) {
+        if (offsets) offsets[j] = o;
+        o = pf::align_up(o + multi_layout(jobs[j].h, opts).slot_bytes * (size_t)jobs[j].batch, 256);
+    }
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_err pf_multi_workspace_size(int n_jobs, const pf_job* jobs, const pf_solve_opts* opts,
+                               size_t* bytes, size_t* job_offsets) {
+    if (!bytes || !multi_ok(n_jobs, jobs, opts)) return PF_EINVAL;
+    *bytes = multi_layout_offsets(n_jobs, jobs, opts, job_offsets);
+    return PF_OK;
+}
+
+pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
+                      const pf_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                      void* stream) {
+    if (!multi_ok(n_jobs, jobs, opts) || !workspace || !(tol > 0.0) || max_iter < 0) return PF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
+    for (int j = 0; j < n_jobs; ++j) {
+        const pf_job& J = jobs[j];
+        if (!J.Pd || !J.Qd || !J.Pg || !J.Vset || !J.Vm || !J.Va || !J.status) return PF_EINVAL;
+        if (J.h->device != jobs[0].h->device) return PF_EINVAL;
+    }
+    size_t offs[pf::kMaxJobs];
+    if (workspace_bytes < multi_layout_offsets(n_jobs, jobs, opts, offs)) return PF_EINVAL;
+    const int threads = opts->group_threads ? opts->group_threads : 128;
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    // most expensive scenarios first (factor blocks x levels as the cost estimate)
+    int order[pf::kMaxJobs];
+    for (int j = 0; j < n_jobs; ++j) order[j] = j;
+    std::stable_sort(order, order + n_jobs, [&](int a, int b) {
+        const pf::Plan &pa = jobs[a].h->plan, &pb = jobs[b].h->plan;
+        return (long long)pa.nnzb() * pa.n_levels > (long long)pb.nnzb() * pb.n_levels;
+    });
+    DeviceGuard guard(jobs[0].h->device);
+    pf::MultiArgs M{};
+    M.n_jobs = n_jobs;
+    M.counter = static_cast<unsigned int*>(workspace);
+    size_t smem = 0;
+    int first = 0;
+    for (int k = 0; k < n_jobs; ++k) {
+        const pf_job& J = jobs[order[k]];
+        pf::SlotLayout L = multi_layout(J.h, opts);
+        smem = std::max(smem, L.fwd.smem_bytes);
+        pf::SolveArgs& A = M.args[k];
+        A = pf::SolveArgs{};
+        A.batch = J.batch;
+        A.ipc = 1;
+        A.tol = tol;
+        A.max_iter = max_iter;
+        A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
+        A.ir_rtol = opts->ir_rtol;
+        A.ir_gate = opts->ir_gate;
+        A.keep_factors = opts->keep_factors ? 1 : 0;
+        A.Pd = J.Pd;
+        A.Qd = J.Qd;
+        A.Pg = J.Pg;
+        A.Vset = J.Vset;
+        A.Vm = J.Vm;
+        A.Va = J.Va;
+        A.Pg_out = J.Pg_out;
+        A.Qg_out = J.Qg_out;
+        A.fmis = J.final_mismatch;
+        A.iters = J.iters;
+        A.status = J.status;
+        A.ws = static_cast<char*>(workspace) + offs[order[k]];
+        A.L = L;
+        M.plans[k] = J.h->dp;
+        M.first[k] = first;
+        first += J.batch;
+    }
+    M.first[n_jobs] = first;
+    M.total = first;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int per_sm = 0;
+    cudaError_t e = ft == 4 ? pf::multi_blocks_per_sm<float>(threads, smem, &per_sm)
+                            : pf::multi_blocks_per_sm<double>(threads, smem, &per_sm);
+    if (e != cudaSuccess || per_sm < 1) return PF_ECUDA;
+    const int grid = std::min(per_sm * jobs[0].h->num_sms, M.total);
+    if (cudaMemsetAsync(M.counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PF_ECUDA;
+    e = ft == 4 ? pf::launch_solve_multi<float>(M, threads, grid, smem, s)
+                : pf::launch_solve_multi<double>(M, threads, grid, smem, s);
+    if (e != cudaSuccess) return PF_ECUDA;
+    for (int k = 0; k < n_jobs; ++k) {  // each handle can now run pf_adjoint on its part
+        pf_handle* h = jobs[order[k]].h;
+        h->last_batch = M.args[k].batch;
+        h->last_ft = ft;
+        h->last_keep = M.args[k].keep_factors;
+        h->last_threads = threads;
+        h->last_ws = M.args[k].ws;
+        h->last_layout = M.args[k].L;
+    }
     return PF_OK;
 }
 

@@ -65,6 +65,7 @@ struct SolveArgs {
     int max_iter;
     int ir_steps;
     double ir_rtol;
+    double ir_gate;
     int keep_factors;
     const double* Pd;
     const double* Qd;
@@ -79,6 +80,18 @@ struct SolveArgs {
     int* status;
     char* ws;
     SlotLayout L;
+};
+
+// Several networks in one launch (pf_solve_multi): per job its plan and solve arguments,
+// and the first global work item of each job (jobs are contiguous ranges of items).
+constexpr int kMaxJobs = 8;
+struct MultiArgs {
+    int n_jobs;
+    int total;
+    unsigned int* counter;  // work counter in the workspace, zeroed before the launch
+    int first[kMaxJobs + 1];
+    DevPlan plans[kMaxJobs];
+    SolveArgs args[kMaxJobs];
 };
 
 struct AdjArgs {

@@ -518,10 +518,9 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, FT* x, doubl
 // ---------------------------------------------------------------- forward kernel
 // The Newton loop of one scenario, run by one group (see GTID / GSZ).
 template <typename FT, bool VSM, bool FSM, bool XSM, bool W>
-__device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
+__device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A, const int b,
                                            unsigned char* smem, double* red, int* s_bad_ptr) {
     int& s_bad = *s_bad_ptr;
-    const int b = W ? (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) : (int)blockIdx.x;
     if (b >= A.batch) return;
     const SlotLayout& L = A.L;
     const KernelSmem& K = L.fwd;
@@ -571,9 +570,12 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         if (mixed) {
             for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] = double(x[k]);
             gsync<W>();
-            for (int s = 0; s < A.ir_steps; ++s) {
+            const int sweeps = (A.ir_gate > 0.0 && norm > A.ir_gate) ? 0 : A.ir_steps;
+            for (int s = 0; s < sweeps; ++s) {
                 const double rmax = phase_residual<FT, W>(P, a, x, red);  // ends with a barrier
-                if (A.ir_rtol > 0.0 && rmax <= A.ir_rtol * norm) break;
+                // forcing term min(ir_rtol, ||F1||): loose far from the solution, quadratic
+                // near it, so the inexact Newton steps keep the quadratic convergence
+                if (A.ir_rtol > 0.0 && rmax <= fmin(A.ir_rtol, norm) * norm) break;
                 phase_solve<FT, W>(P, fac, x);
                 for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] += double(x[k]);
                 gsync<W>();
@@ -598,8 +600,10 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
         A.Vm[row + i] = a.Vm[i];
         A.Va[row + i] = a.Va[i];
-        st[i] = a.Vm[i];
-        st[P.n_bus + i] = a.Va[i];
+        if (A.keep_factors) {  // the solution the adjoint differentiates at
+            st[i] = a.Vm[i];
+            st[P.n_bus + i] = a.Va[i];
+        }
         if (A.Pg_out) A.Pg_out[row + i] = (t == 1) ? A.Pg[row + i] : (t == 2 ? Pi + A.Pd[row + i] : 0.0);
         if (A.Qg_out) A.Qg_out[row + i] = (t == 0) ? 0.0 : Qi + A.Qd[row + i];
     }
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     __shared__ int s_bad;
-    solve_body<FT, VSM, FSM, XSM, false>(P, A, smem, red, &s_bad);
+    solve_body<FT, VSM, FSM, XSM, false>(P, A, blockIdx.x, smem, red, &s_bad);
 }
 
 // Several scenarios per CTA, one per warp; the tighter register budget (42 per thread)
@@ -633,7 +637,35 @@ template <typename FT, bool VSM, bool FSM, bool XSM>
 __global__ void __launch_bounds__(256, 6) nr_solve_warps_kernel(DevPlan P, SolveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     int unused = 0;  // the warp groups vote instead of sharing a flag
-    solve_body<FT, VSM, FSM, XSM, true>(P, A, smem, nullptr, &unused);
+    const int b = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    solve_body<FT, VSM, FSM, XSM, true>(P, A, b, smem, nullptr, &unused);
+}
+
+// Several networks in one persistent launch: CTAs take scenarios from a work counter,
+// jobs in the order given (the host puts the most expensive first), and run each with
+// its own plan.  Every job keeps its data in the global workspace (the solve vector in
+// shared memory when it is small), so one launch shape serves all of them.
+template <typename FT>
+__global__ void __launch_bounds__(1024) nr_solve_multi_kernel(MultiArgs M) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ int s_bad;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(M.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();  // everyone has read s_item before it is overwritten
+        if (item >= M.total) break;
+        int j = 0;
+        while (j + 1 < M.n_jobs && item >= M.first[j + 1]) ++j;
+        const int b = item - M.first[j];
+        if (M.args[j].L.fwd.x_in_smem)
+            solve_body<FT, false, false, true, false>(M.plans[j], M.args[j], b, smem, red, &s_bad);
+        else
+            solve_body<FT, false, false, false, false>(M.plans[j], M.args[j], b, smem, red, &s_bad);
+        __syncthreads();  // the next scenario reuses the shared arrays
+    }
 }
 
 // ---------------------------------------------------------------- adjoint kernel
@@ -849,6 +881,24 @@ cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cuda
     return launch_one(adjoint_kernel<FT, false, false>, P, A, K, threads, s);
 }
 
+template <typename FT>
+cudaError_t launch_solve_multi(const MultiArgs& M, int threads, int grid, size_t smem, cudaStream_t s) {
+    auto k = nr_solve_multi_kernel<FT>;
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, s>>>(M);
+    return cudaGetLastError();
+}
+
+template <typename FT>
+cudaError_t multi_blocks_per_sm(int threads, size_t smem, int* out) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, nr_solve_multi_kernel<FT>, threads, smem);
+}
+
+template cudaError_t launch_solve_multi<float>(const MultiArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t launch_solve_multi<double>(const MultiArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t multi_blocks_per_sm<float>(int, size_t, int*);
+template cudaError_t multi_blocks_per_sm<double>(int, size_t, int*);
 template cudaError_t launch_solve<float>(const DevPlan&, const SolveArgs&, int, cudaStream_t);
 template cudaError_t launch_solve<double>(const DevPlan&, const SolveArgs&, int, cudaStream_t);
 template cudaError_t launch_adjoint<float>(const DevPlan&, const AdjArgs&, int, cudaStream_t);

@@ -7,5 +7,9 @@ namespace pf {
 template <typename FT>
 cudaError_t launch_solve(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s);
 template <typename FT>
+cudaError_t launch_solve_multi(const MultiArgs& M, int threads, int grid, size_t smem, cudaStream_t s);
+template <typename FT>
+cudaError_t multi_blocks_per_sm(int threads, size_t smem, int* out);
+template <typename FT>
 cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s);
 }  // namespace pf

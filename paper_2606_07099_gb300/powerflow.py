@@ -144,14 +144,16 @@ class PowerFlow:
 
     @staticmethod
     def make_opts(precision="mixed", ir_steps=2, ir_rtol=1e-3, group_threads=0, keep_factors=False,
-                  placement=0, instances_per_cta=0):
+                  placement=0, instances_per_cta=0, ir_gate=0.0):
         """Solve options.  Mixed precision refines with the FP64 residual until
-        ||r|| <= ir_rtol * ||F1|| (at most ir_steps sweeps; ir_rtol = 0 runs every sweep,
-        ir_steps = 0 is the unrefined FP32 step)."""
+        ||r|| <= min(ir_rtol, ||F1||) * ||F1|| (at most ir_steps sweeps; ir_rtol = 0 runs
+        every sweep, ir_steps = 0 is the unrefined FP32 step), on the Newton steps taken
+        once ||F1|| <= ir_gate (0 = on every step)."""
         if precision not in _PREC:
             raise ValueError("precision must be 'fp64' or 'mixed'")
         return L.SolveOpts(_PREC[precision], int(ir_steps), float(ir_rtol), int(group_threads),
-                           1 if keep_factors else 0, int(placement), int(instances_per_cta))
+                           1 if keep_factors else 0, int(placement), int(instances_per_cta),
+                           float(ir_gate))
 
     def workspace_bytes(self, batch: int, opts: L.SolveOpts) -> int:
         n = C.c_size_t(0)
@@ -168,13 +170,13 @@ class PowerFlow:
     def solve(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
               ir_rtol=1e-3, group_threads=0, keep_factors=False, out: SolveResult | None = None,
               workspace: torch.Tensor | None = None, placement=0,
-              instances_per_cta=0) -> SolveResult:
+              instances_per_cta=0, ir_gate=0.0) -> SolveResult:
         """Batched Newton-Raphson (pf_solve) on the current stream; returns device tensors."""
         batch = Pd.shape[0]
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
             _check_bus_tensor(v, nm, self.n_bus, batch)
         opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
-                              instances_per_cta)
+                              instances_per_cta, ir_gate)
         ws = self.workspace(batch, opts) if workspace is None else workspace
         if out is None:
             e = dict(dtype=torch.float64, device=Pd.device)
@@ -195,13 +197,13 @@ class PowerFlow:
         return out
 
     def autotune(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
-                 ir_rtol=1e-3, keep_factors=False) -> dict:
+                 ir_rtol=1e-3, keep_factors=False, ir_gate=0.0) -> dict:
         """Time every launch configuration on these inputs (pf_autotune) and keep the
         fastest for later solves at this precision.  Stream-synchronous."""
         batch = Pd.shape[0]
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
             _check_bus_tensor(v, nm, self.n_bus, batch)
-        opts = self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, 0)
+        opts = self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, 0, 0, ir_gate)
         ws = self.workspace(batch, self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors,
                                                   L.PF_PLACE_GLOBAL))
         res = L.TuneResult()
@@ -284,3 +286,47 @@ class PFLayer(torch.autograd.Function):
         g = pf.adjoint(dense(gVm), dense(gVa), None if gPg is None else gPg.contiguous(),
                        None if gQg is None else gQg.contiguous())
         return None, g.dPd, g.dQd, g.dPg, g.dVset, None, None, None, None
+
+
+def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,
+                group_threads=0, keep_factors=False, ir_gate=0.0):
+    """Several networks in one persistent launch (pf_solve_multi).
+
+    ``items`` is a list of ``(PowerFlow, Pd, Qd, Pg, Vset)``; returns one SolveResult per
+    item.  With ``keep_factors`` each PowerFlow can run ``adjoint`` on its part afterwards.
+    """
+    if not 1 <= len(items) <= L.PF_MAX_JOBS:
+        raise ValueError(f"1..{L.PF_MAX_JOBS} networks per launch")
+    lib = L.load()
+    opts = PowerFlow.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors,
+                               L.PF_PLACE_GLOBAL, 0, ir_gate)
+    jobs = (L.Job * len(items))()
+    results = []
+    for k, (pf, Pd, Qd, Pg, Vset) in enumerate(items):
+        batch = Pd.shape[0]
+        for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
+            _check_bus_tensor(v, nm, pf.n_bus, batch)
+        e = dict(dtype=torch.float64, device=Pd.device)
+        r = SolveResult(Vm=torch.empty(batch, pf.n_bus, **e), Va=torch.empty(batch, pf.n_bus, **e),
+                        Pg=torch.empty(batch, pf.n_bus, **e), Qg=torch.empty(batch, pf.n_bus, **e),
+                        iters=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                        status=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                        final_mismatch=torch.empty(batch, **e))
+        results.append(r)
+        jobs[k] = L.Job(pf._h.value, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(), Vset.data_ptr(),
+                        r.Vm.data_ptr(), r.Va.data_ptr(), r.Pg.data_ptr(), r.Qg.data_ptr(),
+                        r.iters.data_ptr(), r.status.data_ptr(), r.final_mismatch.data_ptr())
+    nbytes = C.c_size_t(0)
+    offs = (C.c_size_t * len(items))()
+    L.check(lib.pf_multi_workspace_size(len(items), jobs, C.byref(opts), C.byref(nbytes), offs),
+            "pf_multi_workspace_size")
+    dev = items[0][1].device
+    ws = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    L.check(lib.pf_solve_multi(len(items), jobs, float(tol), int(max_iter), C.byref(opts),
+                               ws.data_ptr(), ws.numel(), stream), "pf_solve_multi")
+    ends = [offs[k + 1] if k + 1 < len(items) else nbytes.value for k in range(len(items))]
+    for k, (pf, Pd, *_rest) in enumerate(items):
+        pf._solve_id += 1
+        pf._last = (Pd.shape[0], ws[offs[k]:ends[k]], bool(keep_factors))
+    return results

@@ -33,15 +33,16 @@ def test_c0_all_scenarios_match_stored_oracle(PowerFlow, precision, ir):
     compare(gpu, orc, iter_slack=0 if precision == "fp64" else 1)
 
 
-@pytest.mark.parametrize("precision,ir,rtol", [("fp64", 0, 0.0), ("mixed", 1, 0.0),
-                                               ("mixed", 2, 1e-3), ("mixed", 0, 0.0)])
-def test_c1_full_batch_sampled(PowerFlow, precision, ir, rtol):
+@pytest.mark.parametrize("precision,ir,rtol,gate", [("fp64", 0, 0.0, 0.0), ("mixed", 1, 0.0, 0.0),
+                                                    ("mixed", 2, 1e-3, 0.0), ("mixed", 0, 0.0, 0.0),
+                                                    ("mixed", 2, 1e-3, 1e-2)])
+def test_c1_full_batch_sampled(PowerFlow, precision, ir, rtol, gate):
     """118-bus, 4096 scenarios in one launch; 48 sampled scenarios against the oracle.
     Mixed forms: unconditional refinement, residual-checked refinement (the default),
     and the unrefined FP32 step."""
     g, sc = workload("c1")
     pf = PowerFlow.from_grid(g)
-    gpu = run_gpu(pf, sc, precision=precision, ir_steps=ir, ir_rtol=rtol)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=ir, ir_rtol=rtol, ir_gate=gate)
     rng = np.random.default_rng(0)
     idx = sorted(set([0, sc.n - 1] + rng.choice(sc.n, 46, replace=False).tolist()))
     compare(gpu, run_oracle(g, sc, idx), iter_slack=0 if precision == "fp64" else 1,
