@@ -309,6 +309,52 @@ def gpu_leg(args, rank, world):
         res2 = pf2.solve(*in2, keep_factors=True, **opts)
         fb2 = graphed(make_fwd_bwd(pf2, in2, torch.as_tensor(g2.bus_type == 2, device=dev), res2))
 
+    if "multi_c4" in secs:  # uneven batch: 30/300/2000-bus networks in one persistent launch
+        from paper_2606_07099_gb300.powerflow import solve_multi
+        items4, slacks4 = [], []
+        for name in ("c4a", "c4b", "c4c"):
+            g4 = configs.grid(name)
+            sc4 = configs.scenarios(name, g=g4)
+            items4.append((PowerFlow.from_grid(g4),
+                           *[torch.as_tensor(np.ascontiguousarray(a), device=dev)
+                             for a in (sc4.Pd, sc4.Qd, sc4.Pg, sc4.Vset)]))
+            slacks4.append(torch.as_tensor(g4.bus_type == 2, device=dev))
+        n4 = sum(it[1].shape[0] for it in items4)
+        # launch shape of the single launch: fastest of a few thread counts (setup, not timed)
+        best4 = None
+        for th in (64, 128, 256):
+            solve_multi(items4, group_threads=th, **opts)
+            torch.cuda.synchronize(dev)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            solve_multi(items4, group_threads=th, **opts)
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+            if best4 is None or t0.elapsed_time(t1) < best4[1]:
+                best4 = (th, t0.elapsed_time(t1))
+        tuned["multi_c4"] = {"group_threads": best4[0]}
+        res4 = [None]
+
+        def multi_fwd():
+            res4[0] = solve_multi(items4, group_threads=best4[0], **opts)
+
+        def multi_fwd_bwd():
+            rs = solve_multi(items4, group_threads=best4[0], keep_factors=True, **opts)
+            for (pfx, *_), r, sl in zip(items4, rs, slacks4):
+                dVm = 2 * torch.relu(r.Vm - 1.06) - 2 * torch.relu(0.94 - r.Vm)
+                pfx.adjoint(dVm, torch.zeros_like(r.Vm), 2 * r.Pg * sl, None)
+    if "c3" in secs:  # the 9241-bus grid, 256 scenarios: the factor streams through memory
+        g3 = configs.grid("c3")
+        sc3 = configs.scenarios("c3", g=g3)
+        pf3 = PowerFlow.from_grid(g3)
+        in3 = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (sc3.Pd, sc3.Qd, sc3.Pg, sc3.Vset)]
+        pf3.workspace(sc3.n, pf3.make_opts("mixed", placement=3))
+        if args.autotune:
+            tuned["c3"] = pf3.autotune(*in3, **opts)
+        res3 = pf3.solve(*in3, **opts)
+        c3_fn = graphed(lambda: pf3.solve(*in3, out=res3, **opts))
+
     # end to end through the public API with host buffers
     out_host = [torch.empty(N, nb, dtype=torch.float64).pin_memory() for _ in range(2)]
     st_host = torch.empty(N, dtype=torch.int32).pin_memory()
@@ -331,6 +377,10 @@ def gpu_leg(args, rank, world):
         t_fb = timed(fwd_bwd, args.steps, args.warmup, "fwdbwd") if "fwdbwd" in secs else none
         t_fb2 = timed(fb2, args.steps, args.warmup, "layer_c2") if "layer_c2" in secs else none
         t_e2e = timed(e2e, args.steps, args.warmup, "e2e") if "e2e" in secs else none
+        t_m4 = timed(multi_fwd, args.steps, args.warmup, "multi_c4") if "multi_c4" in secs else none
+        t_m4b = (timed(multi_fwd_bwd, args.steps, args.warmup, "multi_c4_fb")
+                 if "multi_c4" in secs else none)
+        t_c3 = timed(c3_fn, args.steps, args.warmup, "c3") if "c3" in secs else none
     clocks = clk.summary()
     torch.cuda.synchronize(dev)
     st = res.status.cpu().numpy()
@@ -348,7 +398,32 @@ def gpu_leg(args, rank, world):
             tot = float(t.item())
         return tot
 
-    T_mixed, T_fp64, T_fb, T_fb2, T_e2e = (agg(t) for t in (t_mixed, t_fp64, t_fb, t_fb2, t_e2e))
+    T_mixed, T_fp64, T_fb, T_fb2, T_e2e, T_m4, T_m4b, T_c3 = (
+        agg(t) for t in (t_mixed, t_fp64, t_fb, t_fb2, t_e2e, t_m4, t_m4b, t_c3))
+    K = args.steps
+    extra = {}
+    if "multi_c4" in secs:
+        conv4 = sum(int((r.status == 0).sum().item()) for r in res4[0])
+        extra["multi_c4"] = {
+            "workload": "2048 x 30-bus + 512 x 300-bus + 64 x 2000-bus scenarios, loads x U(0.6, 1.4), "
+                        "one persistent launch", "scenarios": n4, "converged": conv4,
+            "solves_per_s": world * conv4 * K / (T_m4 / 1e3), "ms_per_step": T_m4 / K,
+            "fwd_bwd_per_s": world * n4 * K / (T_m4b / 1e3), "fwd_bwd_ms_per_step": T_m4b / K}
+    if "c3" in secs:
+        conv3 = int((res3.status == 0).sum().item())
+        info3 = pf3.info()
+        f64_3, f32_3, _ = alg_counts(info3, g3.n_bus, res3.iters.cpu().numpy(), args.ir_steps, "mixed")
+        # factor traffic per Newton iteration and scenario: written by the fill, read and
+        # written once by the LU (every block is a Schur target or an L/U operand at least
+        # once), read by each triangular solve pair
+        fac_b = 16 * info3["nnzb_lu"]
+        it3 = float(res3.iters.sum().item())
+        bytes3 = it3 * fac_b * (1 + 2 + 2) + sc3.n * (8 * 8 * g3.n_bus)
+        extra["c3"] = {"workload": "9241-bus grid, 256 scenarios, mixed", "converged": conv3,
+                       "solves_per_s": world * conv3 * K / (T_c3 / 1e3), "ms_per_step": T_c3 / K,
+                       "hbm_algorithmic_gbs": bytes3 / (T_c3 / K / 1e3) / 1e9,
+                       "hbm_frac": bytes3 / (T_c3 / K / 1e3) / 1e9 / hbm_peak()[0],
+                       "traffic_per_launch": profiled_traffic("nr_solve_c3_mixed.json")}
     K = args.steps
     value = world * conv * K / (T_mixed / 1e3)
     ms_launch = statistics.mean(t_mixed)
@@ -392,6 +467,7 @@ def gpu_leg(args, rank, world):
                 "peak_source": hbm_src, "frac": hbm_bytes / (ms_launch / 1e3) / 1e9 / hbm_peak_gbs,
                 "bytes_per_launch": hbm_bytes},
         "clocks": clocks,
+        **extra,
     }
     return line
 
@@ -411,7 +487,7 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
-    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e",
+    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3",
                     help="timed sections to run (the first one, mixed, always runs)")
     ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
     args = ap.parse_args()
