@@ -18,6 +18,9 @@ What it computes, in the paper's notation (SABLE, arXiv 2606.07099, Sec. II):
   J1^T lambda = g_z1, dL/dx = g_x - [lambda_G; J3^T lambda], extended to the
   loads through dF1/dpd = -1 and dF1/dqd = -1 on the matching rows.
 
+Beyond the paper: ``nr_solve_qlim`` adds the reactive-limit (PV -> PQ switching) outer
+loop of production power-flow tools around the same Newton iteration.
+
 Readings where the paper is silent (each one is listed in the design notes):
 
 * Ybus is the standard pi model: series admittance ys = 1/(r + jx), half the
@@ -161,6 +164,47 @@ def _solve(J, rhs):
     return lu.solve(rhs)
 
 
+def _newton(Y, bus_type, Pspec, Qspec, Vm, Va, tol, max_iter, hist):
+    """Newton steps J1 dz = -F1, z1 <- z1 + dz from (Vm, Va) on the partition
+    ``bus_type`` until ||F1||_inf <= tol; returns (Vm, Va, steps, status)."""
+    D, G, R, BnR, BnD = bus_sets(bus_type)
+    nD = D.shape[0]
+    k = 0
+    while True:
+        F1 = F1_of(Y, bus_type, Vm, Va, Pspec, Qspec)
+        norm = float(np.max(np.abs(F1))) if F1.size else 0.0
+        hist.append(norm)
+        if not np.all(np.isfinite(F1)) or norm > DIVERGE_LIMIT:
+            return Vm, Va, k, DIVERGED
+        if norm <= tol:
+            return Vm, Va, k, CONVERGED
+        if k >= max_iter:
+            return Vm, Va, k, MAXITER
+        J1 = J1_of(Y, bus_type, Vm, Va)
+        try:
+            dz = _solve(J1, -F1)
+        except (np.linalg.LinAlgError, RuntimeError):
+            return Vm, Va, k, SINGULAR
+        if not np.all(np.isfinite(dz)):
+            return Vm, Va, k, SINGULAR
+        Vm = Vm.copy()
+        Va = Va.copy()
+        Vm[D] += dz[:nD]
+        Va[BnR] += dz[nD:]
+        k += 1
+
+
+def _step2(Y, bus_type, Vm, Va, Pd, Qd, Pg):
+    """Step 2 (Eq. F2_completion): dP_R = 0 and dQ_{B\\D} = 0 solved for z2."""
+    D, G, R, BnR, BnD = bus_sets(bus_type)
+    S = injections(Y, Vm, Va)
+    Qg = np.zeros_like(Vm)
+    Qg[BnD] = S.imag[BnD] + np.asarray(Qd, float)[BnD]
+    Pg_out = np.where(np.asarray(bus_type) == PV, np.asarray(Pg, float), 0.0)
+    Pg_out[R] = S.real[R] + np.asarray(Pd, float)[R]
+    return Pg_out, Qg
+
+
 def nr_solve(Y, bus_type, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, record=False):
     """Newton-Raphson on F1 from the flat start for one scenario (Step 1 + Step 2).
 
@@ -169,51 +213,65 @@ def nr_solve(Y, bus_type, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, record=False)
     recovered qg on B\\D, 0 on D) -- plus iters, status, final_mismatch and, if
     ``record``, the list of the iterates' ||F1||_inf.
     """
-    D, G, R, BnR, BnD = bus_sets(bus_type)
     Pspec, Qspec = specified_injections(bus_type, Pd, Qd, Pg)
     Vm, Va = flat_start(bus_type, Vset)
-    nD = D.shape[0]
     hist = []
-    status = MAXITER
-    k = 0
-    while True:
-        F1 = F1_of(Y, bus_type, Vm, Va, Pspec, Qspec)
-        norm = float(np.max(np.abs(F1))) if F1.size else 0.0
-        hist.append(norm)
-        if not np.all(np.isfinite(F1)) or norm > DIVERGE_LIMIT:
-            status = DIVERGED
-            break
-        if norm <= tol:
-            status = CONVERGED
-            break
-        if k >= max_iter:
-            status = MAXITER
-            break
-        J1 = J1_of(Y, bus_type, Vm, Va)
-        try:
-            dz = _solve(J1, -F1)
-        except (np.linalg.LinAlgError, RuntimeError):
-            status = SINGULAR
-            break
-        if not np.all(np.isfinite(dz)):
-            status = SINGULAR
-            break
-        Vm = Vm.copy()
-        Va = Va.copy()
-        Vm[D] += dz[:nD]
-        Va[BnR] += dz[nD:]
-        k += 1
-    # Step 2 (Eq. F2_completion): dP_R = 0 and dQ_{B\D} = 0 solved for z2
-    S = injections(Y, Vm, Va)
-    Qg = np.zeros_like(Vm)
-    Qg[BnD] = S.imag[BnD] + np.asarray(Qd, float)[BnD]
-    Pg_out = np.where(np.asarray(bus_type) == PV, np.asarray(Pg, float), 0.0)
-    Pg_out[R] = S.real[R] + np.asarray(Pd, float)[R]
+    Vm, Va, k, status = _newton(Y, bus_type, Pspec, Qspec, Vm, Va, tol, max_iter, hist)
+    Pg_out, Qg = _step2(Y, bus_type, Vm, Va, Pd, Qd, Pg)
     out = dict(Vm=Vm, Va=Va, Pg=Pg_out, Qg=Qg, iters=k, status=status,
                final_mismatch=hist[-1])
     if record:
         out["history"] = hist
     return out
+
+
+def nr_solve_qlim(Y, bus_type, Pd, Qd, Pg, Vset, Qmin, Qmax, tol=1e-8, max_iter=20,
+                  max_rounds=10):
+    """Newton-Raphson with reactive-power limits at the PV buses (PV -> PQ switching).
+
+    Not part of the paper's method: the limit handling of production power-flow
+    tools, on top of Step 1 / Step 2.  Round 0 is ``nr_solve``.  When a round has
+    converged, the recovered qg_i = Q_i + qd_i of every bus that is still PV is
+    compared with [Qmin_i, Qmax_i].  All violators at once become PQ buses whose
+    reactive generation is fixed at the violated limit (Q_spec_i = qlim_i - qd_i; their
+    Vm joins z1), and Newton continues from the current voltages on the new partition,
+    with max_iter steps per round.  A switched bus stays PQ.  The result is CONVERGED
+    when a converged round leaves no violator, MAXITER when a round runs out of steps
+    or violators remain after ``max_rounds`` switching rounds, and DIVERGED/SINGULAR as
+    in ``nr_solve``.  Returns the fields of ``nr_solve`` (Pg and Qg on the original bus
+    sets; iters = Newton steps over all rounds) plus the final per-bus ``bus_type`` and
+    the number of switching ``rounds``.
+    """
+    bt0 = np.asarray(bus_type)
+    bt = bt0.copy()
+    Qd = np.asarray(Qd, float)
+    Pspec, _ = specified_injections(bt0, Pd, Qd, Pg)
+    qfix = np.zeros(bt.shape[0])
+    Vm, Va = flat_start(bt0, Vset)
+    hist = []
+    total = 0
+    rounds = 0
+    while True:
+        Qspec = np.where(bt == PQ, qfix - Qd, -Qd)
+        Vm, Va, k, status = _newton(Y, bt, Pspec, Qspec, Vm, Va, tol, max_iter, hist)
+        total += k
+        if status != CONVERGED:
+            break
+        qg = injections(Y, Vm, Va).imag + Qd
+        hi = (bt == PV) & (qg > Qmax)
+        lo = (bt == PV) & (qg < Qmin)
+        if not (hi.any() or lo.any()):
+            break
+        if rounds >= max_rounds:
+            status = MAXITER
+            break
+        bt = bt.copy()
+        bt[hi | lo] = PQ
+        qfix = np.where(hi, Qmax, np.where(lo, Qmin, qfix))
+        rounds += 1
+    Pg_out, Qg = _step2(Y, bt0, Vm, Va, Pd, Qd, Pg)
+    return dict(Vm=Vm, Va=Va, Pg=Pg_out, Qg=Qg, iters=total, status=status,
+                final_mismatch=hist[-1], bus_type=bt, rounds=rounds)
 
 
 # --------------------------------------------------------------------------
