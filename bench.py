@@ -344,16 +344,108 @@ def gpu_leg(args, rank, world):
             for (pfx, *_), r, sl in zip(items4, rs, slacks4):
                 dVm = 2 * torch.relu(r.Vm - 1.06) - 2 * torch.relu(0.94 - r.Vm)
                 pfx.adjoint(dVm, torch.zeros_like(r.Vm), 2 * r.Pg * sl, None)
-    if "c3" in secs:  # the 9241-bus grid, 256 scenarios: the factor streams through memory
-        g3 = configs.grid("c3")
-        sc3 = configs.scenarios("c3", g=g3)
-        pf3 = PowerFlow.from_grid(g3)
-        in3 = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (sc3.Pd, sc3.Qd, sc3.Pg, sc3.Vset)]
-        pf3.workspace(sc3.n, pf3.make_opts("mixed", placement=3))
+    large = {}  # the grids whose factors stream through memory: 9241 and 25,000 buses
+    for lname in ("c3", "c5"):
+        if lname not in secs:
+            continue
+        gl = configs.grid(lname)
+        scl = configs.scenarios(lname, g=gl)
+        pfl = PowerFlow.from_grid(gl)
+        inl = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (scl.Pd, scl.Qd, scl.Pg, scl.Vset)]
+        pfl.workspace(scl.n, pfl.make_opts("mixed", placement=3))
         if args.autotune:
-            tuned["c3"] = pf3.autotune(*in3, **opts)
-        res3 = pf3.solve(*in3, **opts)
-        c3_fn = graphed(lambda: pf3.solve(*in3, out=res3, **opts))
+            tuned[lname] = pfl.autotune(*inl, **opts)
+        resl = pfl.solve(*inl, **opts)
+        # the tuple keeps the inputs alive: a captured graph holds only their addresses
+        large[lname] = (gl, scl, pfl, resl,
+                        graphed(lambda pfl=pfl, inl=inl, resl=resl: pfl.solve(*inl, out=resl, **opts)),
+                        inl)
+
+    if "qlim" in secs:  # reactive limits at a third of the PV buses (PV -> PQ switching)
+        Qg0 = res.Qg[0].clone()
+        pv = np.flatnonzero(g.bus_type == 1)
+        pick = torch.as_tensor(np.random.default_rng(1).choice(pv, len(pv) // 3, replace=False),
+                               device=dev)
+        qmax_row = torch.full((nb,), 1e30, dtype=torch.float64, device=dev)
+        qmin_row = torch.full((nb,), -1e30, dtype=torch.float64, device=dev)
+        qmax_row[pick] = Qg0[pick] - 0.02
+        qmin_row[pick] = Qg0[pick] - 1.0
+        Qmax_b = qmax_row.expand(N, nb).contiguous()
+        Qmin_b = qmin_row.expand(N, nb).contiguous()
+        resq = [pf.solve_qlim(Pd, Qd, Pg, Vset, Qmin_b, Qmax_b, **opts)]
+        qlim_fn = lambda: resq.__setitem__(0, pf.solve_qlim(Pd, Qd, Pg, Vset, Qmin_b, Qmax_b, **opts))
+
+    if "jacobian" in secs:  # block-diagonal export of J1 (Alg. 1 values into the BDE template)
+        jac_cases = []
+        for jname, jn in (("c2", 64), ("c2", 1024), ("c3", 64)):
+            gj = configs.grid(jname)
+            pfj = PowerFlow.from_grid(gj)
+            scj = configs.scenarios(jname, jn, gj)
+            rj = pfj.solve(*[torch.as_tensor(np.ascontiguousarray(a), device=dev)
+                             for a in (scj.Pd, scj.Qd, scj.Pg, scj.Vset)], precision="fp64")
+            outj = pfj.export_jacobian(rj.Vm, rj.Va)
+            jac_cases.append((jname, jn, gj, pfj, rj, outj))
+
+    if "train" in secs:  # the layer inside a DC3-style training loop (network -> PF -> loss)
+        from paper_2606_07099_gb300 import embedded as em
+        from synthgrid import make_opf_limits
+        train_sets = []
+        for tname, batches in (("c1", (256, 1024, 4096)), ("c2", (64, 256, 1024))):
+            gt = configs.grid(tname)
+            sct = configs.scenarios(tname, 2 * max(batches), gt)
+            pft = PowerFlow.from_grid(gt)
+            ldt = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (sct.Pd, sct.Qd)]
+            pft.workspace(max(batches), pft.make_opts("fp64", keep_factors=True, placement=3))
+            if args.autotune:  # launch shape of the layer's solve (setup, not timed)
+                tuned[f"train_{tname}"] = pft.autotune(
+                    ldt[0][:max(batches)], ldt[1][:max(batches)],
+                    torch.as_tensor(sct.Pg[:max(batches)], device=dev),
+                    torch.as_tensor(sct.Vset[:max(batches)], device=dev), keep_factors=True, **opts)
+            train_sets.append((tname, gt, pft, ldt, batches, make_opf_limits(gt, 11)))
+
+    def train_run(gt, pft, ldt, B, lim, steps, warmup, graph):
+        torch.manual_seed(0)
+        base_mem = torch.cuda.memory_allocated(dev)
+        torch.cuda.reset_peak_memory_stats(dev)
+        model = em.EmbeddedPF(pft, gt.bus_type, gt.Pd0, gt.Qd0, lim, hidden=256,
+                              ir_steps=args.ir_steps, ir_rtol=args.ir_rtol,
+                              ir_gate=args.ir_gate).to(dev)
+        optim = torch.optim.Adam(model.net.parameters(), lr=1e-3, capturable=graph)
+        nbt = ldt[0].shape[0] // B
+        Pdb = ldt[0][:nbt * B].view(nbt, B, -1)
+        Qdb = ldt[1][:nbt * B].view(nbt, B, -1)
+        stats = []
+        it = [0]
+        if graph:
+            trainer = em.GraphedTrainer(model, optim, Pdb[0], Qdb[0])
+            one = trainer.step
+        else:
+            one = lambda Pd_, Qd_: em.train_step(model, optim, Pd_, Qd_)
+
+        def step():
+            k = it[0] % nbt
+            it[0] += 1
+            L_, n_ = one(Pdb[k], Qdb[k])
+            stats.append((L_.clone(), n_.clone()))
+        t_host = time.perf_counter()
+        ts = timed(step, steps, warmup, f"train_{gt.name}_{B}{'_graph' if graph else ''}")
+        t_host = (time.perf_counter() - t_host) / (steps + warmup)
+        loss = torch.stack([x[0] for x in stats]).cpu().numpy()
+        n_ok = torch.stack([x[1] for x in stats]).cpu().numpy()
+        peak = torch.cuda.max_memory_allocated(dev) - base_mem
+        return {"batch": B, "graph": graph, "samples_per_s": world * B * steps / (agg(ts) / 1e3),
+                "ms_per_step": agg(ts) / steps, "host_ms_per_step": 1e3 * t_host,
+                "converged_frac": float(n_ok.sum() / (B * len(n_ok))),
+                "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
+                "peak_train_mem_mb": peak / 2**20, "train_mem_mb_per_sample": peak / 2**20 / B}
+
+    def agg(ts):
+        tot = sum(ts)
+        if world > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return tot
 
     # end to end through the public API with host buffers
     out_host = [torch.empty(N, nb, dtype=torch.float64).pin_memory() for _ in range(2)]
@@ -380,7 +472,17 @@ def gpu_leg(args, rank, world):
         t_m4 = timed(multi_fwd, args.steps, args.warmup, "multi_c4") if "multi_c4" in secs else none
         t_m4b = (timed(multi_fwd_bwd, args.steps, args.warmup, "multi_c4_fb")
                  if "multi_c4" in secs else none)
-        t_c3 = timed(c3_fn, args.steps, args.warmup, "c3") if "c3" in secs else none
+        t_large = {k: timed(v[4], args.steps, args.warmup, k) for k, v in large.items()}
+        t_qlim = timed(qlim_fn, args.steps, args.warmup, "qlim") if "qlim" in secs else none
+        t_jac = [timed(lambda c=c: c[3].export_jacobian(c[4].Vm, c[4].Va, out=c[5]), args.steps,
+                       args.warmup, f"jacobian_{c[0]}_{c[1]}")
+                 for c in (jac_cases if "jacobian" in secs else [])]
+        train_out = {}
+        if "train" in secs:
+            ksteps = max(5, min(args.steps, 20))
+            for tname, gt, pft, ldt, batches, lim in train_sets:
+                train_out[tname] = [train_run(gt, pft, ldt, B, lim, ksteps, max(3, args.warmup), gr)
+                                    for B in batches for gr in (True, False)]
     clocks = clk.summary()
     torch.cuda.synchronize(dev)
     st = res.status.cpu().numpy()
@@ -390,16 +492,8 @@ def gpu_leg(args, rank, world):
     conve = int((rese.status.cpu().numpy() == 0).sum()) if "e2e" in secs else 0
     fmax = float(res.final_mismatch.max().item())
 
-    def agg(ts):
-        tot = sum(ts)
-        if world > 1:
-            t = torch.tensor([tot], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot
-
-    T_mixed, T_fp64, T_fb, T_fb2, T_e2e, T_m4, T_m4b, T_c3 = (
-        agg(t) for t in (t_mixed, t_fp64, t_fb, t_fb2, t_e2e, t_m4, t_m4b, t_c3))
+    T_mixed, T_fp64, T_fb, T_fb2, T_e2e, T_m4, T_m4b = (
+        agg(t) for t in (t_mixed, t_fp64, t_fb, t_fb2, t_e2e, t_m4, t_m4b))
     K = args.steps
     extra = {}
     if "multi_c4" in secs:
@@ -409,22 +503,74 @@ def gpu_leg(args, rank, world):
                         "one persistent launch", "scenarios": n4, "converged": conv4,
             "solves_per_s": world * conv4 * K / (T_m4 / 1e3), "ms_per_step": T_m4 / K,
             "fwd_bwd_per_s": world * n4 * K / (T_m4b / 1e3), "fwd_bwd_ms_per_step": T_m4b / K}
-    if "c3" in secs:
-        conv3 = int((res3.status == 0).sum().item())
-        info3 = pf3.info()
-        f64_3, f32_3, _ = alg_counts(info3, g3.n_bus, res3.iters.cpu().numpy(), args.ir_steps, "mixed")
+    for lname, (gl, scl, pfl, resl, _, _) in large.items():
+        Tl = agg(t_large[lname])
+        convl = int((resl.status == 0).sum().item())
         # factor traffic per Newton iteration and scenario: written by the fill, read and
         # written once by the LU (every block is a Schur target or an L/U operand at least
         # once), read by each triangular solve pair
-        fac_b = 16 * info3["nnzb_lu"]
-        it3 = float(res3.iters.sum().item())
-        bytes3 = it3 * fac_b * (1 + 2 + 2) + sc3.n * (8 * 8 * g3.n_bus)
-        extra["c3"] = {"workload": "9241-bus grid, 256 scenarios, mixed", "converged": conv3,
-                       "solves_per_s": world * conv3 * K / (T_c3 / 1e3), "ms_per_step": T_c3 / K,
-                       "hbm_algorithmic_gbs": bytes3 / (T_c3 / K / 1e3) / 1e9,
-                       "hbm_frac": bytes3 / (T_c3 / K / 1e3) / 1e9 / hbm_peak()[0],
-                       "traffic_per_launch": profiled_traffic("nr_solve_c3_mixed.json")}
-    K = args.steps
+        fac_b = 16 * pfl.info()["nnzb_lu"]
+        itl = float(resl.iters.sum().item())
+        bytesl = itl * fac_b * (1 + 2 + 2) + scl.n * (8 * 8 * gl.n_bus)
+        extra[lname] = {"workload": f"{gl.n_bus}-bus grid, {scl.n} scenarios, mixed",
+                        "converged": convl, "mean_iters": itl / scl.n,
+                        "solves_per_s": world * convl * K / (Tl / 1e3), "ms_per_step": Tl / K,
+                        "hbm_algorithmic_gbs": bytesl / (Tl / K / 1e3) / 1e9,
+                        "hbm_frac": bytesl / (Tl / K / 1e3) / 1e9 / hbm_peak()[0],
+                        "traffic_per_launch": profiled_traffic(f"nr_solve_{lname}_mixed.json")}
+    if "qlim" in secs:
+        Tq = agg(t_qlim)
+        rq = resq[0]
+        convq = int((rq.status == 0).sum().item())
+        extra["qlim"] = {
+            "workload": "the headline batch with reactive limits just below the unlimited "
+                        "output at a third of the PV buses (PV -> PQ switching, pf_solve_qlim)",
+            "converged": convq, "solves_per_s": world * convq * K / (Tq / 1e3),
+            "ms_per_step": Tq / K, "mean_rounds": float(rq.rounds.double().mean().item()),
+            "mean_iters": float(rq.iters.double().mean().item()),
+            "switched_buses_per_scenario": float(((rq.bus_type == 0).sum(1).double()
+                                                  - int((g.bus_type == 0).sum())).mean().item())}
+    if "jacobian" in secs:
+        rows = []
+        for (jname, jn, gj, pfj, rj, outj), tj in zip(jac_cases, t_jac):
+            ms = agg(tj) / K
+            info_j = pfj.info()
+            byts = jn * (8 * info_j["nnz_j1"] + 16 * gj.n_bus)  # values written, V read
+            rows.append({"workload": f"{gj.n_bus}-bus grid, {jn} scenarios", "ms": ms,
+                         "values_per_s": jn * info_j["nnz_j1"] / (ms / 1e3),
+                         "hbm_gbs": byts / (ms / 1e3) / 1e9,
+                         "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm_peak()[0]})
+        extra["jacobian_export"] = {
+            "what": "pf_export_jacobian: J1 values of every scenario at its solution, written "
+                    "in FP64 into the fixed block-diagonal (BDE) template",
+            "cases": rows}
+    if "memory" in secs:  # device bytes: the shared plan plus a fixed slot per scenario
+        mem = {}
+        for mname in ("c0", "c1", "c2", "c3", "c5"):
+            gm = configs.grid(mname)
+            pfm_ = PowerFlow.from_grid(gm)
+            per = {}
+            for prec in ("mixed", "fp64"):
+                for keep in (False, True):
+                    o_ = pfm_.make_opts(prec, keep_factors=keep, placement=3)
+                    b1, b2 = pfm_.workspace_bytes(1, o_), pfm_.workspace_bytes(1024, o_)
+                    assert b2 == 1024 * b1  # linear in the batch, no per-batch term
+                    per[f"{prec}{'_keep' if keep else ''}"] = b1
+            mem[mname] = {"n_bus": gm.n_bus, "plan_bytes": pfm_.info()["plan_bytes"],
+                          "workspace_bytes_per_scenario": per}
+            pfm_.close()
+        extra["memory"] = {"note": "workspace = batch x slot (global placement), plan shared by "
+                                   "all scenarios; keep = factors kept for the adjoint",
+                           "grids": mem}
+    if "train" in secs:
+        extra["train"] = {
+            "workload": ("DC3-style learning loop: MLP (2 x 256, ReLU, FP32) from loads to "
+                         "[pg_G; Vm_B\\D], PF layer (mixed, fwd + implicit bwd), loss = cost + "
+                         "100 x squared limit violations, Adam 1e-3; batches cycle through "
+                         "2 x max-batch synthetic load scenarios; graph: the whole step "
+                         "(forward, implicit backward, optimiser) replayed from one CUDA graph, "
+                         "else eager PyTorch around the libpf calls"),
+            "unit": "samples/s", **train_out}
     value = world * conv * K / (T_mixed / 1e3)
     ms_launch = statistics.mean(t_mixed)
     f64, f32, hbm_bytes = alg_counts(info, nb, its, args.ir_steps, "mixed")
@@ -487,7 +633,7 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
-    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3",
+    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3,c5,qlim,jacobian,memory,train",
                     help="timed sections to run (the first one, mixed, always runs)")
     ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
     args = ap.parse_args()

@@ -80,6 +80,7 @@ typedef struct {
     int nnzb_lu;       /* 2x2 blocks in the filled L+U pattern */
     int n_levels;      /* depth of the elimination tree */
     long long schur_block_ops; /* 2x2 multiply-subtracts of one factorisation */
+    long long plan_bytes;      /* the network's device plan (shared by every scenario) */
 } pf_plan_info;
 
 /* Tunables of a solve; zero-initialise and set what you need. */
@@ -155,16 +156,52 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices,
  * pf_create (host).  If pos2bus / lu_ptr / lu_col / lev_ptr are non-NULL they
  * receive the block ordering (pos2bus[n_block]: bus of pivot position p), the
  * filled L+U block pattern in CSR over positions (lu_ptr[n_block + 1],
- * lu_col[nnzb_lu]) and the level ranges (lev_ptr[n_levels + 1]); call first with
- * them NULL to learn the sizes from *info.  Errors as pf_create, minus
- * PF_ENOMEM / PF_ECUDA.
+ * lu_col[nnzb_lu]) and the level ranges (lev_ptr[n_levels + 1]); if j1_ptr / j1_col
+ * are non-NULL they receive the scalar J1 template of pf_jacobian_pattern
+ * (j1_ptr[n_unknowns + 1], j1_col[nnz_j1]).  Call first with them NULL to learn the
+ * sizes from *info.  Errors as pf_create, minus PF_ENOMEM / PF_ECUDA.
  */
 pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices,
                   const double* y_re, const double* y_im, const int* bus_type,
-                  pf_plan_info* info, int* pos2bus, int* lu_ptr, int* lu_col, int* lev_ptr);
+                  pf_plan_info* info, int* pos2bus, int* lu_ptr, int* lu_col, int* lev_ptr,
+                  int* j1_ptr, int* j1_col);
 
 /* Plan facts (host only, no device work).  PF_EINVAL on NULL arguments. */
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info);
+
+/*
+ * pf_jacobian_pattern -- the fixed sparse template of J1 (Eq. step1_jacobian) of one
+ * scenario as a scalar CSR in the paper's ordering (host output): rows
+ * [dP_{B\R}; dQ_D], columns z1 = [Vm_D; theta_{B\R}], each part in bus order, columns
+ * ascending within a row; one entry per Ybus entry (i, j) and applicable (row, column)
+ * pair.  j1_ptr[n_unknowns + 1], j1_col[nnz_j1] (sizes from pf_plan_info).  This is the
+ * per-scenario block of the block-diagonal embedding (BDE) of Sec. III-A.
+ * Errors: PF_EINVAL on NULL arguments.
+ */
+pf_err pf_jacobian_pattern(const pf_handle* h, int* j1_ptr, int* j1_col);
+
+/*
+ * pf_bde_pattern -- the index arrays of the block-diagonal embedding (Sec. III-A) of
+ * `batch` scenarios, written on the device: one CSR of size (batch n1) x (batch n1)
+ * whose diagonal block k is the J1 template shifted by k n1 (n1 = n_unknowns):
+ * row_ptr[batch n1 + 1] (device int) and col_idx[batch nnz_j1] (device int).  The
+ * pattern is fixed; pf_export_jacobian refreshes only the values.  Asynchronous on
+ * `stream`.  Errors: PF_EINVAL (NULL, batch < 1, batch nnz_j1 >= 2^31), PF_ECUDA.
+ */
+pf_err pf_bde_pattern(const pf_handle* h, int batch, int* row_ptr, int* col_idx, void* stream);
+
+/*
+ * pf_export_jacobian -- the values of J1 = dF1/dz1 (Eq. step1_jacobian, element formulas
+ * of Alg. 1) of `batch` scenarios at the voltages Vm, Va (device, [batch][n_bus],
+ * FP64), written in FP64 into values[batch][nnz_j1] (device) in the order of
+ * pf_jacobian_pattern: scenario k's values are the k-th block of the BDE matrix of
+ * pf_bde_pattern (an in-place value update of the fixed template, Sec. III-A/III-B).
+ * Inputs at slack buses are read for V only.  Asynchronous on `stream`.  For callers
+ * that hand the batch to another sparse solver; pf_solve itself never forms this
+ * matrix (it fills its factor directly).  Errors: PF_EINVAL, PF_ECUDA.
+ */
+pf_err pf_export_jacobian(const pf_handle* h, int batch, const double* Vm, const double* Va,
+                          double* values, void* stream);
 
 /*
  * pf_workspace_size -- device bytes pf_solve / pf_adjoint need for `batch`
@@ -196,6 +233,46 @@ pf_err pf_solve(pf_handle* h, int batch,
                 double* Vm, double* Va, double* Pg_out, double* Qg_out,
                 int* iters, int* status, double* final_mismatch,
                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * pf_qlim_workspace_size -- device bytes pf_solve_qlim needs for `batch` scenarios with
+ * these options (the pf_solve workspace plus the scenario's own bus partition).
+ * opts->keep_factors must be 0.  Errors: PF_EINVAL.
+ */
+pf_err pf_qlim_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts,
+                              size_t* bytes);
+
+/*
+ * pf_solve_qlim -- pf_solve with reactive-power limits at the PV buses.  The paper has
+ * no counterpart (its PV buses hold Vm at any reactive output); this is the PV -> PQ
+ * switching of production power-flow tools, around the same Step 1 / Step 2.
+ * When a scenario has converged, every bus of it that is still PV and whose recovered
+ * reactive generation qg = Q + qd lies outside [Qmin, Qmax] becomes a PQ bus of that
+ * scenario with qg fixed at the violated limit (all violators at once); Newton then
+ * continues from the current voltages on the new partition, with max_iter steps per
+ * round.  A switched bus stays PQ.  The symbolic plan is unchanged: every bus already
+ * owns a full 2x2 block of the factor pattern (a PV bus's Vm row and column are padded
+ * with the identity), so a switch changes values only.
+ * Inputs as pf_solve, plus Qmin, Qmax (device, [batch][n_bus], read on PV buses).
+ * Outputs as pf_solve (Pg_out and Qg_out on the network's bus sets: a switched bus
+ * reports its input pg and its qg, at the limit), plus bus_type_out (device int,
+ * [batch][n_bus], nullable: the final partition of each scenario) and rounds (device
+ * int [batch], nullable: switching rounds taken); iters counts the Newton steps of all
+ * rounds.  status: PF_CONVERGED when a converged round leaves no violator;
+ * PF_MAXITER when a round ran out of steps or violators remain after max_rounds rounds
+ * (the outputs are then the last converged point, on its partition); PF_DIVERGED /
+ * PF_SINGULAR as pf_solve.  The workspace (pf_qlim_workspace_size) keeps no factors:
+ * keep_factors must be 0 and pf_adjoint does not apply to this call.
+ * Errors: as pf_solve, and PF_EINVAL for NULL limits, max_rounds < 0 or keep_factors.
+ */
+pf_err pf_solve_qlim(pf_handle* h, int batch,
+                     const double* Pd, const double* Qd, const double* Pg, const double* Vset,
+                     const double* Qmin, const double* Qmax,
+                     double tol, int max_iter, int max_rounds, const pf_solve_opts* opts,
+                     double* Vm, double* Va, double* Pg_out, double* Qg_out,
+                     int* iters, int* status, double* final_mismatch,
+                     int* bus_type_out, int* rounds,
+                     void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * pf_autotune -- picks the launch configuration (threads per scenario and placement

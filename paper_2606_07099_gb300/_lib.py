@@ -25,7 +25,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("n_bus", C.c_int), ("n_slack", C.c_int), ("n_pv", C.c_int), ("n_pq", C.c_int),
                 ("n_unknowns", C.c_int), ("n_block", C.c_int), ("nnz_ybus", C.c_int),
                 ("nnz_j1", C.c_int), ("nnzb_lu", C.c_int), ("n_levels", C.c_int),
-                ("schur_block_ops", C.c_longlong)]
+                ("schur_block_ops", C.c_longlong), ("plan_bytes", C.c_longlong)]
 
 
 class SolveOpts(C.Structure):
@@ -53,7 +53,11 @@ class Job(C.Structure):
 SIGNATURES = {
     "pf_build_ybus": (_i, [_i, _i, _ip, _ip, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _ip]),
     "pf_create": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(_p)]),
-    "pf_analyze": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanInfo), _ip, _ip, _ip, _ip]),
+    "pf_analyze": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanInfo), _ip, _ip, _ip, _ip,
+                        _ip, _ip]),
+    "pf_jacobian_pattern": (_i, [_p, _ip, _ip]),
+    "pf_bde_pattern": (_i, [_p, _i, _p, _p, _p]),
+    "pf_export_jacobian": (_i, [_p, _i, _p, _p, _p, _p]),
     "pf_get_plan_info": (_i, [_p, C.POINTER(PlanInfo)]),
     "pf_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
     "pf_solve": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
@@ -66,6 +70,9 @@ SIGNATURES = {
     "pf_multi_workspace_size": (_i, [_i, C.POINTER(Job), C.POINTER(SolveOpts), C.POINTER(_sz),
                                      C.POINTER(_sz)]),
     "pf_solve_multi": (_i, [_i, C.POINTER(Job), _d, _i, C.POINTER(SolveOpts), _p, _sz, _p]),
+    "pf_qlim_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
+    "pf_solve_qlim": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _d, _i, _i, C.POINTER(SolveOpts),
+                           _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "pf_destroy": (None, [_p]),
     "pf_error_string": (C.c_char_p, [_i]),
 }

@@ -54,6 +54,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     cxx_flags = ["-O2", "-std=c++17", "-fPIC", "-I", os.path.join(_cuda_home(), "include")] + inc
     jobs = [
         [nvcc, "-c", os.path.join(CSRC, "pf_kernels.cu"), "-o", os.path.join(BUILD, "pf_kernels.o")] + cu_flags,
+        [nvcc, "-c", os.path.join(CSRC, "pf_qlim.cu"), "-o", os.path.join(BUILD, "pf_qlim.o")] + cu_flags,
         [nvcc, "-c", os.path.join(CSRC, "pf_noalloc.cu"), "-o", os.path.join(BUILD, "pf_noalloc.o")] + cu_flags,
         [cxx, "-c", os.path.join(CSRC, "pf_api.cpp"), "-o", os.path.join(BUILD, "pf_api.o")] + cxx_flags,
         [cxx, "-c", os.path.join(CSRC, "pf_plan.cpp"), "-o", os.path.join(BUILD, "pf_plan.o")] + cxx_flags,
@@ -62,6 +63,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         outs = list(ex.map(_run, jobs))
     tmp = LIB + ".tmp"
     _run([nvcc, "-shared"] + ARCH + ["-o", tmp, os.path.join(BUILD, "pf_kernels.o"),
+                                     os.path.join(BUILD, "pf_qlim.o"),
                                      os.path.join(BUILD, "pf_noalloc.o"),
                                      os.path.join(BUILD, "pf_api.o"), os.path.join(BUILD, "pf_plan.o"),
                                      "-cudart", "static", "-lpthread", "-ldl", "-lrt"])

@@ -32,6 +32,7 @@ struct pf_handle {
     int last_threads = 0;
     const void* last_ws = nullptr;
     pf::SlotLayout last_layout{};
+    size_t plan_bytes = 0;  // the device plan buffer
 };
 
 namespace {
@@ -119,7 +120,8 @@ int heuristic_placement(const pf_handle* h, int ft_bytes) {
     return PF_PLACE_GLOBAL;
 }
 
-pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int placement) {
+pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int placement,
+                           bool qlim = false) {
     const pf::Plan& P = h->plan;
     pf::SlotLayout L{};
     L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
@@ -144,6 +146,10 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int place
     if (vec_global) {
         L.off_vec = o;
         o = pf::align_up(o + vec_global, 256);
+    }
+    if (qlim) {  // per-scenario partition: int8 type per bus, then FP64 fixed qg per bus
+        L.off_qlim = o;
+        o = pf::align_up(o + pf::align_up((size_t)P.n_bus, 16) + sizeof(double) * (size_t)P.n_bus, 256);
     }
     L.slot_bytes = o;
     return L;
@@ -189,6 +195,121 @@ size_t push(std::vector<unsigned char>& buf, const std::vector<T>& v) {
     buf.resize(off + sizeof(T) * v.size());
     if (!v.empty()) std::memcpy(buf.data() + off, v.data(), sizeof(T) * v.size());
     return off;
+}
+
+}  // namespace
+
+namespace {
+
+// Every plan array packed into one buffer (one device allocation per network).
+struct PlanOffsets {
+    size_t ygb, ytgb, ygb32, yptr, yidx, ytptr, ytidx, bt, p2b, b2p, lev, lup, lur, luc, lud,
+        lum, fy, lap, la, stp, stg, scp, sch, levg, j1pos, j1ptr, j1col;
+};
+
+void pack_plan(const pf::Plan& P, std::vector<unsigned char>& buf, PlanOffsets& o) {
+    std::vector<double2> ygb(P.y_g.size()), ytgb(P.yt_g.size());
+    std::vector<float2> ygb32(P.y_g.size());
+    for (size_t k = 0; k < P.y_g.size(); ++k) {
+        ygb[k] = make_double2(P.y_g[k], P.y_b[k]);
+        ygb32[k] = make_float2((float)P.y_g[k], (float)P.y_b[k]);
+    }
+    for (size_t k = 0; k < P.yt_g.size(); ++k) ytgb[k] = make_double2(P.yt_g[k], P.yt_b[k]);
+    std::vector<int2> la(P.la_L.size()), sch(P.sch_L.size());
+    std::vector<int4> levg(P.n_levels), j1pos(P.y_idx.size());
+    for (int l = 0; l < P.n_levels; ++l) levg[l] = make_int4(P.lev_gL[l], P.lev_gU[l], P.lev_gS[l], 0);
+    for (size_t k = 0; k < la.size(); ++k) la[k] = make_int2(P.la_L[k], P.la_D[k]);
+    for (size_t k = 0; k < sch.size(); ++k) sch[k] = make_int2(P.sch_L[k], P.sch_U[k]);
+    for (size_t k = 0; k < j1pos.size(); ++k)
+        j1pos[k] = make_int4(P.j1_pos[4 * k], P.j1_pos[4 * k + 1], P.j1_pos[4 * k + 2],
+                             P.j1_pos[4 * k + 3]);
+    o.ygb = push(buf, ygb), o.ytgb = push(buf, ytgb), o.ygb32 = push(buf, ygb32);
+    o.yptr = push(buf, P.y_ptr), o.yidx = push(buf, P.y_idx);
+    o.ytptr = push(buf, P.yt_ptr), o.ytidx = push(buf, P.yt_idx);
+    o.bt = push(buf, P.bus_type), o.p2b = push(buf, P.pos2bus), o.b2p = push(buf, P.bus2pos);
+    o.lev = push(buf, P.lev_ptr), o.lup = push(buf, P.lu_ptr), o.lur = push(buf, P.lu_row);
+    o.luc = push(buf, P.lu_col), o.lud = push(buf, P.lu_diag), o.lum = push(buf, P.lu_mirror);
+    o.fy = push(buf, P.fill_y), o.lap = push(buf, P.la_ptr), o.la = push(buf, la);
+    o.stp = push(buf, P.sch_tptr), o.stg = push(buf, P.sch_tgt), o.scp = push(buf, P.sch_cptr);
+    o.sch = push(buf, sch), o.levg = push(buf, levg), o.j1pos = push(buf, j1pos);
+    o.j1ptr = push(buf, P.j1_ptr), o.j1col = push(buf, P.j1_col);
+}
+
+// Reactive-limit inputs of pf_solve_qlim (null for pf_solve).
+struct QlimIn {
+    const double* Qmin;
+    const double* Qmax;
+    int max_rounds;
+    int* types_out;
+    int* rounds_out;
+};
+
+pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
+                  const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
+                  double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
+                  double* final_mismatch, void* workspace, size_t workspace_bytes, void* stream,
+                  const QlimIn* q) {
+    if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
+        return PF_EINVAL;
+    if (!(tol > 0.0) || max_iter < 0 || !opts_ok(opts)) return PF_EINVAL;
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    LaunchCfg cfg = resolve(h, opts);
+    if (q) cfg.ipc = 1;  // reactive limits: one CTA per scenario (32 threads if tuned to warps)
+    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, cfg.placement, q != nullptr);
+    if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
+    const int threads = cfg.threads;
+    if (cfg.ipc > 1 && L.fwd.smem_bytes * (size_t)cfg.ipc > smem_budget(h)) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    pf::SolveArgs A{};
+    A.batch = batch;
+    A.ipc = cfg.ipc;
+    A.tol = tol;
+    A.max_iter = max_iter;
+    A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
+    A.ir_rtol = opts->ir_rtol;
+    A.ir_gate = opts->ir_gate;
+    A.keep_factors = opts->keep_factors ? 1 : 0;
+    A.Pd = Pd;
+    A.Qd = Qd;
+    A.Pg = Pg;
+    A.Vset = Vset;
+    A.Vm = Vm;
+    A.Va = Va;
+    A.Pg_out = Pg_out;
+    A.Qg_out = Qg_out;
+    A.fmis = final_mismatch;
+    A.iters = iters;
+    A.status = status;
+    A.ws = static_cast<char*>(workspace);
+    A.L = L;
+    if (q) {
+        A.Qmin = q->Qmin;
+        A.Qmax = q->Qmax;
+        A.max_rounds = q->max_rounds;
+        A.types_out = q->types_out;
+        A.rounds_out = q->rounds_out;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (q)  // one CTA per scenario: the warp-per-scenario form has no reactive-limit variant
+        e = ft == 4 ? pf::launch_solve_qlim<float>(h->dp, A, threads, s)
+                    : pf::launch_solve_qlim<double>(h->dp, A, threads, s);
+    else
+        e = ft == 4 ? pf::launch_solve<float>(h->dp, A, threads, s)
+                    : pf::launch_solve<double>(h->dp, A, threads, s);
+    if (e != cudaSuccess) {
+        h->last_batch = -1;
+        return PF_ECUDA;
+    }
+    // a solve under reactive limits leaves no state for pf_adjoint (keep_factors is 0)
+    h->last_batch = batch;
+    h->last_ft = ft;
+    h->last_keep = A.keep_factors;
+    h->last_threads = threads;
+    h->last_ws = workspace;
+    h->last_layout = L;
+    return PF_OK;
 }
 
 }  // namespace
@@ -278,29 +399,9 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
         delete h;
         return PF_ECUDA;
     }
-    // pack every plan array into one device buffer
     std::vector<unsigned char> buf;
-    std::vector<double2> ygb(P.y_g.size()), ytgb(P.yt_g.size());
-    std::vector<float2> ygb32(P.y_g.size());
-    for (size_t k = 0; k < P.y_g.size(); ++k) {
-        ygb[k] = make_double2(P.y_g[k], P.y_b[k]);
-        ygb32[k] = make_float2((float)P.y_g[k], (float)P.y_b[k]);
-    }
-    for (size_t k = 0; k < P.yt_g.size(); ++k) ytgb[k] = make_double2(P.yt_g[k], P.yt_b[k]);
-    std::vector<int2> la(P.la_L.size()), sch(P.sch_L.size());
-    std::vector<int4> levg(P.n_levels);
-    for (int l = 0; l < P.n_levels; ++l) levg[l] = make_int4(P.lev_gL[l], P.lev_gU[l], P.lev_gS[l], 0);
-    for (size_t k = 0; k < la.size(); ++k) la[k] = make_int2(P.la_L[k], P.la_D[k]);
-    for (size_t k = 0; k < sch.size(); ++k) sch[k] = make_int2(P.sch_L[k], P.sch_U[k]);
-    size_t o_ygb = push(buf, ygb), o_ytgb = push(buf, ytgb), o_ygb32 = push(buf, ygb32);
-    size_t o_yptr = push(buf, P.y_ptr), o_yidx = push(buf, P.y_idx);
-    size_t o_ytptr = push(buf, P.yt_ptr), o_ytidx = push(buf, P.yt_idx);
-    size_t o_bt = push(buf, P.bus_type), o_p2b = push(buf, P.pos2bus), o_b2p = push(buf, P.bus2pos);
-    size_t o_lev = push(buf, P.lev_ptr), o_lup = push(buf, P.lu_ptr), o_lur = push(buf, P.lu_row);
-    size_t o_luc = push(buf, P.lu_col), o_lud = push(buf, P.lu_diag), o_lum = push(buf, P.lu_mirror);
-    size_t o_fy = push(buf, P.fill_y), o_lap = push(buf, P.la_ptr), o_la = push(buf, la);
-    size_t o_stp = push(buf, P.sch_tptr), o_stg = push(buf, P.sch_tgt), o_scp = push(buf, P.sch_cptr);
-    size_t o_sch = push(buf, sch), o_levg = push(buf, levg);
+    PlanOffsets po;
+    pack_plan(P, buf, po);
     if (buf.empty()) buf.resize(16);
     if (cudaMalloc(&h->d_buf, buf.size()) != cudaSuccess) {
         delete h;
@@ -311,6 +412,7 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
         delete h;
         return PF_ECUDA;
     }
+    h->plan_bytes = buf.size();
     auto* base = static_cast<unsigned char*>(h->d_buf);
     auto I = [&](size_t o) { return reinterpret_cast<const int*>(base + o); };
     pf::DevPlan& d = h->dp;
@@ -318,35 +420,40 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     d.n = P.n;
     d.nnzb = P.nnzb();
     d.n_levels = P.n_levels;
-    d.y_ptr = I(o_yptr);
-    d.y_idx = I(o_yidx);
-    d.y_gb = reinterpret_cast<const double2*>(base + o_ygb);
-    d.y_gb32 = reinterpret_cast<const float2*>(base + o_ygb32);
-    d.yt_ptr = I(o_ytptr);
-    d.yt_idx = I(o_ytidx);
-    d.yt_gb = reinterpret_cast<const double2*>(base + o_ytgb);
-    d.bus_type = I(o_bt);
-    d.pos2bus = I(o_p2b);
-    d.bus2pos = I(o_b2p);
-    d.lev_ptr = I(o_lev);
-    d.lev_g = reinterpret_cast<const int4*>(base + o_levg);
-    d.lu_ptr = I(o_lup);
-    d.lu_row = I(o_lur);
-    d.lu_col = I(o_luc);
-    d.lu_diag = I(o_lud);
-    d.lu_mirror = I(o_lum);
-    d.fill_y = I(o_fy);
-    d.la_ptr = I(o_lap);
-    d.la = reinterpret_cast<const int2*>(base + o_la);
-    d.sch_tptr = I(o_stp);
-    d.sch_tgt = I(o_stg);
-    d.sch_cptr = I(o_scp);
-    d.sch = reinterpret_cast<const int2*>(base + o_sch);
+    d.y_ptr = I(po.yptr);
+    d.y_idx = I(po.yidx);
+    d.y_gb = reinterpret_cast<const double2*>(base + po.ygb);
+    d.y_gb32 = reinterpret_cast<const float2*>(base + po.ygb32);
+    d.yt_ptr = I(po.ytptr);
+    d.yt_idx = I(po.ytidx);
+    d.yt_gb = reinterpret_cast<const double2*>(base + po.ytgb);
+    d.bus_type = I(po.bt);
+    d.pos2bus = I(po.p2b);
+    d.bus2pos = I(po.b2p);
+    d.lev_ptr = I(po.lev);
+    d.lev_g = reinterpret_cast<const int4*>(base + po.levg);
+    d.lu_ptr = I(po.lup);
+    d.lu_row = I(po.lur);
+    d.lu_col = I(po.luc);
+    d.lu_diag = I(po.lud);
+    d.lu_mirror = I(po.lum);
+    d.fill_y = I(po.fy);
+    d.la_ptr = I(po.lap);
+    d.la = reinterpret_cast<const int2*>(base + po.la);
+    d.sch_tptr = I(po.stp);
+    d.sch_tgt = I(po.stg);
+    d.sch_cptr = I(po.scp);
+    d.sch = reinterpret_cast<const int2*>(base + po.sch);
+    d.n1 = P.n1;
+    d.nnz_j1 = P.nnz_j1;
+    d.j1_pos = reinterpret_cast<const int4*>(base + po.j1pos);
+    d.j1_ptr = I(po.j1ptr);
+    d.j1_col = I(po.j1col);
     *out = h;
     return PF_OK;
 }
 
-static void fill_info(const pf::Plan& P, pf_plan_info* info) {
+static void fill_info(const pf::Plan& P, size_t plan_bytes, pf_plan_info* info) {
     info->n_bus = P.n_bus;
     info->n_slack = P.n_slack;
     info->n_pv = P.n_pv;
@@ -358,22 +465,53 @@ static void fill_info(const pf::Plan& P, pf_plan_info* info) {
     info->nnzb_lu = P.nnzb();
     info->n_levels = P.n_levels;
     info->schur_block_ops = P.schur_ops;
+    info->plan_bytes = (long long)plan_bytes;
 }
 
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info) {
     if (!h || !info) return PF_EINVAL;
-    fill_info(h->plan, info);
+    fill_info(h->plan, h->plan_bytes, info);
     return PF_OK;
+}
+
+pf_err pf_jacobian_pattern(const pf_handle* h, int* j1_ptr, int* j1_col) {
+    if (!h || !j1_ptr || !j1_col) return PF_EINVAL;
+    std::copy(h->plan.j1_ptr.begin(), h->plan.j1_ptr.end(), j1_ptr);
+    std::copy(h->plan.j1_col.begin(), h->plan.j1_col.end(), j1_col);
+    return PF_OK;
+}
+
+pf_err pf_bde_pattern(const pf_handle* h, int batch, int* row_ptr, int* col_idx, void* stream) {
+    if (!h || batch < 1 || !row_ptr || !col_idx) return PF_EINVAL;
+    if ((long long)batch * h->plan.nnz_j1 >= (1LL << 31) ||
+        (long long)batch * h->plan.n1 >= (1LL << 31)) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    return pf::launch_bde_pattern(h->dp, batch, row_ptr, col_idx, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+pf_err pf_export_jacobian(const pf_handle* h, int batch, const double* Vm, const double* Va,
+                          double* values, void* stream) {
+    if (!h || batch < 1 || !Vm || !Va || !values) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    return pf::launch_export_jacobian(h->dp, batch, Vm, Va, values,
+                                      static_cast<cudaStream_t>(stream)) == cudaSuccess ? PF_OK
+                                                                                        : PF_ECUDA;
 }
 
 pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
                   const double* y_im, const int* bus_type, pf_plan_info* info, int* pos2bus,
-                  int* lu_ptr, int* lu_col, int* lev_ptr) {
+                  int* lu_ptr, int* lu_col, int* lev_ptr, int* j1_ptr, int* j1_col) {
     if (!info) return PF_EINVAL;
     pf::Plan P;
     pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, P);
     if (bs != pf::BUILD_OK) return bs == pf::BUILD_ESINGULAR ? PF_ESINGULAR_PATTERN : PF_EINVAL;
-    fill_info(P, info);
+    std::vector<unsigned char> buf;
+    PlanOffsets po;
+    pack_plan(P, buf, po);
+    fill_info(P, buf.size(), info);
+    if (j1_ptr) std::copy(P.j1_ptr.begin(), P.j1_ptr.end(), j1_ptr);
+    if (j1_col) std::copy(P.j1_col.begin(), P.j1_col.end(), j1_col);
     if (pos2bus) std::copy(P.pos2bus.begin(), P.pos2bus.end(), pos2bus);
     if (lu_ptr) std::copy(P.lu_ptr.begin(), P.lu_ptr.end(), lu_ptr);
     if (lu_col) std::copy(P.lu_col.begin(), P.lu_col.end(), lu_col);
@@ -393,53 +531,28 @@ pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, con
                 const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
                 double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
                 double* final_mismatch, void* workspace, size_t workspace_bytes, void* stream) {
-    if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
-        return PF_EINVAL;
-    if (!(tol > 0.0) || max_iter < 0 || !opts_ok(opts)) return PF_EINVAL;
+    return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
+                      iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr);
+}
+
+pf_err pf_qlim_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts,
+                              size_t* bytes) {
+    if (!h || !bytes || batch < 1 || !opts_ok(opts) || opts->keep_factors) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    const LaunchCfg cfg = resolve(h, opts);
-    pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, cfg.placement);
-    if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
-    if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
-    const int threads = cfg.threads;
-    if (cfg.ipc > 1 && L.fwd.smem_bytes * (size_t)cfg.ipc > smem_budget(h)) return PF_EINVAL;
-    DeviceGuard guard(h->device);
-    pf::SolveArgs A{};
-    A.batch = batch;
-    A.ipc = cfg.ipc;
-    A.tol = tol;
-    A.max_iter = max_iter;
-    A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
-    A.ir_rtol = opts->ir_rtol;
-    A.ir_gate = opts->ir_gate;
-    A.keep_factors = opts->keep_factors ? 1 : 0;
-    A.Pd = Pd;
-    A.Qd = Qd;
-    A.Pg = Pg;
-    A.Vset = Vset;
-    A.Vm = Vm;
-    A.Va = Va;
-    A.Pg_out = Pg_out;
-    A.Qg_out = Qg_out;
-    A.fmis = final_mismatch;
-    A.iters = iters;
-    A.status = status;
-    A.ws = static_cast<char*>(workspace);
-    A.L = L;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = ft == 4 ? pf::launch_solve<float>(h->dp, A, threads, s)
-                            : pf::launch_solve<double>(h->dp, A, threads, s);
-    if (e != cudaSuccess) {
-        h->last_batch = -1;
-        return PF_ECUDA;
-    }
-    h->last_batch = batch;
-    h->last_ft = ft;
-    h->last_keep = A.keep_factors;
-    h->last_threads = threads;
-    h->last_ws = workspace;
-    h->last_layout = L;
+    *bytes = make_layout(h, ft, 0, resolve(h, opts).placement, true).slot_bytes * (size_t)batch;
     return PF_OK;
+}
+
+pf_err pf_solve_qlim(pf_handle* h, int batch, const double* Pd, const double* Qd,
+                     const double* Pg, const double* Vset, const double* Qmin, const double* Qmax,
+                     double tol, int max_iter, int max_rounds, const pf_solve_opts* opts,
+                     double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters,
+                     int* status, double* final_mismatch, int* bus_type_out, int* rounds,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+    if (!Qmin || !Qmax || max_rounds < 0 || !opts || opts->keep_factors) return PF_EINVAL;
+    QlimIn q{Qmin, Qmax, max_rounds, bus_type_out, rounds};
+    return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
+                      iters, status, final_mismatch, workspace, workspace_bytes, stream, &q);
 }
 
 pf_err pf_adjoint(pf_handle* h, int batch, const double* dVm, const double* dVa, const double* dPg,

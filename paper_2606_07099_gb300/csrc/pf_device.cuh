@@ -33,6 +33,10 @@ struct DevPlan {
     const int* yt_ptr;    // transpose of Ybus (column access for the adjoint products)
     const int* yt_idx;
     const double2* yt_gb;
+    int n1, nnz_j1;       // scalar J1 template (block-diagonal export)
+    const int* j1_ptr;    // its CSR in the paper's ordering
+    const int* j1_col;
+    const int4* j1_pos;   // per Ybus entry: positions of (dP/dtheta, dP/dVm, dQ/dtheta, dQ/dVm)
 };
 
 // Where one kernel keeps the scenario's vectors and factor (shared or global memory).
@@ -53,6 +57,8 @@ struct SlotLayout {
     size_t off_flags;   // int status, iters, has_factor, pad
     size_t off_fac;     // factor values (if stored in global memory), or 0
     size_t off_vec;     // vector arena (if a kernel keeps it in global memory), or 0
+    size_t off_qlim;    // reactive-limit state (pf_solve_qlim): int8 type[n_bus], then
+                        // double qfix[n_bus] at off_qlim + align16(n_bus); 0 = none
     int fac_global;     // factor region present in the slot
     size_t fac_bytes;
     KernelSmem fwd, adj;
@@ -80,6 +86,12 @@ struct SolveArgs {
     int* status;
     char* ws;
     SlotLayout L;
+    // reactive limits at PV buses (pf_solve_qlim); Qmax == nullptr: no limits
+    const double* Qmin;
+    const double* Qmax;
+    int max_rounds;
+    int* types_out;
+    int* rounds_out;
 };
 
 // Several networks in one launch (pf_solve_multi): per job its plan and solve arguments,
@@ -123,6 +135,10 @@ struct Arrays {
     // FP32 copies per bus feeding the FP32 Jacobian fill: V, u, Vm and u conj(I)
     float *fvr, *fvi, *fur, *fui, *fvm, *fpu, *fqu;
     void* x;  // FT[2n], the triangular-solve vector
+    // per-scenario partition under reactive limits (null without limits): the current
+    // bus type and, for PV buses switched to PQ, the reactive generation fixed at the limit
+    signed char* stype;
+    double* qfix;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -166,6 +182,8 @@ __host__ __device__ inline size_t carve(unsigned char* base, int n_bus, int n, i
         a->Psp = a->Qsp = a->w0 = a->w1 = a->gV = a->r = nullptr;
     }
     a->x = take((size_t)ft_bytes * 2 * n);
+    a->stype = nullptr;
+    a->qfix = nullptr;
     return o;
 }
 

@@ -1,824 +1,15 @@
-// pf_kernels.cu -- the batched Newton-Raphson power flow and its adjoint on sm_103a.
-//
-// One CTA owns one scenario at a time (the grid has one CTA per scenario, so the
-// hardware block scheduler balances scenarios that need different iteration
-// counts).  Every step of a Newton iteration runs inside the same kernel, on the
-// scenario's state staged in shared memory when it fits:
-//
-//   mismatch  I = Y V, S = V conj(I), F1 = spec - S           (Sec. II-A, FP64)
-//   fill      polar 2x2 Jacobian blocks on the fixed pattern  (Alg. 1 values, FT)
-//   factor    level-scheduled right-looking 2x2-block LU      (FT = float | double)
-//   solve     level-scheduled block triangular sweeps         (FT)
-//   refine    FP64 residual r = -F1 - J1 dz (matrix-free)     (Table I + refinement)
-//   update    theta_{B\R} += dtheta, Vm_D += dVm, u and V     (FP64)
-//
-// until ||F1||_inf <= tol; then Step 2 (Eq. F2_completion) writes the recovered
-// generation.  The convergence decision is taken on the device per scenario;
-// the host never waits inside the loop.
-#include <cfloat>
-#include <cmath>
+// pf_kernels.cu -- kernel instantiations and launchers of libpf (sm_103a): the Newton
+// solve, the multi-network solve, the adjoint and the block-diagonal export.  The device
+// code itself is in pf_body.cuh; pf_qlim.cu instantiates the reactive-limit solve.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
 
-#include "pf_device.cuh"
+#include "pf_body.cuh"
+#include "pf_launch.h"
 
 namespace pf {
-
-// ---------------------------------------------------------------- small helpers
-template <typename T>
-struct Blk {
-    T a, b, c, d;  // [[a, b], [c, d]]: rows (dP, dQ), columns (theta, Vm)
-};
-
-__device__ __forceinline__ Blk<float> ldb(const float* f, int e) {
-    float4 v = reinterpret_cast<const float4*>(f)[e];
-    return {v.x, v.y, v.z, v.w};
-}
-__device__ __forceinline__ Blk<double> ldb(const double* f, int e) {
-    const double2* p = reinterpret_cast<const double2*>(f) + 2 * e;
-    double2 u = p[0], w = p[1];
-    return {u.x, u.y, w.x, w.y};
-}
-__device__ __forceinline__ void stb(float* f, int e, Blk<float> v) {
-    reinterpret_cast<float4*>(f)[e] = make_float4(v.a, v.b, v.c, v.d);
-}
-__device__ __forceinline__ void stb(double* f, int e, Blk<double> v) {
-    double2* p = reinterpret_cast<double2*>(f) + 2 * e;
-    p[0] = make_double2(v.a, v.b);
-    p[1] = make_double2(v.c, v.d);
-}
-template <typename T>
-__device__ __forceinline__ Blk<T> mul(Blk<T> x, Blk<T> y) {
-    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c,
-            x.c * y.b + x.d * y.d};
-}
-// x - y*z
-template <typename T>
-__device__ __forceinline__ Blk<T> msub(Blk<T> x, Blk<T> y, Blk<T> z) {
-    return {x.a - (y.a * z.a + y.b * z.c), x.b - (y.a * z.b + y.b * z.d),
-            x.c - (y.c * z.a + y.d * z.c), x.d - (y.c * z.b + y.d * z.d)};
-}
-// inverse of a 2x2 block; *bad = 1 if (numerically) singular or non-finite
-template <typename T>
-__device__ __forceinline__ Blk<T> inv2(Blk<T> m, int* bad) {
-    T det = m.a * m.d - m.b * m.c;
-    T amax = fmax(fmax(fabs(m.a), fabs(m.b)), fmax(fabs(m.c), fabs(m.d)));
-    if (!(fabs(det) > T(1e-30) * amax * amax) || !(amax < T(INFINITY))) *bad = 1;
-    T r = T(1) / det;
-    return {m.d * r, -m.b * r, -m.c * r, m.a * r};
-}
-
-template <typename T>
-__device__ __forceinline__ T* ftptr(void* p) { return reinterpret_cast<T*>(p); }
-
-// A "group" solves one scenario: either the whole CTA (W = false) or one warp of it
-// (W = true: several independent scenarios per CTA, one per warp).  GTID / GSZ are the
-// thread's rank and the size of its group; gsync<W> is the group barrier.
-#define GTID (W ? (int)(threadIdx.x & 31u) : (int)threadIdx.x)
-#define GSZ (W ? 32 : (int)blockDim.x)
-
-template <bool W>
-__device__ __forceinline__ void gsync() {
-    if (W || blockDim.x == 32) __syncwarp();
-    else __syncthreads();
-}
-
-// |v| with non-finite values mapped to +inf (so that max-reductions see them)
-__device__ __forceinline__ double absinf(double v) {
-    double a = fabs(v);
-    return (a <= DBL_MAX) ? a : INFINITY;
-}
-
-// Group-wide max; every thread gets the result.  `red` holds one double per warp.
-template <bool W>
-__device__ double group_max(double v, double* red) {
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (W || blockDim.x == 32) {
-        __syncwarp();  // also orders the shared-memory writes of the phase that reduced
-        return v;
-    }
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double r = red[0];
-    for (int i = 1; i < nw; ++i) r = fmax(r, red[i]);
-    return r;
-}
-
-// ---------------------------------------------------------------- FP64 network kernels
-// u = e^{j theta}, V = Vm u
-template <bool W>
-__device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        double s, c;
-        sincos(a.Va[i], &s, &c);
-        a.Uc[i] = c;
-        a.Us[i] = s;
-        a.Vre[i] = a.Vm[i] * c;
-        a.Vim[i] = a.Vm[i] * s;
-    }
-}
-
-// e^{j d} for a Newton angle step |d| <= 1/8 from the Maclaurin series of sin and cos,
-// truncated after d^9 and d^10: the first omitted terms are below 3e-18 relative.
-// (Horner form; the factors are 1/(k(k+1)) of consecutive terms, as products so that no
-// division is emitted.)
-__device__ __forceinline__ void small_angle_phasor(double d, double* c, double* s) {
-    const double d2 = d * d;
-    *s = d * (1.0 - d2 * (1.0 / 6.0) *
-                        (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
-    *c = 1.0 - d2 * 0.5 *
-                   (1.0 - d2 * (1.0 / 12.0) *
-                              (1.0 - d2 * (1.0 / 30.0) * (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
-}
-
-// Newton update of one bus (FP64) that also advances u = e^{j theta} and V = Vm u: small
-// angle steps rotate u by e^{j dth}; larger ones recompute it from theta.
-__device__ __forceinline__ void update_bus(const Arrays& a, int i, double dth, double dvm, bool pq) {
-    const double th = a.Va[i] + dth;
-    a.Va[i] = th;
-    const double vm = pq ? a.Vm[i] + dvm : a.Vm[i];
-    a.Vm[i] = vm;
-    double c, s;
-    if (fabs(dth) <= 0.125) {
-        double rc, rs;
-        small_angle_phasor(dth, &rc, &rs);
-        const double uc = a.Uc[i], us = a.Us[i];
-        c = uc * rc - us * rs;
-        s = us * rc + uc * rs;
-    } else {
-        sincos(th, &s, &c);
-    }
-    a.Uc[i] = c;
-    a.Us[i] = s;
-    a.Vre[i] = vm * c;
-    a.Vim[i] = vm * s;
-}
-
-// FP32 copies of the per-bus quantities the FP32 Jacobian fill reads:
-// V, u, Vm and (pu, qu) = u conj(I), so that S = Vm (pu + j qu).
-__device__ __forceinline__ void store_bus_f32(const Arrays& a, int i, double ir, double ii) {
-    const double c = a.Uc[i], s = a.Us[i];
-    a.fvr[i] = float(a.Vre[i]);
-    a.fvi[i] = float(a.Vim[i]);
-    a.fur[i] = float(c);
-    a.fui[i] = float(s);
-    a.fvm[i] = float(a.Vm[i]);
-    a.fpu[i] = float(c * ir + s * ii);
-    a.fqu[i] = float(s * ir - c * ii);
-}
-
-// I = Y V, S = V conj(I), F1 at pivot positions; returns ||F1||_inf (inf if non-finite).
-// The specified injections P_spec = pg - pd (pg on PV buses only) and Q_spec = -qd are
-// read from the scenario's input rows.  With F32COPY the FP32 per-bus copies for the
-// FP32 Jacobian fill are written too.
-template <bool F32COPY, bool W>
-__device__ double phase_mismatch(const DevPlan& P, const Arrays& a, const double* Pd,
-                                 const double* Qd, const double* Pg, double* red) {
-    double lmax = 0.0;
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        double ir = 0.0, ii = 0.0;
-        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
-            const int j = __ldg(P.y_idx + k);
-            const double2 y = __ldg(P.y_gb + k);
-            const double vr = a.Vre[j], vi = a.Vim[j];
-            ir = fma(y.x, vr, fma(-y.y, vi, ir));
-            ii = fma(y.x, vi, fma(y.y, vr, ii));
-        }
-        a.Ire[i] = ir;
-        a.Iim[i] = ii;
-        if (F32COPY) store_bus_f32(a, i, ir, ii);
-        const int p = __ldg(P.bus2pos + i);
-        if (p >= 0) {
-            const double vr = a.Vre[i], vi = a.Vim[i];
-            const double Pi = vr * ir + vi * ii;
-            const double Qi = vi * ir - vr * ii;
-            const int t = __ldg(P.bus_type + i);
-            const double psp = (t == 1 ? __ldg(Pg + i) : 0.0) - __ldg(Pd + i);
-            const double fP = psp - Pi;
-            const double fQ = (t == 0) ? -__ldg(Qd + i) - Qi : 0.0;
-            a.F[2 * p] = fP;
-            a.F[2 * p + 1] = fQ;
-            lmax = fmax(lmax, fmax(absinf(fP), absinf(fQ)));
-        }
-    }
-    return group_max<W>(lmax, red);
-}
-
-// G_j = conj(m_j I_j) + sum_i m_i conj(V_i) Y_ij;  w0_j = Re(G_j u_j) = d(m.S)/dVm_j,
-// w1_j = -Im(G_j V_j) = d(m.S)/dtheta_j, for the injection weights m = mP + j mQ held in
-// (Psp, Qsp).  This is (d[P;Q]/d[Vm;theta])^T [mP; mQ] without forming the Jacobian.
-template <bool W>
-__device__ void phase_jvt(const DevPlan& P, const Arrays& a) {
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        const double mr = a.Psp[i], mi = a.Qsp[i];
-        // h = m conj(V)
-        a.dVre[i] = mr * a.Vre[i] + mi * a.Vim[i];
-        a.dVim[i] = mi * a.Vre[i] - mr * a.Vim[i];
-    }
-    gsync<W>();
-    for (int j = GTID; j < P.n_bus; j += GSZ) {
-        double gr = 0.0, gi = 0.0;
-        for (int k = __ldg(P.yt_ptr + j); k < __ldg(P.yt_ptr + (j + 1)); ++k) {
-            const int i = __ldg(P.yt_idx + k);
-            const double2 y = __ldg(P.yt_gb + k);  // Y_ij
-            const double hr = a.dVre[i], hi = a.dVim[i];
-            gr = fma(hr, y.x, fma(-hi, y.y, gr));
-            gi = fma(hr, y.y, fma(hi, y.x, gi));
-        }
-        const double mr = a.Psp[j], mi = a.Qsp[j];
-        const double Ir = a.Ire[j], Ii = a.Iim[j];
-        gr += mr * Ir - mi * Ii;      // conj(m I) = (mr Ir - mi Ii) - j(mr Ii + mi Ir)
-        gi -= mr * Ii + mi * Ir;
-        const double vr = a.Vre[j], vi = a.Vim[j];
-        a.w0[j] = gr * a.Uc[j] - gi * a.Us[j];
-        a.w1[j] = -(gr * vi + gi * vr);
-    }
-}
-
-// ---------------------------------------------------------------- Jacobian fill (Alg. 1)
-// J1 = dF1/dz1 in 2x2 blocks; F = spec - S, so every entry is minus the derivative of
-// the calculated injection.  With u = e^{j theta}, W = V_i conj(Y_ij V_j) and
-// W' = V_i conj(Y_ij u_j) = W / Vm_j (i != j):
-//   dP_i/dtheta_j = Im W, dQ_i/dtheta_j = -Re W, dP_i/dVm_j = Re W', dQ_i/dVm_j = Im W';
-// on the diagonal, with pu + j qu = u_i conj(I_i) (so P_i + j Q_i = Vm_i (pu + j qu)):
-//   dP_i/dtheta_i = -Q_i - B_ii Vm_i^2, dQ_i/dtheta_i = P_i - G_ii Vm_i^2,
-//   dP_i/dVm_i = pu + G_ii Vm_i,        dQ_i/dVm_i = qu - B_ii Vm_i.
-// The values are the same as Alg. 1's; they are computed in the precision of the
-// factor they feed (FP32 from FP32 copies of the bus quantities, or FP64).
-template <typename T>
-__device__ __forceinline__ Blk<T> jac_block(bool diag, T gij, T bij, T vri, T vii, T urj, T uij,
-                                            T vmj, T vmi, T pui, T qui) {
-    if (diag) {
-        const T vm2 = vmi * vmi;
-        return {vmi * qui + bij * vm2, -(pui + gij * vmi), -vmi * pui + gij * vm2,
-                -(qui - bij * vmi)};
-    }
-    const T yur = gij * urj - bij * uij, yui = gij * uij + bij * urj;  // Y_ij u_j
-    const T wr = vri * yur + vii * yui;                                 // W' = V_i conj(Y_ij u_j)
-    const T wi = vii * yur - vri * yui;
-    return {-wi * vmj, -wr, wr * vmj, -wi};
-}
-
-template <typename T>
-__device__ __forceinline__ Blk<T> pad_pv(Blk<T> m, bool diag, int ti, int tj) {
-    // PV buses: no dQ row and no Vm column; padded with the identity equation dVm_i = 0
-    if (ti == 1) { m.c = T(0); m.d = T(0); }
-    if (tj == 1) { m.b = T(0); m.d = T(0); }
-    if (diag && ti == 1) m.d = T(1);
-    return m;
-}
-
-template <bool W>
-__device__ void phase_fill(const DevPlan& P, const Arrays& a, float* fac) {
-    for (int e = GTID; e < P.nnzb; e += GSZ) {
-        const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
-        const int yi = __ldg(P.fill_y + e);
-        const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
-        Blk<float> m{0.f, 0.f, 0.f, 0.f};
-        if (yi >= 0) {
-            const float2 y = __ldg(P.y_gb32 + yi);
-            m = jac_block<float>(p == q, y.x, y.y, a.fvr[i], a.fvi[i], a.fur[j], a.fui[j],
-                                 a.fvm[j], a.fvm[i], a.fpu[i], a.fqu[i]);
-        }
-        stb(fac, e, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
-    }
-}
-
-template <bool W>
-__device__ void phase_fill(const DevPlan& P, const Arrays& a, double* fac) {
-    for (int e = GTID; e < P.nnzb; e += GSZ) {
-        const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
-        const int yi = __ldg(P.fill_y + e);
-        const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
-        Blk<double> m{0.0, 0.0, 0.0, 0.0};
-        if (yi >= 0) {
-            const double2 y = __ldg(P.y_gb + yi);
-            const double c = a.Uc[i], s = a.Us[i], ir = a.Ire[i], ii = a.Iim[i];
-            m = jac_block<double>(p == q, y.x, y.y, a.Vre[i], a.Vim[i], a.Uc[j], a.Us[j],
-                                  a.Vm[j], a.Vm[i], c * ir + s * ii, s * ir - c * ii);
-        }
-        stb(fac, e, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
-    }
-}
-
-// ---------------------------------------------------------------- block LU
-// Gathers (one row of a triangular sweep, or the Schur updates of one target block) run
-// on one thread; their indices and operands are loaded kBatch at a time before any
-// arithmetic, so the loads of a gather overlap instead of forming one long chain (four
-// FP32 blocks, or two FP64 blocks to stay within the register budget).  The summation
-// order depends only on the plan, so results do not depend on blockDim.
-template <typename FT>
-constexpr int kBatch = sizeof(FT) == 4 ? 4 : 2;
-
-// Right-looking, one elimination-tree level at a time.  Phase A scales the L columns of
-// the level's pivots; phase B gathers every Schur update of the level into its target
-// block (no two threads write the same block) and replaces the level's pivot blocks by
-// their inverses.  (A variant with one barrier per level, recomputing L(i,k) inside each
-// Schur update, measured slower: the extra 2x2 inverse per update costs more than the
-// barrier it saves.)  Returns nonzero if a pivot was singular.
-template <typename FT, bool W>
-__device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
-    int bad = 0;
-    if (!W && threadIdx.x == 0) *s_bad = 0;
-    for (int l = 0; l < P.n_levels; ++l) {
-        const int a0 = __ldg(P.la_ptr + l), a1 = __ldg(P.la_ptr + l + 1);
-        for (int c = a0 + GTID; c < a1; c += GSZ) {
-            const int2 ld = __ldg(P.la + c);
-            int dummy = 0;
-            stb(fac, ld.x, mul(ldb(fac, ld.x), inv2(ldb(fac, ld.y), &dummy)));
-        }
-        gsync<W>();
-        const int t0 = __ldg(P.sch_tptr + l), t1 = __ldg(P.sch_tptr + l + 1);
-        for (int t = t0 + GTID; t < t1; t += GSZ) {
-            const int c0 = __ldg(P.sch_cptr + t), c1 = __ldg(P.sch_cptr + t + 1);
-            Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
-            constexpr int NB = kBatch<FT>;
-            for (int c = c0; c < c1; c += NB) {
-                int2 lu[NB];
-#pragma unroll
-                for (int k = 0; k < NB; ++k) lu[k] = (c + k < c1) ? __ldg(P.sch + c + k) : make_int2(-1, -1);
-                Blk<FT> xl[NB], yu[NB];
-#pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    if (lu[k].x >= 0) {
-                        xl[k] = ldb(fac, lu[k].x);
-                        yu[k] = ldb(fac, lu[k].y);
-                    } else {
-                        xl[k] = yu[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    acc.a += xl[k].a * yu[k].a + xl[k].b * yu[k].c;
-                    acc.b += xl[k].a * yu[k].b + xl[k].b * yu[k].d;
-                    acc.c += xl[k].c * yu[k].a + xl[k].d * yu[k].c;
-                    acc.d += xl[k].c * yu[k].b + xl[k].d * yu[k].d;
-                }
-            }
-            const int tg = __ldg(P.sch_tgt + t);
-            Blk<FT> m = ldb(fac, tg);
-            m.a -= acc.a;
-            m.b -= acc.b;
-            m.c -= acc.c;
-            m.d -= acc.d;
-            stb(fac, tg, m);
-        }
-        for (int p = __ldg(P.lev_ptr + l) + GTID; p < __ldg(P.lev_ptr + l + 1); p += GSZ) {
-            const int dk = __ldg(P.lu_diag + p);
-            stb(fac, dk, inv2(ldb(fac, dk), &bad));
-        }
-        gsync<W>();
-    }
-    if (W) return __any_sync(0xffffffffu, bad);
-    if (bad) *s_bad = 1;
-    gsync<W>();
-    return *s_bad;
-}
-
-// One level of a block triangular sweep: x_p <- op(x_p - sum_e M_e x_q(e)) for the rows p
-// of the level, where the gathered entries e of row p are the L part (lower sweeps) or
-// the U part (upper sweeps) of row p in the L+U pattern.  TRANS sweeps read the block at
-// the mirrored position, transposed (row p of U^T / L^T).  The stored pivot inverse (or
-// its transpose) is applied by the upper sweep of LU and by the first sweep of (LU)^T.
-template <typename FT, bool UPPER, bool TRANS, bool W>
-__device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT* x, int l) {
-    constexpr bool DIAG = UPPER != TRANS;
-    const int r1 = __ldg(P.lev_ptr + l + 1);
-    for (int p = __ldg(P.lev_ptr + l) + GTID; p < r1; p += GSZ) {
-        const int dg = __ldg(P.lu_diag + p);
-        const int e0 = UPPER ? dg + 1 : __ldg(P.lu_ptr + p);
-        const int e1 = UPPER ? __ldg(P.lu_ptr + p + 1) : dg;
-        FT s0 = FT(0), s1 = FT(0);
-        constexpr int NB = kBatch<FT>;
-        for (int e = e0; e < e1; e += NB) {
-            int q[NB], pos[NB];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                const bool ok = e + k < e1;
-                q[k] = ok ? __ldg(P.lu_col + e + k) : -1;
-                pos[k] = ok ? (TRANS ? __ldg(P.lu_mirror + e + k) : e + k) : 0;
-            }
-            Blk<FT> m[NB];
-            FT y0[NB], y1[NB];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (q[k] >= 0) {
-                    m[k] = ldb(fac, pos[k]);
-                    y0[k] = x[2 * q[k]];
-                    y1[k] = x[2 * q[k] + 1];
-                } else {
-                    m[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
-                    y0[k] = y1[k] = FT(0);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (TRANS) {
-                    s0 += m[k].a * y0[k] + m[k].c * y1[k];
-                    s1 += m[k].b * y0[k] + m[k].d * y1[k];
-                } else {
-                    s0 += m[k].a * y0[k] + m[k].b * y1[k];
-                    s1 += m[k].c * y0[k] + m[k].d * y1[k];
-                }
-            }
-        }
-        const FT x0 = x[2 * p] - s0, x1 = x[2 * p + 1] - s1;
-        if (DIAG) {
-            const Blk<FT> d = ldb(fac, dg);
-            if (TRANS) {
-                x[2 * p] = d.a * x0 + d.c * x1;
-                x[2 * p + 1] = d.b * x0 + d.d * x1;
-            } else {
-                x[2 * p] = d.a * x0 + d.b * x1;
-                x[2 * p + 1] = d.c * x0 + d.d * x1;
-            }
-        } else {
-            x[2 * p] = x0;
-            x[2 * p + 1] = x1;
-        }
-    }
-}
-
-// x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
-// then U x = y by descending levels.
-template <typename FT, bool W>
-__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x) {
-    for (int l = 0; l < P.n_levels; ++l) {
-        sweep_level<FT, false, false, W>(P, fac, x, l);
-        gsync<W>();
-    }
-    for (int l = P.n_levels - 1; l >= 0; --l) {
-        sweep_level<FT, true, false, W>(P, fac, x, l);
-        gsync<W>();
-    }
-}
-
-// x <- (LU)^{-T} x: U^T y = x by ascending levels (row p of U^T = mirrored L-part
-// positions of row p), then L^T x = y by descending levels (mirrored U-part positions).
-template <typename FT, bool W>
-__device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
-    for (int l = 0; l < P.n_levels; ++l) {
-        sweep_level<FT, false, true, W>(P, fac, x, l);
-        gsync<W>();
-    }
-    for (int l = P.n_levels - 1; l >= 0; --l) {
-        sweep_level<FT, true, true, W>(P, fac, x, l);
-        gsync<W>();
-    }
-}
-
-// r = -F1 - J1 dz with J1 dz = -[Re dS; Im dS] linearised through Ybus (FP64):
-// dV_i = u_i dVm_i + j V_i dtheta_i, dS_i = dV_i conj(I_i) + V_i conj(sum_k Y_ik dV_k).
-// r is rounded straight into the solve vector x (the next right-hand side).  Returns
-// ||r||_inf over the true (unpadded) rows.
-template <typename FT, bool W>
-__device__ double phase_residual(const DevPlan& P, const Arrays& a, FT* x, double* red) {
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        const int p = __ldg(P.bus2pos + i);
-        double dr = 0.0, di = 0.0;
-        if (p >= 0) {
-            const double dth = a.dz[2 * p];
-            const double dvm = (__ldg(P.bus_type + i) == 0) ? a.dz[2 * p + 1] : 0.0;
-            dr = a.Uc[i] * dvm - a.Vim[i] * dth;  // dV = u dVm + j V dtheta
-            di = a.Us[i] * dvm + a.Vre[i] * dth;
-        }
-        a.dVre[i] = dr;
-        a.dVim[i] = di;
-    }
-    gsync<W>();
-    double lmax = 0.0;
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        const int p = __ldg(P.bus2pos + i);
-        if (p < 0) continue;
-        double ir = 0.0, ii = 0.0;
-        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
-            const int j = __ldg(P.y_idx + k);
-            const double2 y = __ldg(P.y_gb + k);
-            const double vr = a.dVre[j], vi = a.dVim[j];
-            ir = fma(y.x, vr, fma(-y.y, vi, ir));
-            ii = fma(y.x, vi, fma(y.y, vr, ii));
-        }
-        const double vr = a.Vre[i], vi = a.Vim[i], Ir = a.Ire[i], Ii = a.Iim[i];
-        const double dvr = a.dVre[i], dvi = a.dVim[i];
-        // dS = dV conj(I) + V conj(dI)
-        const double dSr = dvr * Ir + dvi * Ii + vr * ir + vi * ii;
-        const double dSi = dvi * Ir - dvr * Ii + vi * ir - vr * ii;
-        const double rP = -a.F[2 * p] + dSr;
-        const double rQ = (__ldg(P.bus_type + i) == 0) ? -a.F[2 * p + 1] + dSi : 0.0;
-        x[2 * p] = FT(rP);
-        x[2 * p + 1] = FT(rQ);
-        lmax = fmax(lmax, fmax(absinf(rP), absinf(rQ)));
-    }
-    return group_max<W>(lmax, red);
-}
-
-// ---------------------------------------------------------------- forward kernel
-// The Newton loop of one scenario, run by one group (see GTID / GSZ).
-template <typename FT, bool VSM, bool FSM, bool XSM, bool W>
-__device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A, const int b,
-                                           unsigned char* smem, double* red, int* s_bad_ptr) {
-    int& s_bad = *s_bad_ptr;
-    if (b >= A.batch) return;
-    const SlotLayout& L = A.L;
-    const KernelSmem& K = L.fwd;
-    unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
-    // VSM / FSM are compile-time so that the compiler sees which pointers address
-    // shared memory (plain shared loads instead of generic ones)
-    if (W) smem += (threadIdx.x >> 5) * K.smem_bytes;  // this warp's own arena
-    unsigned char* vbase = VSM ? smem : slot + L.off_vec;
-    FT* fac = FSM ? reinterpret_cast<FT*>(smem + K.smem_fac_off)
-                  : reinterpret_cast<FT*>(slot + L.off_fac);
-    Arrays a;
-    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), false, &a);
-    FT* x = XSM ? reinterpret_cast<FT*>(smem + K.smem_x_off) : ftptr<FT>(a.x);
-    constexpr bool mixed = sizeof(FT) == 4;
-    const size_t row = (size_t)b * P.n_bus;
-
-    // flat start and specified injections (Sec. II-A, Sec. IV-A)
-    for (int i = GTID; i < P.n_bus; i += GSZ) {  // theta = 0: u = 1, V = Vm
-        const int t = __ldg(P.bus_type + i);
-        const double vm = (t == 0) ? 1.0 : A.Vset[row + i];
-        a.Vm[i] = vm;
-        a.Va[i] = 0.0;
-        a.Uc[i] = 1.0;
-        a.Us[i] = 0.0;
-        a.Vre[i] = vm;
-        a.Vim[i] = 0.0;
-    }
-    if (!W && GTID == 0) s_bad = 0;
-    gsync<W>();
-
-    int it = 0, status = 1;
-    double norm = 0.0;
-    bool factored = false;
-    for (;;) {
-        norm = phase_mismatch<mixed, W>(P, a, A.Pd + row, A.Qd + row, A.Pg + row, red);
-        if (!(norm <= 1e10)) { status = 2; break; }
-        if (norm <= A.tol) { status = 0; break; }
-        if (it >= A.max_iter) { status = 1; break; }
-        phase_fill<W>(P, a, fac);
-        gsync<W>();
-        if (phase_lu<FT, W>(P, fac, &s_bad)) { status = 3; factored = false; break; }
-        factored = true;
-        // first solve with the FT factor
-        for (int k = GTID; k < 2 * P.n; k += GSZ) x[k] = FT(-a.F[k]);
-        gsync<W>();
-        phase_solve<FT, W>(P, fac, x);
-        if (mixed) {
-            for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] = double(x[k]);
-            gsync<W>();
-            const int sweeps = (A.ir_gate > 0.0 && norm > A.ir_gate) ? 0 : A.ir_steps;
-            for (int s = 0; s < sweeps; ++s) {
-                const double rmax = phase_residual<FT, W>(P, a, x, red);  // ends with a barrier
-                // forcing term min(ir_rtol, ||F1||): loose far from the solution, quadratic
-                // near it, so the inexact Newton steps keep the quadratic convergence
-                if (A.ir_rtol > 0.0 && rmax <= fmin(A.ir_rtol, norm) * norm) break;
-                phase_solve<FT, W>(P, fac, x);
-                for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] += double(x[k]);
-                gsync<W>();
-            }
-        }
-        // update (FP64)
-        for (int p = GTID; p < P.n; p += GSZ) {
-            const int i = __ldg(P.pos2bus + p);
-            const double dth = mixed ? a.dz[2 * p] : double(x[2 * p]);
-            const double dvm = mixed ? a.dz[2 * p + 1] : double(x[2 * p + 1]);
-            update_bus(a, i, dth, dvm, __ldg(P.bus_type + i) == 0);
-        }
-        ++it;
-        gsync<W>();
-    }
-
-    // Step 2 and outputs
-    double* st = reinterpret_cast<double*>(slot + L.off_state);
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        const int t = __ldg(P.bus_type + i);
-        const double vr = a.Vre[i], vi = a.Vim[i], ir = a.Ire[i], ii = a.Iim[i];
-        const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
-        A.Vm[row + i] = a.Vm[i];
-        A.Va[row + i] = a.Va[i];
-        if (A.keep_factors) {  // the solution the adjoint differentiates at
-            st[i] = a.Vm[i];
-            st[P.n_bus + i] = a.Va[i];
-        }
-        if (A.Pg_out) A.Pg_out[row + i] = (t == 1) ? A.Pg[row + i] : (t == 2 ? Pi + A.Pd[row + i] : 0.0);
-        if (A.Qg_out) A.Qg_out[row + i] = (t == 0) ? 0.0 : Qi + A.Qd[row + i];
-    }
-    if (A.keep_factors && factored && FSM) {
-        FT* dst = reinterpret_cast<FT*>(slot + L.off_fac);
-        const int nv = P.nnzb * 4;
-        for (int k = GTID; k < nv; k += GSZ) dst[k] = fac[k];
-    }
-    if (GTID == 0) {
-        A.status[b] = status;
-        if (A.iters) A.iters[b] = it;
-        if (A.fmis) A.fmis[b] = norm;
-        int* fl = reinterpret_cast<int*>(slot + L.off_flags);
-        fl[0] = status;
-        fl[1] = it;
-        fl[2] = (A.keep_factors && factored) ? 1 : 0;
-    }
-}
-
-template <typename FT, bool VSM, bool FSM, bool XSM>
-__global__ void __launch_bounds__(1024) nr_solve_kernel(DevPlan P, SolveArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    __shared__ int s_bad;
-    solve_body<FT, VSM, FSM, XSM, false>(P, A, blockIdx.x, smem, red, &s_bad);
-}
-
-// Several scenarios per CTA, one per warp; the tighter register budget (42 per thread)
-// lets more warps -- more scenarios in flight -- share an SM.
-template <typename FT, bool VSM, bool FSM, bool XSM>
-__global__ void __launch_bounds__(256, 6) nr_solve_warps_kernel(DevPlan P, SolveArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    int unused = 0;  // the warp groups vote instead of sharing a flag
-    const int b = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    solve_body<FT, VSM, FSM, XSM, true>(P, A, b, smem, nullptr, &unused);
-}
-
-// Several networks in one persistent launch: CTAs take scenarios from a work counter,
-// jobs in the order given (the host puts the most expensive first), and run each with
-// its own plan.  Every job keeps its data in the global workspace (the solve vector in
-// shared memory when it is small), so one launch shape serves all of them.
-template <typename FT>
-__global__ void __launch_bounds__(1024) nr_solve_multi_kernel(MultiArgs M) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    __shared__ int s_bad;
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(M.counter, 1u);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();  // everyone has read s_item before it is overwritten
-        if (item >= M.total) break;
-        int j = 0;
-        while (j + 1 < M.n_jobs && item >= M.first[j + 1]) ++j;
-        const int b = item - M.first[j];
-        if (M.args[j].L.fwd.x_in_smem)
-            solve_body<FT, false, false, true, false>(M.plans[j], M.args[j], b, smem, red, &s_bad);
-        else
-            solve_body<FT, false, false, false, false>(M.plans[j], M.args[j], b, smem, red, &s_bad);
-        __syncthreads();  // the next scenario reuses the shared arrays
-    }
-}
-
-// ---------------------------------------------------------------- adjoint kernel
-// Sec. II-B.2 at the converged state: v_bar2 = -J2^T c, g_z1, J1^T lambda = g_z1,
-// dL/dx = g_x - [lambda_G; J3^T lambda]; loads through dF1/dpd = dF1/dqd = -1.
-// All Jacobian-transpose products are taken matrix-free through Ybus^T (phase_jvt);
-// the transposed solve uses the stored factor of the last Newton step and refines
-// with the FP64 residual of J1 at the solution.
-template <typename FT, bool VSM, bool FSM>
-__global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    __shared__ int s_bad;
-    const int b = blockIdx.x;
-    if (b >= A.batch) return;
-    const SlotLayout& L = A.L;
-    const KernelSmem& K = L.adj;
-    unsigned char* slot = reinterpret_cast<unsigned char*>(A.ws) + (size_t)b * L.slot_bytes;
-    unsigned char* vbase = VSM ? smem : slot + L.off_vec;
-    FT* gfac = reinterpret_cast<FT*>(slot + L.off_fac);
-    FT* fac = FSM ? reinterpret_cast<FT*>(smem + K.smem_fac_off) : gfac;
-    Arrays a;
-    carve(vbase, P.n_bus, P.n, (int)sizeof(FT), true, &a);
-    FT* x = ftptr<FT>(a.x);
-    const size_t row = (size_t)b * P.n_bus;
-    const int* fl = reinterpret_cast<const int*>(slot + L.off_flags);
-    const int fwd_status = fl[0];
-    const int has_factor = fl[2];
-
-    if (fwd_status != 0) {
-        for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-            A.dPd[row + i] = 0.0;
-            A.dQd[row + i] = 0.0;
-            A.dPg_in[row + i] = 0.0;
-            A.dVset[row + i] = 0.0;
-        }
-        if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = fwd_status;
-        return;
-    }
-    const double* st = reinterpret_cast<const double*>(slot + L.off_state);
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        a.Vm[i] = st[i];
-        a.Va[i] = st[P.n_bus + i];
-    }
-    if (threadIdx.x == 0) s_bad = 0;
-    gsync<false>();
-    phase_voltage<false>(P, a);
-    gsync<false>();
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {  // I = Y V
-        double ir = 0.0, ii = 0.0;
-        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
-            const int j = __ldg(P.y_idx + k);
-            const double2 y = __ldg(P.y_gb + k);
-            ir = fma(y.x, a.Vre[j], fma(-y.y, a.Vim[j], ir));
-            ii = fma(y.x, a.Vim[j], fma(y.y, a.Vre[j], ii));
-        }
-        a.Ire[i] = ir;
-        a.Iim[i] = ii;
-        store_bus_f32(a, i, ir, ii);
-    }
-    // Step-2 weights: c_P on R (dL/dpg_R), c_Q on B\D (dL/dqg)
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = __ldg(P.bus_type + i);
-        a.Psp[i] = (t == 2 && A.dPg) ? A.dPg[row + i] : 0.0;
-        a.Qsp[i] = (t != 0 && A.dQg) ? A.dQg[row + i] : 0.0;
-    }
-    gsync<false>();
-    phase_jvt<false>(P, a);  // v_bar2 = -J2^T c = (d[P_R; Q_{B\D}]/dv)^T c
-    gsync<false>();
-    double lg = 0.0;
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const double gvm = A.dVm[row + i] + a.w0[i];
-        const double gva = A.dVa[row + i] + a.w1[i];
-        a.gV[i] = gvm;
-        const int p = __ldg(P.bus2pos + i);
-        if (p >= 0) {
-            a.F[2 * p] = gva;                                   // theta component of g_z1
-            a.F[2 * p + 1] = (__ldg(P.bus_type + i) == 0) ? gvm : 0.0;  // Vm component (PQ only)
-            lg = fmax(lg, fmax(absinf(gva), absinf(a.F[2 * p + 1])));
-        }
-    }
-    const double gnorm = group_max<false>(lg, red);
-
-    // stage the stored factor
-    bool have = has_factor != 0;
-    if (have && FSM) {
-        const int nv = P.nnzb * 4;
-        for (int k = threadIdx.x; k < nv; k += blockDim.x) fac[k] = gfac[k];
-        gsync<false>();
-    }
-    int astat = 0;
-    bool refactored = false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if (!have) {
-            phase_fill<false>(P, a, fac);
-            gsync<false>();
-            if (phase_lu<FT, false>(P, fac, &s_bad)) { astat = 3; break; }
-            have = true;
-            refactored = true;
-        }
-        for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.F[k]);
-        gsync<false>();
-        phase_solve_t<FT, false>(P, fac, x);
-        for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] = double(x[k]);
-        gsync<false>();
-        bool conv = false;
-        for (int s = 0;; ++s) {
-            // m1 = lambda on the F1 rows; r = g_z1 - J1^T lambda = g_z1 + (Jv^T m1)[z1]
-            for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-                const int p = __ldg(P.bus2pos + i);
-                a.Psp[i] = (p >= 0) ? a.dz[2 * p] : 0.0;
-                a.Qsp[i] = (p >= 0 && __ldg(P.bus_type + i) == 0) ? a.dz[2 * p + 1] : 0.0;
-            }
-            gsync<false>();
-            phase_jvt<false>(P, a);
-            gsync<false>();
-            double lr = 0.0;
-            for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
-                const int i = __ldg(P.pos2bus + p);
-                const double r0 = a.F[2 * p] + a.w1[i];
-                const double r1 = (__ldg(P.bus_type + i) == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
-                a.r[2 * p] = r0;
-                a.r[2 * p + 1] = r1;
-                lr = fmax(lr, fmax(absinf(r0), absinf(r1)));
-            }
-            const double rmax = group_max<false>(lr, red);
-            if (rmax <= A.ir_rtol * gnorm) { conv = true; break; }
-            if (s >= A.ir_max || !(rmax <= 1e300)) break;
-            for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
-            gsync<false>();
-            phase_solve_t<FT, false>(P, fac, x);
-            for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] += double(x[k]);
-            gsync<false>();
-        }
-        if (conv) break;
-        if (refactored) { astat = 1; break; }
-        have = false;  // stale factor did not converge: refactor at the solution
-    }
-    // gradients; w0 holds (Jv^T m1)_Vm for the final lambda
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = __ldg(P.bus_type + i);
-        const int p = __ldg(P.bus2pos + i);
-        const double lP = (p >= 0) ? a.dz[2 * p] : 0.0;
-        const double lQ = (p >= 0 && t == 0) ? a.dz[2 * p + 1] : 0.0;
-        const double cP = A.dPg ? A.dPg[row + i] : 0.0;
-        const double cQ = A.dQg ? A.dQg[row + i] : 0.0;
-        A.dPd[row + i] = (t == 2) ? cP : lP;
-        A.dQd[row + i] = (t == 0) ? lQ : cQ;
-        A.dPg_in[row + i] = (t == 1) ? cP - lP : 0.0;
-        A.dVset[row + i] = (t != 0) ? a.gV[i] + a.w0[i] : 0.0;
-    }
-    if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = astat;
-}
 
 // ---------------------------------------------------------------- launchers
 // The dynamic shared-memory limit of a kernel is raised once per (device, kernel) to the
@@ -838,14 +29,84 @@ cudaError_t ensure_smem_limit(const void* k, size_t bytes) {
     return e;
 }
 
-template <typename KernelT, typename ArgT>
-cudaError_t launch_one(KernelT k, const DevPlan& P, const ArgT& A, const KernelSmem& K,
-                       int threads, cudaStream_t s) {
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(k), K.smem_bytes);
-    if (e != cudaSuccess) return e;
-    k<<<A.batch, threads, K.smem_bytes, s>>>(P, A);
-    return cudaGetLastError();
+// ---------------------------------------------------------------- block-diagonal export
+// The J1 values of every scenario at the given voltages, written straight into the fixed
+// scalar template (Sec. III-A; Alg. 1's element formulas, here jac_block in FP64).  One
+// CTA per scenario: first the unit phasor u = e^{j theta} of every bus (one FP64 sincos
+// per bus, the costly part on this GPU's FP64 pipe), kept in shared memory (UMEM) when it
+// fits, else recomputed per use; then one thread per non-slack bus forms I_i from its
+// Ybus row and the 2x2 block of every entry (i, j) of that row, and stores the applicable
+// entries at the positions the plan holds for them.
+template <bool UMEM>
+__global__ void __launch_bounds__(256) export_j1_kernel(DevPlan P, int batch, const double* Vm,
+                                                        const double* Va, double* values) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* su = reinterpret_cast<double2*>(smem_raw);
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        const double* vm = Vm + (size_t)b * P.n_bus;
+        const double* va = Va + (size_t)b * P.n_bus;
+        auto unit = [&](int j) {
+            if (UMEM) return su[j];
+            double sj, cj;
+            sincos(va[j], &sj, &cj);
+            return make_double2(cj, sj);
+        };
+        if (UMEM) {
+            for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+                double si, ci;
+                sincos(va[i], &si, &ci);
+                su[i] = make_double2(ci, si);
+            }
+            __syncthreads();
+        }
+        double* out = values + (size_t)b * P.nnz_j1;
+        for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
+            if (__ldg(P.bus_type + i) == 2) continue;
+            const double2 ui = unit(i);
+            const double vmi = vm[i], vri = vmi * ui.x, vii = vmi * ui.y;
+            const int k0 = __ldg(P.y_ptr + i), k1 = __ldg(P.y_ptr + (i + 1));
+            double ir = 0.0, ii = 0.0;
+            for (int k = k0; k < k1; ++k) {
+                const int j = __ldg(P.y_idx + k);
+                const double2 y = __ldg(P.y_gb + k);
+                const double2 uj = unit(j);
+                const double vr = vm[j] * uj.x, vi = vm[j] * uj.y;
+                ir = fma(y.x, vr, fma(-y.y, vi, ir));
+                ii = fma(y.x, vi, fma(y.y, vr, ii));
+            }
+            const double pu = ui.x * ir + ui.y * ii, qu = ui.y * ir - ui.x * ii;  // u_i conj(I_i)
+            for (int k = k0; k < k1; ++k) {
+                const int j = __ldg(P.y_idx + k);
+                const double2 y = __ldg(P.y_gb + k);
+                const double2 uj = unit(j);
+                const Blk<double> m = jac_block<double>(i == j, y.x, y.y, vri, vii, uj.x, uj.y,
+                                                        vm[j], vmi, pu, qu);
+                const int4 pos = __ldg(P.j1_pos + k);
+                if (pos.x >= 0) out[pos.x] = m.a;
+                if (pos.y >= 0) out[pos.y] = m.b;
+                if (pos.z >= 0) out[pos.z] = m.c;
+                if (pos.w >= 0) out[pos.w] = m.d;
+            }
+        }
+        if (UMEM) __syncthreads();  // the next scenario overwrites the phasors
+    }
 }
+
+// Index arrays of the block-diagonal embedding: block k is the template shifted by k n1.
+__global__ void __launch_bounds__(256) bde_pattern_kernel(DevPlan P, int batch, int* row_ptr,
+                                                          int* col_idx) {
+    const long long rows = (long long)batch * P.n1, nz = (long long)batch * P.nnz_j1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r <= rows; r += stride) {
+        const long long b = r / P.n1, rr = r - b * P.n1;
+        row_ptr[r] = (r == rows) ? (int)nz : (int)(b * P.nnz_j1 + __ldg(P.j1_ptr + rr));
+    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nz; e += stride) {
+        const long long b = e / P.nnz_j1, ee = e - b * P.nnz_j1;
+        col_idx[e] = (int)(b * P.n1 + __ldg(P.j1_col + ee));
+    }
+}
+
 
 template <typename FT, bool VSM, bool FSM, bool XSM>
 cudaError_t launch_solve_cfg(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s) {
@@ -893,6 +154,32 @@ cudaError_t launch_solve_multi(const MultiArgs& M, int threads, int grid, size_t
 template <typename FT>
 cudaError_t multi_blocks_per_sm(int threads, size_t smem, int* out) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, nr_solve_multi_kernel<FT>, threads, smem);
+}
+
+cudaError_t launch_export_jacobian(const DevPlan& P, int batch, const double* Vm, const double* Va,
+                                   double* values, cudaStream_t s) {
+    const size_t smem = sizeof(double2) * (size_t)P.n_bus;
+    int optin = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(batch, 152 * 16);
+    if (smem + 1024 <= (size_t)optin) {
+        e = ensure_smem_limit(reinterpret_cast<const void*>(export_j1_kernel<true>), smem);
+        if (e != cudaSuccess) return e;
+        export_j1_kernel<true><<<grid, 256, smem, s>>>(P, batch, Vm, Va, values);
+    } else {
+        export_j1_kernel<false><<<grid, 256, 0, s>>>(P, batch, Vm, Va, values);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bde_pattern(const DevPlan& P, int batch, int* row_ptr, int* col_idx,
+                               cudaStream_t s) {
+    const long long total = (long long)batch * P.nnz_j1;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8 * 4);
+    bde_pattern_kernel<<<grid, 256, 0, s>>>(P, batch, row_ptr, col_idx);
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_solve_multi<float>(const MultiArgs&, int, int, size_t, cudaStream_t);

@@ -334,6 +334,51 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         }
     }
     P.nnz_j1 = (int)nnz;
+
+    // the scalar J1 template in the paper's ordering
+    std::vector<int> rowP(n_bus, -1), rowQ(n_bus, -1), colV(n_bus, -1), colT(n_bus, -1);
+    int nBR = 0, nD = 0;
+    for (int i = 0; i < n_bus; ++i) {
+        if (bus_type[i] != 2) colT[i] = nBR, rowP[i] = nBR++;
+        if (bus_type[i] == 0) colV[i] = nD++;
+    }
+    for (int i = 0; i < n_bus; ++i) {
+        if (bus_type[i] == 0) rowQ[i] = nBR + colV[i];
+        if (bus_type[i] != 2) colT[i] += nD;
+    }
+    P.n1 = nBR + nD;
+    std::vector<int> cntV(n_bus, 0), cntT(n_bus, 0);
+    for (int i = 0; i < n_bus; ++i)
+        for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+            cntV[i] += bus_type[P.y_idx[k]] == 0;
+            cntT[i] += bus_type[P.y_idx[k]] != 2;
+        }
+    P.j1_ptr.assign(P.n1 + 1, 0);
+    for (int i = 0; i < n_bus; ++i) {
+        if (rowP[i] >= 0) P.j1_ptr[rowP[i] + 1] = cntV[i] + cntT[i];
+        if (rowQ[i] >= 0) P.j1_ptr[rowQ[i] + 1] = cntV[i] + cntT[i];
+    }
+    for (int r = 0; r < P.n1; ++r) P.j1_ptr[r + 1] += P.j1_ptr[r];
+    P.j1_col.assign(P.j1_ptr[P.n1], -1);
+    P.j1_pos.assign(4 * P.y_idx.size(), -1);
+    for (int i = 0; i < n_bus; ++i) {
+        const int rows[2] = {rowP[i], rowQ[i]};
+        for (int h = 0; h < 2; ++h) {  // h = 0: the dP_i row, h = 1: the dQ_i row
+            if (rows[h] < 0) continue;
+            int v = P.j1_ptr[rows[h]], t = v + cntV[i];
+            for (int k = P.y_ptr[i]; k < P.y_ptr[i + 1]; ++k) {
+                const int j = P.y_idx[k];
+                if (colV[j] >= 0) {
+                    P.j1_col[v] = colV[j];
+                    P.j1_pos[4 * k + 2 * h + 1] = v++;
+                }
+                if (bus_type[j] != 2) {
+                    P.j1_col[t] = colT[j];
+                    P.j1_pos[4 * k + 2 * h] = t++;
+                }
+            }
+        }
+    }
     return BUILD_OK;
 }
 

@@ -50,6 +50,14 @@ struct Plan {
     std::vector<int> la_ptr, la_L, la_D;
     std::vector<int> sch_tptr, sch_tgt, sch_cptr, sch_L, sch_U;
 
+    // J1 as a scalar CSR in the paper's ordering (rows [dP_{B\R}; dQ_D], columns
+    // [Vm_D; theta_{B\R}], each part in bus order; columns sorted within a row), and for
+    // every Ybus entry (i, j) the positions of its up to four J1 entries
+    // (dP_i/dtheta_j, dP_i/dVm_j, dQ_i/dtheta_j, dQ_i/dVm_j; -1 where absent): the
+    // fixed template the block-diagonal export writes into (Sec. III-A, Alg. 1)
+    int n1 = 0;
+    std::vector<int> j1_ptr, j1_col, j1_pos;
+
     // statistics
     int nnz_j1 = 0;
     long long schur_ops = 0;

@@ -54,15 +54,34 @@ def analyze(n_bus, indptr, indices, g, bv, bus_type):
     bt = np.ascontiguousarray(bus_type, np.int32)
     info = L.PlanInfo()
     L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
-                           C.byref(info), None, None, None, None), "pf_analyze")
+                           C.byref(info), None, None, None, None, None, None), "pf_analyze")
     pos2bus = np.zeros(info.n_block, np.int32)
     lu_ptr = np.zeros(info.n_block + 1, np.int32)
     lu_col = np.zeros(info.nnzb_lu, np.int32)
     lev_ptr = np.zeros(info.n_levels + 1, np.int32)
     L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
                            C.byref(info), _iptr(pos2bus), _iptr(lu_ptr), _iptr(lu_col),
-                           _iptr(lev_ptr)), "pf_analyze")
+                           _iptr(lev_ptr), None, None), "pf_analyze")
     return _info_dict(info), pos2bus, lu_ptr, lu_col, lev_ptr
+
+
+def jacobian_template(n_bus, indptr, indices, g, bv, bus_type):
+    """Host-only: the fixed scalar CSR pattern (j1_ptr, j1_col) of J1 in the paper's
+    ordering -- rows [dP_{B\\R}; dQ_D], columns [Vm_D; theta_{B\\R}] -- that the
+    block-diagonal export fills."""
+    lib = L.load()
+    ip, ix = np.ascontiguousarray(indptr, np.int32), np.ascontiguousarray(indices, np.int32)
+    gg, bb = np.ascontiguousarray(g, np.float64), np.ascontiguousarray(bv, np.float64)
+    bt = np.ascontiguousarray(bus_type, np.int32)
+    info = L.PlanInfo()
+    L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
+                           C.byref(info), None, None, None, None, None, None), "pf_analyze")
+    j1_ptr = np.zeros(info.n_unknowns + 1, np.int32)
+    j1_col = np.zeros(info.nnz_j1, np.int32)
+    L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
+                           C.byref(info), None, None, None, None, _iptr(j1_ptr), _iptr(j1_col)),
+            "pf_analyze")
+    return j1_ptr, j1_col
 
 
 def _info_dict(info: L.PlanInfo) -> dict:
@@ -78,6 +97,8 @@ class SolveResult:
     iters: torch.Tensor
     status: torch.Tensor
     final_mismatch: torch.Tensor
+    bus_type: torch.Tensor | None = None   # pf_solve_qlim: final partition per scenario
+    rounds: torch.Tensor | None = None     # pf_solve_qlim: switching rounds taken
 
 
 @dataclass
@@ -122,6 +143,7 @@ class PowerFlow:
         self._lib = lib
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._ws = None
+        self._ws_q = None
         self._ws_key = None
         self._solve_id = 0
         self._last = None
@@ -196,6 +218,87 @@ class PowerFlow:
         self._last = (batch, ws, bool(keep_factors))
         return out
 
+    def solve_qlim(self, Pd, Qd, Pg, Vset, Qmin, Qmax, tol=1e-8, max_iter=20, max_rounds=10,
+                   precision="mixed", ir_steps=2, ir_rtol=1e-3, group_threads=0, placement=0,
+                   instances_per_cta=0, ir_gate=0.0) -> SolveResult:
+        """Newton-Raphson with reactive-power limits at the PV buses (pf_solve_qlim):
+        violating PV buses switch to PQ with qg at the limit, between Newton rounds.
+        The result also carries ``bus_type`` (final partition per scenario) and
+        ``rounds``."""
+        batch = Pd.shape[0]
+        for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset), ("Qmin", Qmin),
+                      ("Qmax", Qmax)):
+            _check_bus_tensor(v, nm, self.n_bus, batch)
+        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, False, placement,
+                              instances_per_cta, ir_gate)
+        n = C.c_size_t(0)
+        L.check(self._lib.pf_qlim_workspace_size(self._h, batch, C.byref(opts), C.byref(n)),
+                "pf_qlim_workspace_size")
+        # a buffer of its own: replacing the solve workspace would free memory that a
+        # captured CUDA graph of an earlier solve may still address
+        if self._ws_q is None or self._ws_q.numel() < n.value:
+            self._ws_q = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+        ws = self._ws_q
+        e = dict(dtype=torch.float64, device=Pd.device)
+        i32 = dict(dtype=torch.int32, device=Pd.device)
+        out = SolveResult(
+            Vm=torch.empty(batch, self.n_bus, **e), Va=torch.empty(batch, self.n_bus, **e),
+            Pg=torch.empty(batch, self.n_bus, **e), Qg=torch.empty(batch, self.n_bus, **e),
+            iters=torch.empty(batch, **i32), status=torch.empty(batch, **i32),
+            final_mismatch=torch.empty(batch, **e), bus_type=torch.empty(batch, self.n_bus, **i32),
+            rounds=torch.empty(batch, **i32))
+        stream = torch.cuda.current_stream(Pd.device).cuda_stream
+        L.check(self._lib.pf_solve_qlim(
+            self._h, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(), Vset.data_ptr(),
+            Qmin.data_ptr(), Qmax.data_ptr(), float(tol), int(max_iter), int(max_rounds),
+            C.byref(opts), out.Vm.data_ptr(), out.Va.data_ptr(), out.Pg.data_ptr(),
+            out.Qg.data_ptr(), out.iters.data_ptr(), out.status.data_ptr(),
+            out.final_mismatch.data_ptr(), out.bus_type.data_ptr(), out.rounds.data_ptr(),
+            ws.data_ptr(), ws.numel(), stream), "pf_solve_qlim")
+        self._solve_id += 1
+        self._last = None   # nothing for pf_adjoint to differentiate
+        return out
+
+    def jacobian_pattern(self):
+        """The fixed scalar CSR template of J1 in the paper's ordering (host numpy):
+        rows [dP_{B\\R}; dQ_D], columns [Vm_D; theta_{B\\R}] (pf_jacobian_pattern)."""
+        info = self.info()
+        j1_ptr = np.zeros(info["n_unknowns"] + 1, np.int32)
+        j1_col = np.zeros(info["nnz_j1"], np.int32)
+        L.check(self._lib.pf_jacobian_pattern(self._h, _iptr(j1_ptr), _iptr(j1_col)),
+                "pf_jacobian_pattern")
+        return j1_ptr, j1_col
+
+    def export_jacobian(self, Vm, Va, out: torch.Tensor | None = None) -> torch.Tensor:
+        """J1 values of every scenario at (Vm, Va) [batch, n_bus] (pf_export_jacobian):
+        a [batch, nnz_j1] FP64 device tensor in the order of ``jacobian_pattern``."""
+        batch = Vm.shape[0]
+        for nm, v in (("Vm", Vm), ("Va", Va)):
+            _check_bus_tensor(v, nm, self.n_bus, batch)
+        nnz = self.info()["nnz_j1"]
+        if out is None:
+            out = torch.empty(batch, nnz, dtype=torch.float64, device=Vm.device)
+        stream = torch.cuda.current_stream(Vm.device).cuda_stream
+        L.check(self._lib.pf_export_jacobian(self._h, batch, Vm.data_ptr(), Va.data_ptr(),
+                                             out.data_ptr(), stream), "pf_export_jacobian")
+        return out
+
+    def bde_matrix(self, Vm, Va) -> torch.Tensor:
+        """The block-diagonal embedding (Sec. III-A) of the batch's J1 as one
+        ``torch.sparse_csr_tensor`` of size (batch n1) x (batch n1): index arrays from
+        pf_bde_pattern, values from pf_export_jacobian, both written on the device and
+        used by the tensor without a copy."""
+        batch = Vm.shape[0]
+        info = self.info()
+        n1, nnz = info["n_unknowns"], info["nnz_j1"]
+        row_ptr = torch.empty(batch * n1 + 1, dtype=torch.int32, device=Vm.device)
+        col_idx = torch.empty(batch * nnz, dtype=torch.int32, device=Vm.device)
+        stream = torch.cuda.current_stream(Vm.device).cuda_stream
+        L.check(self._lib.pf_bde_pattern(self._h, batch, row_ptr.data_ptr(), col_idx.data_ptr(),
+                                         stream), "pf_bde_pattern")
+        vals = self.export_jacobian(Vm, Va).view(-1)
+        return torch.sparse_csr_tensor(row_ptr, col_idx, vals, (batch * n1, batch * n1))
+
     def autotune(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
                  ir_rtol=1e-3, keep_factors=False, ir_gate=0.0) -> dict:
         """Time every launch configuration on these inputs (pf_autotune) and keep the
@@ -259,9 +362,9 @@ class PFLayer(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, pf: PowerFlow, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed",
-                ir_steps=2):
+                ir_steps=2, ir_rtol=1e-3, ir_gate=0.0):
         res = pf.solve(Pd.contiguous(), Qd.contiguous(), Pg.contiguous(), Vset.contiguous(), tol,
-                       max_iter, precision, ir_steps, keep_factors=True)
+                       max_iter, precision, ir_steps, ir_rtol, keep_factors=True, ir_gate=ir_gate)
         ctx.pf = pf
         ctx.solve_id = pf._solve_id
         ctx.mark_non_differentiable(res.status)
@@ -285,7 +388,7 @@ class PFLayer(torch.autograd.Function):
 
         g = pf.adjoint(dense(gVm), dense(gVa), None if gPg is None else gPg.contiguous(),
                        None if gQg is None else gQg.contiguous())
-        return None, g.dPd, g.dQd, g.dPg, g.dVset, None, None, None, None
+        return None, g.dPd, g.dQd, g.dPg, g.dVset, None, None, None, None, None, None
 
 
 def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,

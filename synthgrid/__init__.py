@@ -278,3 +278,46 @@ def make_scenarios(g: Grid, n_scen: int, lo: float, hi: float, seed: int) -> Sce
     Pg = np.broadcast_to(g.Pg0, (n_scen, g.n_bus)).copy()
     Vset = np.broadcast_to(g.Vset, (n_scen, g.n_bus)).copy()
     return Scenarios(Pd=Pd, Qd=Qd, Pg=Pg, Vset=Vset)
+
+
+@dataclass
+class OPFLimits:
+    """Per-bus operating limits and generation costs of a grid (``[n_bus]`` float64).
+
+    Data for the learning loop around the power-flow layer: box limits of the voltage
+    magnitudes, of active generation on generator buses (PV and slack) and of reactive
+    generation on B\\D, plus quadratic cost coefficients c2 pg^2 + c1 pg per generator
+    bus.  Entries off their bus set are 0 (costs, generation limits) or unused.
+    """
+
+    vmin: np.ndarray
+    vmax: np.ndarray
+    pmin: np.ndarray
+    pmax: np.ndarray
+    qmin: np.ndarray
+    qmax: np.ndarray
+    c2: np.ndarray
+    c1: np.ndarray
+
+
+def make_opf_limits(g: Grid, seed: int) -> OPFLimits:
+    """Seeded synthetic limits and costs around the grid's base case.
+
+    Voltages in [0.94, 1.06] pu.  A PV bus may produce [0, 2 Pg0 + 0.02] (its base
+    dispatch sits mid-range); the slack buses share [0, 2 (sum Pd0 - sum Pg0) + 0.1]
+    evenly.  Reactive limits are +-(0.6 pmax + 0.3) on B\\D.  Costs: c2 ~ U(0.5, 1.5),
+    c1 ~ U(1, 3) per generator bus.
+    """
+    rng = np.random.default_rng(seed)
+    n = g.n_bus
+    gen = g.bus_type != PQ
+    slack = g.bus_type == SLACK
+    pmax = np.zeros(n)
+    pmax[g.bus_type == PV] = 2.0 * g.Pg0[g.bus_type == PV] + 0.02
+    deficit = max(float(g.Pd0.sum() - g.Pg0.sum()), 0.0)
+    pmax[slack] = (2.0 * deficit + 0.1) / max(int(slack.sum()), 1)
+    qmax = np.where(gen, 0.6 * pmax + 0.3, 0.0)
+    c2 = np.where(gen, rng.uniform(0.5, 1.5, n), 0.0)
+    c1 = np.where(gen, rng.uniform(1.0, 3.0, n), 0.0)
+    return OPFLimits(vmin=np.full(n, 0.94), vmax=np.full(n, 1.06), pmin=np.zeros(n), pmax=pmax,
+                     qmin=-qmax, qmax=qmax, c2=c2, c1=c1)

@@ -29,6 +29,10 @@ CONFIGS = {
     # 9241-bus: tree + 4800 extra edges, 1400 PV, 10% transformers, 10 reference buses
     "c3": dict(n_bus=9241, n_branch=9240 + 4800, n_pv=1400, n_xfmr=1404, n_slack=10, seed=3,
                n_scen=256, lo=0.9, hi=1.1, tol=1e-8, max_iter=20),
+    # 25k-bus size of the paper's largest standalone case (Table II): tree + 7500 extra
+    # edges (1.3 branches per bus), 15 % PV, 10 % transformers, 20 reference buses
+    "c5": dict(n_bus=25000, n_branch=24999 + 7500, n_pv=3750, n_xfmr=3250, n_slack=20, seed=5,
+               n_scen=256, lo=0.9, hi=1.1, tol=1e-8, max_iter=20),
     # uneven batch: 30 / 300 / 2000-bus grids
     "c4a": dict(n_bus=30, n_branch=41, n_pv=5, n_xfmr=4, n_slack=1, seed=40,
                 n_scen=2048, lo=0.6, hi=1.4, tol=1e-8, max_iter=20),

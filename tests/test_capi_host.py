@@ -189,3 +189,24 @@ def test_all_slack_network_is_trivial(pfm):
     ip, ix, gg, bb = pfm.build_ybus(2, [0], [1], [0.01], [0.1], [0.0], [1.0])
     info = pfm.analyze(2, ip, ix, gg, bb, np.array([SLACK, SLACK], np.int32))[0]
     assert info["n_block"] == 0 and info["nnzb_lu"] == 0 and info["n_levels"] == 0
+
+
+@pytest.mark.parametrize("name", ["c0", "c1", "c2"])
+def test_jacobian_template_is_the_oracle_pattern(pfm, name):
+    """The scalar J1 template (host-only analysis) holds exactly the structural nonzeros
+    of the oracle's J1 at a generic operating point, in the paper's row/column order,
+    columns sorted within every row."""
+    g = configs.grid(name)
+    ip, ix, gg, bb = pfm.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+    j1_ptr, j1_col = pfm.jacobian_template(g.n_bus, ip, ix, gg, bb, g.bus_type)
+    info = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)[0]
+    assert j1_ptr.size == info["n_unknowns"] + 1 and j1_ptr[-1] == info["nnz_j1"]
+    rng = np.random.default_rng(0)
+    Y = O.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+    J = O.J1_of(Y, g.bus_type, 1 + rng.uniform(-0.05, 0.05, g.n_bus),
+                rng.uniform(-0.3, 0.3, g.n_bus)).tocsr()
+    J.eliminate_zeros()
+    J.sort_indices()
+    assert np.array_equal(J.indptr, j1_ptr)
+    assert np.array_equal(J.indices, j1_col)
+    assert info["plan_bytes"] > 0

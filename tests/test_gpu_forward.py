@@ -71,6 +71,18 @@ def test_c3_sampled(PowerFlow, precision):
     assert np.all(gpu["status"] == 0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c5_25k_bus_sampled(PowerFlow, precision):
+    """25,000-bus grid (20 reference buses), all 256 scenarios in one launch; the first
+    and last against the oracle, every scenario converged."""
+    g, sc = workload("c5")
+    pf = PowerFlow.from_grid(g)
+    gpu = run_gpu(pf, sc, precision=precision, ir_steps=2, ir_gate=1e-2)
+    compare(gpu, run_oracle(g, sc, [0, 255]), iter_slack=0 if precision == "fp64" else 1)
+    assert np.all(gpu["status"] == 0)
+    assert np.all(gpu["final_mismatch"] <= 1e-8)
+
+
 @pytest.mark.parametrize("name,n", [("c4a", 2048), ("c4b", 512), ("c4c", 64)])
 def test_c4_grids_flags_and_values(PowerFlow, name, n):
     """Uneven loads x U(0.6, 1.4): every flag and every converged value matches."""
