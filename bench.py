@@ -671,11 +671,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     line = gpu_leg(args, rank, world)
-    if rank == 0 and args.cpu_sample > 0:
-        r, procs, dt, conv = oracle_rate(args.cpu_sample)
-        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
-                                "sample": f"first {args.cpu_sample} of the 4096 scenarios "
-                                          f"({dt:.1f} s wall)", "cpu": cpu_model()}
+    if rank == 0:
+        if args.cpu_sample > 0:
+            r, procs, dt, conv = oracle_rate(args.cpu_sample)
+            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                    "sample": f"first {args.cpu_sample} of the 4096 scenarios "
+                                              f"({dt:.1f} s wall)", "cpu": cpu_model()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
