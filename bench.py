@@ -321,26 +321,33 @@ def gpu_leg(args, rank, world):
             slacks4.append(torch.as_tensor(g4.bus_type == 2, device=dev))
         n4 = sum(it[1].shape[0] for it in items4)
         # launch shape of the single launch: fastest of a few thread counts (setup, not timed)
+        # launch shape of the single launch: threads per CTA x per-network forms (auto) or
+        # every network from the global workspace (3); fastest of 3 timed runs (setup)
         best4 = None
-        for th in (64, 128, 256):
-            solve_multi(items4, group_threads=th, **opts)
-            torch.cuda.synchronize(dev)
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record(stream)
-            solve_multi(items4, group_threads=th, **opts)
-            t1.record(stream)
-            torch.cuda.synchronize(dev)
-            if best4 is None or t0.elapsed_time(t1) < best4[1]:
-                best4 = (th, t0.elapsed_time(t1))
-        tuned["multi_c4"] = {"group_threads": best4[0]}
+        for th in (128, 256, 512):
+            for pl in (0, 3):
+                solve_multi(items4, group_threads=th, placement=pl, **opts)
+                torch.cuda.synchronize(dev)
+                ts4 = []
+                for _ in range(3):
+                    t0 = torch.cuda.Event(enable_timing=True)
+                    t1 = torch.cuda.Event(enable_timing=True)
+                    t0.record(stream)
+                    solve_multi(items4, group_threads=th, placement=pl, **opts)
+                    t1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ts4.append(t0.elapsed_time(t1))
+                if best4 is None or min(ts4) < best4[2]:
+                    best4 = (th, pl, min(ts4))
+        tuned["multi_c4"] = {"group_threads": best4[0], "placement": best4[1], "ms": best4[2]}
         res4 = [None]
 
         def multi_fwd():
-            res4[0] = solve_multi(items4, group_threads=best4[0], **opts)
+            res4[0] = solve_multi(items4, group_threads=best4[0], placement=best4[1], **opts)
 
         def multi_fwd_bwd():
-            rs = solve_multi(items4, group_threads=best4[0], keep_factors=True, **opts)
+            rs = solve_multi(items4, group_threads=best4[0], placement=best4[1], keep_factors=True,
+                             **opts)
             for (pfx, *_), r, sl in zip(items4, rs, slacks4):
                 dVm = 2 * torch.relu(r.Vm - 1.06) - 2 * torch.relu(0.94 - r.Vm)
                 pfx.adjoint(dVm, torch.zeros_like(r.Vm), 2 * r.Pg * sl, None)
@@ -385,6 +392,24 @@ def gpu_leg(args, rank, world):
                              for a in (scj.Pd, scj.Qd, scj.Pg, scj.Vset)], precision="fp64")
             outj = pfj.export_jacobian(rj.Vm, rj.Va)
             jac_cases.append((jname, jn, gj, pfj, rj, outj))
+
+    sweep_cases = []
+    if "sweep" in secs:  # solve time vs batch size on the large grids (the shape of Table II)
+        for sname, sizes in (("c2", (4, 16, 64, 256, 1024)), ("c3", (4, 16, 64, 256)),
+                             ("c5", (4, 16, 64, 256))):
+            if sname in large:
+                gs_, scs_, pfs_ = large[sname][0], large[sname][1], large[sname][2]
+            else:
+                gs_ = configs.grid(sname)
+                scs_ = configs.scenarios(sname, max(sizes), gs_)
+                pfs_ = PowerFlow.from_grid(gs_)
+            ins_ = [torch.as_tensor(np.ascontiguousarray(a[:max(sizes)]), device=dev)
+                    for a in (scs_.Pd, scs_.Qd, scs_.Pg, scs_.Vset)]
+            if sname not in large:  # (a captured graph holds the large grids' workspaces)
+                pfs_.workspace(max(sizes), pfs_.make_opts("fp64", placement=3))
+            if args.autotune and sname not in large:
+                tuned[sname] = pfs_.autotune(*ins_, **opts)
+            sweep_cases.append((sname, gs_, pfs_, ins_, sizes))
 
     if "train" in secs:  # the layer inside a DC3-style training loop (network -> PF -> loss)
         from paper_2606_07099_gb300 import embedded as em
@@ -477,6 +502,22 @@ def gpu_leg(args, rank, world):
         t_jac = [timed(lambda c=c: c[3].export_jacobian(c[4].Vm, c[4].Va, out=c[5]), args.steps,
                        args.warmup, f"jacobian_{c[0]}_{c[1]}")
                  for c in (jac_cases if "jacobian" in secs else [])]
+        sweep_out = {}
+        for sname, gs_, pfs_, ins_, sizes in sweep_cases:
+            rows_ = []
+            for n_ in sizes:
+                sub = [t[:n_] for t in ins_]
+                for prec_ in (("mixed", "fp64") if n_ == 64 else ("mixed",)):
+                    o_ = dict(opts, precision=prec_)
+                    r_ = pfs_.solve(*sub, **o_)
+                    tn = timed(lambda: pfs_.solve(*sub, out=r_, **o_), 5, 3, f"sweep_{sname}_{n_}_{prec_}")
+                    ms_ = statistics.median(tn)
+                    rows_.append({"batch": n_, "precision": prec_, "ms": ms_,
+                                  "solves_per_s": n_ / (ms_ / 1e3),
+                                  "iters": [int(r_.iters.min().item()), int(r_.iters.max().item())],
+                                  "converged": int((r_.status == 0).sum().item()),
+                                  "max_final_mismatch": float(r_.final_mismatch.max().item())})
+            sweep_out[sname] = {"n_bus": gs_.n_bus, "rows": rows_}
         train_out = {}
         if "train" in secs:
             ksteps = max(5, min(args.steps, 20))
@@ -544,6 +585,11 @@ def gpu_leg(args, rank, world):
             "what": "pf_export_jacobian: J1 values of every scenario at its solution, written "
                     "in FP64 into the fixed block-diagonal (BDE) template",
             "cases": rows}
+    if "sweep" in secs:
+        extra["batch_sweep"] = {
+            "what": "one pf_solve per batch size (launch shape tuned on the full batch), "
+                    "median of 5 CUDA-event runs, L2 flushed before each; iters = [min, max]",
+            **sweep_out}
     if "memory" in secs:  # device bytes: the shared plan plus a fixed slot per scenario
         mem = {}
         for mname in ("c0", "c1", "c2", "c3", "c5"):
@@ -633,7 +679,7 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
-    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3,c5,qlim,jacobian,memory,train",
+    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3,c5,qlim,jacobian,memory,sweep,train",
                     help="timed sections to run (the first one, mixed, always runs)")
     ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
     args = ap.parse_args()

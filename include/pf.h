@@ -318,14 +318,18 @@ pf_err pf_multi_workspace_size(int n_jobs, const pf_job* jobs, const pf_solve_op
 
 /*
  * pf_solve_multi -- the scenarios of several networks (grids of different sizes, uneven
- * batches) in ONE persistent launch.  CTAs take scenarios from a device work counter,
- * the most expensive network's scenarios first, and run each with its own plan: same
- * Newton iteration, outputs and status as pf_solve per job.  All data lives in the
- * global workspace (placement PF_PLACE_GLOBAL; opts->placement must be 0 or that),
- * group_threads threads per scenario (0 = 128), instances_per_cta must be 0 or 1.
+ * batches) in ONE persistent launch.  CTAs take work items from a device work counter,
+ * the most expensive network's first, and run each with its own plan: same Newton
+ * iteration, outputs and status as pf_solve per job.  CTAs have group_threads threads
+ * (0 = 256; 64 to 512).  opts->placement PF_PLACE_AUTO gives each network its own form:
+ * networks of up to 160 buses one scenario per warp (group_threads / 32 per item, data
+ * on chip when they fit), larger ones the whole CTA per scenario with the factor in
+ * shared memory when it fits; PF_PLACE_GLOBAL runs every network with the whole CTA from
+ * the global workspace.  instances_per_cta must be 0 or 1.
  * With keep_factors, each job's handle remembers its part of the workspace, so
  * pf_adjoint(job.h, job.batch, ..., workspace + job_offsets[j], ...) differentiates it.
- * All handles must live on the current device.  Errors: PF_EINVAL, PF_ECUDA.
+ * All handles must live on the current device.  Errors: PF_EINVAL, PF_ENOTSUP (the
+ * jobs' shared memory does not fit one CTA of this size), PF_ECUDA.
  */
 pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
                       const pf_solve_opts* opts, void* workspace, size_t workspace_bytes,

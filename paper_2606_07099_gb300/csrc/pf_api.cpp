@@ -663,14 +663,51 @@ bool multi_ok(int n_jobs, const pf_job* jobs, const pf_solve_opts* opts) {
     if (n_jobs < 1 || n_jobs > pf::kMaxJobs || !jobs || !opts_ok(opts)) return false;
     if (opts->placement != PF_PLACE_AUTO && opts->placement != PF_PLACE_GLOBAL) return false;
     if (opts->instances_per_cta > 1) return false;
+    if (opts->group_threads != 0 && (opts->group_threads < 64 || opts->group_threads > 512))
+        return false;
     for (int j = 0; j < n_jobs; ++j)
         if (!jobs[j].h || jobs[j].batch < 1) return false;
     return true;
 }
 
-// the multi path keeps every job in the global workspace
+// Threads per CTA of a multi-network launch.
+int multi_threads(const pf_solve_opts* opts) { return opts->group_threads ? opts->group_threads : 256; }
+
+// Networks up to this size run one scenario per warp inside a multi-network launch (the
+// launch shape single-network tuning picks for them); larger ones use the whole CTA.
+constexpr int kWarpFormBuses = 160;
+
+// The form of one job inside a multi-network launch.  PF_PLACE_GLOBAL: every job in CTA
+// form with its data in the global workspace.  PF_PLACE_AUTO: small networks in warp
+// form (vectors and factor on chip when blockDim / 32 of them fit, else global), larger
+// ones in CTA form with the factor in shared memory when it fits.
+struct JobForm {
+    int warp;
+    int placement;
+};
+
+JobForm multi_form(const pf_handle* h, const pf_solve_opts* opts) {
+    if (opts->placement == PF_PLACE_GLOBAL) return {0, PF_PLACE_GLOBAL};
+    const pf::Plan& P = h->plan;
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    const size_t budget = smem_budget(h);
+    const size_t vec = pf::carve(nullptr, P.n_bus, P.n, ft, false, nullptr);
+    const size_t fac = pf::align_up((size_t)P.nnzb() * 4 * ft, 16);
+    const size_t wpc = (size_t)multi_threads(opts) / 32;
+    if (wpc >= 2 && P.n_bus <= kWarpFormBuses)
+        return {1, (vec + fac) * wpc <= budget ? PF_PLACE_ONCHIP : PF_PLACE_GLOBAL};
+    return {0, fac + (size_t)ft * 2 * P.n <= budget ? PF_PLACE_FACTOR : PF_PLACE_GLOBAL};
+}
+
 pf::SlotLayout multi_layout(const pf_handle* h, const pf_solve_opts* opts) {
-    return make_layout(h, opts->precision == PF_MIXED ? 4 : 8, opts->keep_factors, PF_PLACE_GLOBAL);
+    return make_layout(h, opts->precision == PF_MIXED ? 4 : 8, opts->keep_factors,
+                       multi_form(h, opts).placement);
+}
+
+// Dynamic shared memory one CTA needs for a job (warp form: one arena per warp).
+size_t multi_job_smem(const pf_handle* h, const pf_solve_opts* opts, const pf::SlotLayout& L) {
+    const size_t per = L.fwd.smem_bytes;
+    return multi_form(h, opts).warp ? per * (size_t)(multi_threads(opts) / 32) : per;
 }
 
 // Workspace: a 256-byte header (the work counter), then one region per job.
@@ -707,7 +744,8 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
     }
     size_t offs[pf::kMaxJobs];
     if (workspace_bytes < multi_layout_offsets(n_jobs, jobs, opts, offs)) return PF_EINVAL;
-    const int threads = opts->group_threads ? opts->group_threads : 128;
+    const int threads = multi_threads(opts);
+    const int wpc = threads / 32;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
     // most expensive scenarios first (factor blocks x levels as the cost estimate)
     int order[pf::kMaxJobs];
@@ -725,7 +763,8 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
     for (int k = 0; k < n_jobs; ++k) {
         const pf_job& J = jobs[order[k]];
         pf::SlotLayout L = multi_layout(J.h, opts);
-        smem = std::max(smem, L.fwd.smem_bytes);
+        smem = std::max(smem, multi_job_smem(J.h, opts, L));
+        M.warp_form[k] = multi_form(J.h, opts).warp;
         pf::SolveArgs& A = M.args[k];
         A = pf::SolveArgs{};
         A.batch = J.batch;
@@ -751,7 +790,7 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
         A.L = L;
         M.plans[k] = J.h->dp;
         M.first[k] = first;
-        first += J.batch;
+        first += M.warp_form[k] ? (J.batch + wpc - 1) / wpc : J.batch;
     }
     M.first[n_jobs] = first;
     M.total = first;
@@ -759,7 +798,8 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
     int per_sm = 0;
     cudaError_t e = ft == 4 ? pf::multi_blocks_per_sm<float>(threads, smem, &per_sm)
                             : pf::multi_blocks_per_sm<double>(threads, smem, &per_sm);
-    if (e != cudaSuccess || per_sm < 1) return PF_ECUDA;
+    if (e != cudaSuccess) return PF_ECUDA;
+    if (per_sm < 1) return PF_ENOTSUP;  // the jobs' shared memory does not fit one CTA
     const int grid = std::min(per_sm * jobs[0].h->num_sms, M.total);
     if (cudaMemsetAsync(M.counter, 0, sizeof(unsigned int), s) != cudaSuccess) return PF_ECUDA;
     e = ft == 4 ? pf::launch_solve_multi<float>(M, threads, grid, smem, s)
@@ -770,7 +810,7 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
         h->last_batch = M.args[k].batch;
         h->last_ft = ft;
         h->last_keep = M.args[k].keep_factors;
-        h->last_threads = threads;
+        h->last_threads = M.warp_form[k] ? 32 : threads;  // the adjoint: one CTA per scenario
         h->last_ws = M.args[k].ws;
         h->last_layout = M.args[k].L;
     }

@@ -695,12 +695,13 @@ __global__ void __launch_bounds__(256, 6) nr_solve_warps_kernel(DevPlan P, Solve
     solve_body<FT, VSM, FSM, XSM, true>(P, A, b, smem, nullptr, &unused);
 }
 
-// Several networks in one persistent launch: CTAs take scenarios from a work counter,
-// jobs in the order given (the host puts the most expensive first), and run each with
-// its own plan.  Every job keeps its data in the global workspace (the solve vector in
-// shared memory when it is small), so one launch shape serves all of them.
+// Several networks in one persistent launch: CTAs take work items from a counter, jobs in
+// the order given (the host puts the most expensive first), and run each with its own
+// plan and its own form: a job in CTA form solves one scenario per item with the whole
+// CTA (its factor in shared memory, or everything in the global workspace), a job in warp
+// form solves one scenario per warp, blockDim / 32 of them per item.
 template <typename FT>
-__global__ void __launch_bounds__(1024) nr_solve_multi_kernel(MultiArgs M) {
+__global__ void __launch_bounds__(512, 1) nr_solve_multi_kernel(MultiArgs M) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     __shared__ int s_bad;
@@ -713,12 +714,28 @@ __global__ void __launch_bounds__(1024) nr_solve_multi_kernel(MultiArgs M) {
         if (item >= M.total) break;
         int j = 0;
         while (j + 1 < M.n_jobs && item >= M.first[j + 1]) ++j;
-        const int b = item - M.first[j];
-        if (M.args[j].L.fwd.x_in_smem)
-            solve_body<FT, false, false, true, false>(M.plans[j], M.args[j], b, smem, red, &s_bad);
-        else
-            solve_body<FT, false, false, false, false>(M.plans[j], M.args[j], b, smem, red, &s_bad);
-        __syncthreads();  // the next scenario reuses the shared arrays
+        const int r = item - M.first[j];
+        const KernelSmem& K = M.args[j].L.fwd;
+        if (M.warp_form[j]) {
+            const int b = r * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+            int unused = 0;
+            if (K.vec_in_smem)
+                solve_body<FT, true, true, false, true>(M.plans[j], M.args[j], b, smem, nullptr, &unused);
+            else if (K.x_in_smem)
+                solve_body<FT, false, false, true, true>(M.plans[j], M.args[j], b, smem, nullptr, &unused);
+            else
+                solve_body<FT, false, false, false, true>(M.plans[j], M.args[j], b, smem, nullptr, &unused);
+        } else if (K.fac_in_smem) {
+            if (K.x_in_smem)
+                solve_body<FT, false, true, true, false>(M.plans[j], M.args[j], r, smem, red, &s_bad);
+            else
+                solve_body<FT, false, true, false, false>(M.plans[j], M.args[j], r, smem, red, &s_bad);
+        } else if (K.x_in_smem) {
+            solve_body<FT, false, false, true, false>(M.plans[j], M.args[j], r, smem, red, &s_bad);
+        } else {
+            solve_body<FT, false, false, false, false>(M.plans[j], M.args[j], r, smem, red, &s_bad);
+        }
+        __syncthreads();  // the next item reuses the shared arrays
     }
 }
 

@@ -101,7 +101,8 @@ struct MultiArgs {
     int n_jobs;
     int total;
     unsigned int* counter;  // work counter in the workspace, zeroed before the launch
-    int first[kMaxJobs + 1];
+    int first[kMaxJobs + 1];  // first work item of each job
+    int warp_form[kMaxJobs];  // 1: one scenario per warp (blockDim / 32 per item)
     DevPlan plans[kMaxJobs];
     SolveArgs args[kMaxJobs];
 };

@@ -153,6 +153,8 @@ cudaError_t launch_solve_multi(const MultiArgs& M, int threads, int grid, size_t
 
 template <typename FT>
 cudaError_t multi_blocks_per_sm(int threads, size_t smem, int* out) {
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(nr_solve_multi_kernel<FT>), smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, nr_solve_multi_kernel<FT>, threads, smem);
 }
 

@@ -392,17 +392,20 @@ class PFLayer(torch.autograd.Function):
 
 
 def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,
-                group_threads=0, keep_factors=False, ir_gate=0.0):
+                group_threads=0, keep_factors=False, ir_gate=0.0, placement=0):
     """Several networks in one persistent launch (pf_solve_multi).
 
     ``items`` is a list of ``(PowerFlow, Pd, Qd, Pg, Vset)``; returns one SolveResult per
     item.  With ``keep_factors`` each PowerFlow can run ``adjoint`` on its part afterwards.
+    ``placement`` 0 (auto) gives each network its own form (small ones one scenario per
+    warp, large ones the whole CTA with the factor on chip when it fits); PF_PLACE_GLOBAL
+    runs every network with the whole CTA from the global workspace.
     """
     if not 1 <= len(items) <= L.PF_MAX_JOBS:
         raise ValueError(f"1..{L.PF_MAX_JOBS} networks per launch")
     lib = L.load()
     opts = PowerFlow.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors,
-                               L.PF_PLACE_GLOBAL, 0, ir_gate)
+                               placement, 0, ir_gate)
     jobs = (L.Job * len(items))()
     results = []
     for k, (pf, Pd, Qd, Pg, Vset) in enumerate(items):

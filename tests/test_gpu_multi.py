@@ -27,10 +27,14 @@ def setup():
     return torch, powerflow, items, meta
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_multi_matches_one_launch_per_network(setup, precision):
+@pytest.mark.parametrize("precision,threads,placement", [("mixed", 128, 0), ("fp64", 128, 0),
+                                                        ("mixed", 512, 0), ("mixed", 128, 3)])
+def test_multi_matches_one_launch_per_network(setup, precision, threads, placement):
+    """Every form of the multi launch (per-network warp / CTA forms, factor on chip, or
+    all from the global workspace) gives bit-identical results to one pf_solve per
+    network: the summation order of every gather is fixed by the plan."""
     torch, pm, items, meta = setup
-    multi = pm.solve_multi(items, precision=precision, group_threads=128)
+    multi = pm.solve_multi(items, precision=precision, group_threads=threads, placement=placement)
     torch.cuda.synchronize()
     for (pf, *inputs), res, (name, g, sc) in zip(items, multi, meta):
         single = pf.solve(*inputs, precision=precision, group_threads=128, placement=3)
