@@ -323,6 +323,44 @@ __device__ void phase_fill(const DevPlan& P, const Arrays& a, double* fac) {
 template <typename FT>
 constexpr int kBatch = sizeof(FT) == 4 ? 4 : 2;
 
+// Sum of the Schur contributions L(i,k) U(k,j) of one target over its list entries
+// c, c + stride, ... < c1 (kBatch pairs at a time).
+template <typename FT>
+__device__ __forceinline__ Blk<FT> schur_gather(const DevPlan& P, const FT* fac, int c, int c1,
+                                                int stride) {
+    Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+    constexpr int NB = kBatch<FT>;
+    for (; c < c1; c += NB * stride) {
+        int2 lu[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            lu[k] = (c + k * stride < c1) ? __ldg(P.sch + c + k * stride) : make_int2(-1, -1);
+        Blk<FT> xl[NB], yu[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (lu[k].x >= 0) {
+                xl[k] = ldb(fac, lu[k].x);
+                yu[k] = ldb(fac, lu[k].y);
+            } else {
+                xl[k] = yu[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            acc.a += xl[k].a * yu[k].a + xl[k].b * yu[k].c;
+            acc.b += xl[k].a * yu[k].b + xl[k].b * yu[k].d;
+            acc.c += xl[k].c * yu[k].a + xl[k].d * yu[k].c;
+            acc.d += xl[k].c * yu[k].b + xl[k].d * yu[k].d;
+        }
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ Blk<T> sub_blk(Blk<T> m, Blk<T> s) {
+    return {m.a - s.a, m.b - s.b, m.c - s.c, m.d - s.d};
+}
+
 // Right-looking, one elimination-tree level at a time.  Phase A scales the L columns of
 // the level's pivots; phase B gathers every Schur update of the level into its target
 // block (no two threads write the same block) and replaces the level's pivot blocks by
@@ -342,39 +380,32 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
         }
         gsync<W>();
         const int t0 = __ldg(P.sch_tptr + l), t1 = __ldg(P.sch_tptr + l + 1);
-        for (int t = t0 + GTID; t < t1; t += GSZ) {
-            const int c0 = __ldg(P.sch_cptr + t), c1 = __ldg(P.sch_cptr + t + 1);
-            Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
-            constexpr int NB = kBatch<FT>;
-            for (int c = c0; c < c1; c += NB) {
-                int2 lu[NB];
-#pragma unroll
-                for (int k = 0; k < NB; ++k) lu[k] = (c + k < c1) ? __ldg(P.sch + c + k) : make_int2(-1, -1);
-                Blk<FT> xl[NB], yu[NB];
-#pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    if (lu[k].x >= 0) {
-                        xl[k] = ldb(fac, lu[k].x);
-                        yu[k] = ldb(fac, lu[k].y);
-                    } else {
-                        xl[k] = yu[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
-                    }
+        const int G = __ldg(P.lev_g + l).z;  // lanes per target (a power of two <= 32; uniform)
+        if (G == 1) {  // one thread per target
+            for (int t = t0 + GTID; t < t1; t += GSZ) {
+                const Blk<FT> acc = schur_gather(P, fac, __ldg(P.sch_cptr + t),
+                                                 __ldg(P.sch_cptr + t + 1), 1);
+                const int tg = __ldg(P.sch_tgt + t);
+                stb(fac, tg, sub_blk(ldb(fac, tg), acc));
+            }
+        } else {  // G lanes per target; every lane runs the same rounds
+            const int sub = GTID & (G - 1), nrg = GSZ / G;
+            for (int tb = t0; tb < t1; tb += nrg) {
+                const int t = tb + GTID / G;
+                const bool act = t < t1;
+                Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+                if (act) acc = schur_gather(P, fac, __ldg(P.sch_cptr + t) + sub, __ldg(P.sch_cptr + t + 1), G);
+                for (int o = G >> 1; o; o >>= 1) {  // butterfly over the target's lanes
+                    acc.a += __shfl_xor_sync(0xffffffffu, acc.a, o);
+                    acc.b += __shfl_xor_sync(0xffffffffu, acc.b, o);
+                    acc.c += __shfl_xor_sync(0xffffffffu, acc.c, o);
+                    acc.d += __shfl_xor_sync(0xffffffffu, acc.d, o);
                 }
-#pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    acc.a += xl[k].a * yu[k].a + xl[k].b * yu[k].c;
-                    acc.b += xl[k].a * yu[k].b + xl[k].b * yu[k].d;
-                    acc.c += xl[k].c * yu[k].a + xl[k].d * yu[k].c;
-                    acc.d += xl[k].c * yu[k].b + xl[k].d * yu[k].d;
+                if (act && sub == 0) {
+                    const int tg = __ldg(P.sch_tgt + t);
+                    stb(fac, tg, sub_blk(ldb(fac, tg), acc));
                 }
             }
-            const int tg = __ldg(P.sch_tgt + t);
-            Blk<FT> m = ldb(fac, tg);
-            m.a -= acc.a;
-            m.b -= acc.b;
-            m.c -= acc.c;
-            m.d -= acc.d;
-            stb(fac, tg, m);
         }
         for (int p = __ldg(P.lev_ptr + l) + GTID; p < __ldg(P.lev_ptr + l + 1); p += GSZ) {
             const int dk = __ldg(P.lu_diag + p);
@@ -393,62 +424,97 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
 // the U part (upper sweeps) of row p in the L+U pattern.  TRANS sweeps read the block at
 // the mirrored position, transposed (row p of U^T / L^T).  The stored pivot inverse (or
 // its transpose) is applied by the upper sweep of LU and by the first sweep of (LU)^T.
+// The gathered sum of one row over its entries e0 + first, e0 + first + stride, ... < e1
+// (kBatch at a time): s0, s1 += M_e x_q(e) (or M_e^T x_q(e) for the transposed sweeps).
+template <typename FT, bool TRANS>
+__device__ __forceinline__ void row_gather(const DevPlan& P, const FT* fac, const FT* x, int e,
+                                           int e1, int stride, FT& s0, FT& s1) {
+    constexpr int NB = kBatch<FT>;
+    for (; e < e1; e += NB * stride) {
+        int q[NB], pos[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int ek = e + k * stride;
+            const bool ok = ek < e1;
+            q[k] = ok ? __ldg(P.lu_col + ek) : -1;
+            pos[k] = ok ? (TRANS ? __ldg(P.lu_mirror + ek) : ek) : 0;
+        }
+        Blk<FT> m[NB];
+        FT y0[NB], y1[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (q[k] >= 0) {
+                m[k] = ldb(fac, pos[k]);
+                y0[k] = x[2 * q[k]];
+                y1[k] = x[2 * q[k] + 1];
+            } else {
+                m[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
+                y0[k] = y1[k] = FT(0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (TRANS) {
+                s0 += m[k].a * y0[k] + m[k].c * y1[k];
+                s1 += m[k].b * y0[k] + m[k].d * y1[k];
+            } else {
+                s0 += m[k].a * y0[k] + m[k].b * y1[k];
+                s1 += m[k].c * y0[k] + m[k].d * y1[k];
+            }
+        }
+    }
+}
+
+// x_p <- op(x_p - s) with the row's pivot (inverted) for the sweeps that divide.
+template <typename FT, bool UPPER, bool TRANS>
+__device__ __forceinline__ void row_finish(const FT* fac, FT* x, int p, int dg, FT s0, FT s1) {
+    constexpr bool DIAG = UPPER != TRANS;
+    const FT x0 = x[2 * p] - s0, x1 = x[2 * p + 1] - s1;
+    if (DIAG) {
+        const Blk<FT> d = ldb(fac, dg);
+        if (TRANS) {
+            x[2 * p] = d.a * x0 + d.c * x1;
+            x[2 * p + 1] = d.b * x0 + d.d * x1;
+        } else {
+            x[2 * p] = d.a * x0 + d.b * x1;
+            x[2 * p + 1] = d.c * x0 + d.d * x1;
+        }
+    } else {
+        x[2 * p] = x0;
+        x[2 * p + 1] = x1;
+    }
+}
+
 template <typename FT, bool UPPER, bool TRANS, bool W>
 __device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT* x, int l) {
-    constexpr bool DIAG = UPPER != TRANS;
-    const int r1 = __ldg(P.lev_ptr + l + 1);
-    for (int p = __ldg(P.lev_ptr + l) + GTID; p < r1; p += GSZ) {
-        const int dg = __ldg(P.lu_diag + p);
-        const int e0 = UPPER ? dg + 1 : __ldg(P.lu_ptr + p);
-        const int e1 = UPPER ? __ldg(P.lu_ptr + p + 1) : dg;
+    const int r0 = __ldg(P.lev_ptr + l), r1 = __ldg(P.lev_ptr + l + 1);
+    const int4 lg = __ldg(P.lev_g + l);
+    const int G = UPPER ? lg.y : lg.x;  // lanes per row (a power of two <= 32; uniform)
+    if (G == 1) {  // one thread per row
+        for (int p = r0 + GTID; p < r1; p += GSZ) {
+            const int dg = __ldg(P.lu_diag + p);
+            FT s0 = FT(0), s1 = FT(0);
+            row_gather<FT, TRANS>(P, fac, x, UPPER ? dg + 1 : __ldg(P.lu_ptr + p),
+                                  UPPER ? __ldg(P.lu_ptr + p + 1) : dg, 1, s0, s1);
+            row_finish<FT, UPPER, TRANS>(fac, x, p, dg, s0, s1);
+        }
+        return;
+    }
+    // G lanes per row; every lane runs the same rounds (the shuffles need whole warps)
+    const int sub = GTID & (G - 1), nrg = GSZ / G;
+    for (int pb = r0; pb < r1; pb += nrg) {
+        const int p = pb + GTID / G;
+        const bool act = p < r1;
+        const int dg = act ? __ldg(P.lu_diag + p) : 0;
         FT s0 = FT(0), s1 = FT(0);
-        constexpr int NB = kBatch<FT>;
-        for (int e = e0; e < e1; e += NB) {
-            int q[NB], pos[NB];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                const bool ok = e + k < e1;
-                q[k] = ok ? __ldg(P.lu_col + e + k) : -1;
-                pos[k] = ok ? (TRANS ? __ldg(P.lu_mirror + e + k) : e + k) : 0;
-            }
-            Blk<FT> m[NB];
-            FT y0[NB], y1[NB];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (q[k] >= 0) {
-                    m[k] = ldb(fac, pos[k]);
-                    y0[k] = x[2 * q[k]];
-                    y1[k] = x[2 * q[k] + 1];
-                } else {
-                    m[k] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
-                    y0[k] = y1[k] = FT(0);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                if (TRANS) {
-                    s0 += m[k].a * y0[k] + m[k].c * y1[k];
-                    s1 += m[k].b * y0[k] + m[k].d * y1[k];
-                } else {
-                    s0 += m[k].a * y0[k] + m[k].b * y1[k];
-                    s1 += m[k].c * y0[k] + m[k].d * y1[k];
-                }
-            }
+        if (act)
+            row_gather<FT, TRANS>(P, fac, x, (UPPER ? dg + 1 : __ldg(P.lu_ptr + p)) + sub,
+                                  UPPER ? __ldg(P.lu_ptr + p + 1) : dg, G, s0, s1);
+        for (int o = G >> 1; o; o >>= 1) {  // butterfly over the row's lanes: a fixed order
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         }
-        const FT x0 = x[2 * p] - s0, x1 = x[2 * p + 1] - s1;
-        if (DIAG) {
-            const Blk<FT> d = ldb(fac, dg);
-            if (TRANS) {
-                x[2 * p] = d.a * x0 + d.c * x1;
-                x[2 * p + 1] = d.b * x0 + d.d * x1;
-            } else {
-                x[2 * p] = d.a * x0 + d.b * x1;
-                x[2 * p + 1] = d.c * x0 + d.d * x1;
-            }
-        } else {
-            x[2 * p] = x0;
-            x[2 * p + 1] = x1;
-        }
+        if (act && sub == 0) row_finish<FT, UPPER, TRANS>(fac, x, p, dg, s0, s1);
     }
 }
 

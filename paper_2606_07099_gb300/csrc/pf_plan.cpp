@@ -299,11 +299,17 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         P.schur_ops += (long long)contrib.size();
     }
 
-    // lanes per gathered row: the smallest power of two covering the level's longest
-    // gather, capped at one warp
-    auto lanes = [](int len) {
+    // lanes per gathered row.  One thread gathers a row, except on levels of few rows
+    // (<= 64) whose longest gather exceeds 32 blocks: the top of the elimination tree,
+    // where a level is a handful of long, nearly dense rows and one thread per row would
+    // make the whole level wait on one long sequential gather.  There a row is split over
+    // a power-of-two group of lanes (about four blocks each) and reduced by shuffles.  The
+    // choice depends on the plan only, so the summation order (and every result) is the
+    // same for any number of threads per scenario.
+    auto lanes = [](int len, int rows) {
+        if (len <= 32 || rows > 64) return 1;
         int g = 1;
-        while (g < len && g < 32) g <<= 1;
+        while (g * 4 < len && g < 32) g <<= 1;
         return g;
     };
     P.lev_gL.assign(n_levels, 1);
@@ -317,9 +323,11 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         }
         for (int t = P.sch_tptr[l]; t < P.sch_tptr[l + 1]; ++t)
             mS = std::max(mS, P.sch_cptr[t + 1] - P.sch_cptr[t]);
-        P.lev_gL[l] = lanes(mL);
-        P.lev_gU[l] = lanes(mU);
-        P.lev_gS[l] = lanes(mS);
+        const int rows = P.lev_ptr[l + 1] - P.lev_ptr[l];
+        const int targets = P.sch_tptr[l + 1] - P.sch_tptr[l];
+        P.lev_gL[l] = lanes(mL, rows);
+        P.lev_gU[l] = lanes(mU, rows);
+        P.lev_gS[l] = lanes(mS, targets);
     }
 
     // scalar nonzeros of J1 (rows dP_{B\R}, dQ_D; columns theta_{B\R}, Vm_D)
