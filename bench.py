@@ -44,6 +44,10 @@ FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 
 
+# the device code of the solve kernels (a committed capture is valid while these are unchanged)
+KERNEL_SOURCES = ("pf_body.cuh", "pf_kernels.cu", "pf_device.cuh")
+
+
 def profiled_traffic(kernel_json="nr_solve_c1_mixed.json"):
     """DRAM bytes per launch from the committed ncu capture, if the kernel source is
     unchanged since the capture (else None)."""
@@ -52,7 +56,7 @@ def profiled_traffic(kernel_json="nr_solve_c1_mixed.json"):
         with open(os.path.join(ROOT, "profiles", kernel_json)) as fh:
             prof = json.load(fh)
         src = b""
-        for f in ("pf_kernels.cu", "pf_device.cuh"):
+        for f in KERNEL_SOURCES:
             with open(os.path.join(ROOT, "paper_2606_07099_gb300", "csrc", f), "rb") as fh:
                 src += fh.read()
         if hashlib.sha256(src).hexdigest()[:16] != prof["source_sha256_16"]:
@@ -395,9 +399,11 @@ def gpu_leg(args, rank, world):
 
     sweep_cases = []
     if "sweep" in secs:  # solve time vs batch size on the large grids (the shape of Table II)
-        for sname, sizes in (("c2", (4, 16, 64, 256, 1024)), ("c3", (4, 16, 64, 256)),
-                             ("c5", (4, 16, 64, 256))):
-            if sname in large:
+        for sname, sizes in (("c1", (256, 1024, 2048, 4096)), ("c2", (4, 16, 64, 256, 1024)),
+                             ("c3", (4, 16, 64, 256)), ("c5", (4, 16, 64, 256))):
+            if sname == "c1":  # the headline network (its handle is tuned already)
+                gs_, scs_, pfs_ = g, sc, pf
+            elif sname in large:
                 gs_, scs_, pfs_ = large[sname][0], large[sname][1], large[sname][2]
             else:
                 gs_ = configs.grid(sname)
@@ -405,9 +411,9 @@ def gpu_leg(args, rank, world):
                 pfs_ = PowerFlow.from_grid(gs_)
             ins_ = [torch.as_tensor(np.ascontiguousarray(a[:max(sizes)]), device=dev)
                     for a in (scs_.Pd, scs_.Qd, scs_.Pg, scs_.Vset)]
-            if sname not in large:  # (a captured graph holds the large grids' workspaces)
+            if sname not in large and sname != "c1":  # (captured graphs hold the others')
                 pfs_.workspace(max(sizes), pfs_.make_opts("fp64", placement=3))
-            if args.autotune and sname not in large:
+            if args.autotune and sname not in large and sname != "c1":
                 tuned[sname] = pfs_.autotune(*ins_, **opts)
             sweep_cases.append((sname, gs_, pfs_, ins_, sizes))
 
