@@ -515,10 +515,14 @@ def gpu_leg(args, rank, world):
                 sub = [t[:n_] for t in ins_]
                 for prec_ in (("mixed", "fp64") if n_ == 64 else ("mixed",)):
                     o_ = dict(opts, precision=prec_)
+                    # launch shape for this batch size (a few scenarios of a large grid
+                    # want more threads each than a full batch does); setup, not timed
+                    shape_ = (pfs_.autotune(*sub, **o_) if args.autotune and sname != "c1"
+                              else None)
                     r_ = pfs_.solve(*sub, **o_)
                     tn = timed(lambda: pfs_.solve(*sub, out=r_, **o_), 5, 3, f"sweep_{sname}_{n_}_{prec_}")
                     ms_ = statistics.median(tn)
-                    rows_.append({"batch": n_, "precision": prec_, "ms": ms_,
+                    rows_.append({"batch": n_, "precision": prec_, "ms": ms_, "shape": shape_,
                                   "solves_per_s": n_ / (ms_ / 1e3),
                                   "iters": [int(r_.iters.min().item()), int(r_.iters.max().item())],
                                   "converged": int((r_.status == 0).sum().item()),
@@ -593,8 +597,9 @@ def gpu_leg(args, rank, world):
             "cases": rows}
     if "sweep" in secs:
         extra["batch_sweep"] = {
-            "what": "one pf_solve per batch size (launch shape tuned on the full batch), "
-                    "median of 5 CUDA-event runs, L2 flushed before each; iters = [min, max]",
+            "what": "one pf_solve per batch size (launch shape autotuned at that size, except "
+                    "the headline network, tuned on its full batch), median of 5 CUDA-event "
+                    "runs, L2 flushed before each; iters = [min, max]",
             **sweep_out}
     if "memory" in secs:  # device bytes: the shared plan plus a fixed slot per scenario
         mem = {}

@@ -277,9 +277,10 @@ pf_err pf_solve_qlim(pf_handle* h, int batch,
 /*
  * pf_autotune -- picks the launch configuration (threads per scenario and placement
  * of the scenario data) for this handle, `batch` and opts->precision by timing
- * pf_solve on the given inputs (device, as pf_solve) for every candidate: 32..512
+ * pf_solve on the given inputs (device, as pf_solve) for every candidate: 32..1024
  * threads per scenario, or 2, 4 or 8 one-warp scenarios per CTA, times every placement
- * that fits.  The fastest one is kept in
+ * that fits (the best shape depends on the batch: a few scenarios of a large network
+ * want the most threads each, thousands of small ones the most scenarios per SM).  The fastest one is kept in
  * the handle and used by later pf_solve calls with group_threads = 0 and placement =
  * PF_PLACE_AUTO at the same precision; *out (nullable) receives it.  The workspace
  * must hold pf_workspace_size for PF_PLACE_GLOBAL; the call allocates small temporary

@@ -613,7 +613,8 @@ pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, 
     pf_tune_result best{0, 0, 0, 0.f};
     pf_err err = PF_OK;
     // (threads per scenario, scenarios per CTA)
-    const int cands[][2] = {{32, 1}, {64, 1}, {128, 1}, {256, 1}, {512, 1}, {32, 2}, {32, 4}, {32, 8}};
+    const int cands[][2] = {{32, 1},  {64, 1}, {128, 1}, {256, 1}, {512, 1},
+                            {1024, 1}, {32, 2}, {32, 4},  {32, 8}};
     for (int pl = PF_PLACE_ONCHIP; pl <= PF_PLACE_FACTOR && err == PF_OK; ++pl) {
         // skip placements that fall back to another one (they would time a duplicate)
         const int ft = opts->precision == PF_MIXED ? 4 : 8;
