@@ -121,7 +121,7 @@ def test_autotune_keeps_results(PowerFlow):
     pf = PowerFlow.from_grid(g)
     ref = run_gpu(pf, sc, precision="mixed", group_threads=128, placement=1)
     best = pf.autotune(*to_dev(sc), precision="mixed")
-    assert best["group_threads"] in (32, 64, 128, 256, 512)
+    assert best["group_threads"] in (32, 64, 128, 256, 512, 1024)
     assert best["placement"] in (1, 2, 3, 4) and best["ms"] > 0
     assert best["instances_per_cta"] in (1, 2, 4, 8)
     out = run_gpu(pf, sc, precision="mixed")  # now uses the tuned configuration
@@ -168,6 +168,22 @@ def test_thread_mapping_does_not_change_results(PowerFlow):
     outm = run_gpu(pf, sc, precision="mixed", group_threads=160)
     for k in refm:
         assert np.array_equal(refm[k], outm[k]), k
+
+
+@pytest.mark.parametrize("name,n", [("c2", 24), ("c4c", 16)])
+def test_split_gathers_do_not_depend_on_threads(PowerFlow, name, n):
+    """Networks whose top-of-tree levels split long gathers over lane groups (the plan
+    fixes the lanes per level): bit-identical for every number of threads per scenario,
+    including non-power-of-two ones and the warp-per-scenario form."""
+    g, sc = workload(name, n)
+    pf = PowerFlow.from_grid(g)
+    for prec in ("fp64", "mixed"):
+        ref = run_gpu(pf, sc, precision=prec, group_threads=128, placement=3)
+        for th, ipc in ((32, 1), (96, 1), (160, 1), (512, 1), (1024, 1), (32, 2)):
+            out = run_gpu(pf, sc, precision=prec, group_threads=th, placement=3,
+                          instances_per_cta=ipc)
+            for k in ref:
+                assert np.array_equal(ref[k], out[k]), (prec, th, ipc, k)
 
 
 def test_two_bus_closed_form_on_gpu(PowerFlow):
