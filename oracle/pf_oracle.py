@@ -230,14 +230,14 @@ def nr_solve_qlim(Y, bus_type, Pd, Qd, Pg, Vset, Qmin, Qmax, tol=1e-8, max_iter=
     """Newton-Raphson with reactive-power limits at the PV buses (PV -> PQ switching).
 
     Not part of the paper's method: the limit handling of production power-flow
-    tools, on top of Step 1 / Step 2.  Round 0 is ``nr_solve``.  When a round has
-    converged, the recovered qg_i = Q_i + qd_i of every bus that is still PV is
-    compared with [Qmin_i, Qmax_i].  All violators at once become PQ buses whose
+    tools, on top of Step 1 / Step 2.  The first Newton pass is ``nr_solve``.  When a
+    pass has converged, the recovered qg_i = Q_i + qd_i of every bus that is still PV
+    is compared with [Qmin_i, Qmax_i].  All violators at once become PQ buses whose
     reactive generation is fixed at the violated limit (Q_spec_i = qlim_i - qd_i; their
     Vm joins z1), and Newton continues from the current voltages on the new partition,
-    with max_iter steps per round.  A switched bus stays PQ.  The result is CONVERGED
-    when a converged round leaves no violator, MAXITER when a round runs out of steps
-    or violators remain after ``max_rounds`` switching rounds, and DIVERGED/SINGULAR as
+    with max_iter steps per pass.  A switched bus stays PQ.  The result is CONVERGED
+    when a converged pass leaves no violator, MAXITER when a pass runs out of steps
+    or violators remain after ``max_rounds`` switching passes, and DIVERGED/SINGULAR as
     in ``nr_solve``.  Returns the fields of ``nr_solve`` (Pg and Qg on the original bus
     sets; iters = Newton steps over all rounds) plus the final per-bus ``bus_type`` and
     the number of switching ``rounds``.
