@@ -220,6 +220,34 @@ def alg_counts(info: dict, n_bus: int, iters: np.ndarray, ir_steps: int, precisi
     return f64, f32, hbm
 
 
+def rank_scenarios(workload, g, rank, world):
+    """This rank's scenarios.  One GPU solves the workload's batch; with N ranks, rank r
+    solves the r-th of N equal batches drawn from one seeded stream, so every rank does
+    the same amount of distinct work (weak scaling, no collective on the data path)."""
+    from synthgrid import Scenarios, configs
+    if world == 1:
+        return configs.scenarios(workload, g=g)
+    n = configs.CONFIGS[workload]["n_scen"]
+    sc = configs.scenarios(workload, n * world, g)
+    part = slice(rank * n, (rank + 1) * n)
+    return Scenarios(Pd=sc.Pd[part].copy(), Qd=sc.Qd[part].copy(), Pg=sc.Pg[part].copy(),
+                     Vset=sc.Vset[part].copy())
+
+
+def over_ranks(world, dev, total_ms, count):
+    """(the slowest rank's timed total in ms, the sum of a count over the ranks): the
+    job's time is the max over ranks, its work the units every rank processed."""
+    if world == 1:
+        return total_ms, count
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=dev)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(c.item()))
+
+
 def gpu_leg(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -230,7 +258,7 @@ def gpu_leg(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     g = configs.grid(args.workload)
-    sc = configs.scenarios(args.workload, g=g)
+    sc = rank_scenarios(args.workload, g, rank, world)
     N, nb = sc.n, g.n_bus
     pf = PowerFlow.from_grid(g)
     info = pf.info()
@@ -628,7 +656,8 @@ def gpu_leg(args, rank, world):
                          "(forward, implicit backward, optimiser) replayed from one CUDA graph, "
                          "else eager PyTorch around the libpf calls"),
             "unit": "samples/s", **train_out}
-    value = world * conv * K / (T_mixed / 1e3)
+    T_job, conv_job = over_ranks(world, dev, sum(t_mixed), conv)
+    value = conv_job * K / (T_job / 1e3)
     ms_launch = statistics.mean(t_mixed)
     f64, f32, hbm_bytes = alg_counts(info, nb, its, args.ir_steps, "mixed")
     # ALU roofline: the kernel needs at least max(F64/peak64, F32/peak32) seconds
@@ -655,7 +684,7 @@ def gpu_leg(args, rank, world):
         "fwd_bwd_c2": {"value": world * 1024 * K / (T_fb2 / 1e3), "unit": "fwd+bwd/s",
                        "ms_per_step": T_fb2 / K,
                        "workload": "1354-bus grid, 1024 scenarios, config-2 loss cotangents"},
-        "e2e": {"value": world * conve * K / (T_e2e / 1e3), "unit": UNIT,
+        "e2e": {"value": over_ranks(world, dev, 0.0, conve)[1] * K / (T_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N},
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved_eq, "peak": FP64_PEAK_TFLOPS,
