@@ -329,6 +329,32 @@ def adjoint(Y, bus_type, Vm, Va, dVm, dVa, dPg=None, dQg=None):
 # --------------------------------------------------------------------------
 # Batch helpers
 # --------------------------------------------------------------------------
+def adjoint_qlim(Y, bus_type, final_bus_type, Vm, Va, dVm, dVa, dPg=None, dQg=None):
+    """Implicit-differentiation gradients of a converged ``nr_solve_qlim`` result.
+
+    At the solution a switched bus k (PV in ``bus_type``, PQ in ``final_bus_type``) is a
+    PQ bus whose reactive injection is fixed: Q_spec_k = qlim_k - qd_k, with pg_k still
+    an input.  So the gradients are those of ``adjoint`` on the final partition, with
+    the switched buses' pg and qlim entering like (minus) a load: pd'_k = pd_k - pg_k,
+    qd'_k = qd_k - qlim_k.  The outputs Pg_out[k] = pg_k and Qg_out[k] = qlim_k pass
+    their cotangents straight to pg_k and qlim_k.  Returns dPd, dQd, dPg (on the
+    original G), dVset (on the final B\\D: zero at switched buses) and dQlim (at switched
+    buses, the gradient with respect to the limit they sit at; zero elsewhere).
+    """
+    bt0 = np.asarray(bus_type)
+    bt = np.asarray(final_bus_type)
+    n = bt0.shape[0]
+    sw = (bt0 == PV) & (bt == PQ)
+    dPg_out = np.zeros(n) if dPg is None else np.asarray(dPg, float)
+    dQg_out = np.zeros(n) if dQg is None else np.asarray(dQg, float)
+    a = adjoint(Y, bt, Vm, Va, dVm, dVa, np.where(sw, 0.0, dPg_out), np.where(sw, 0.0, dQg_out))
+    dPg_in = a["dPg"].copy()
+    dPg_in[sw] = dPg_out[sw] - a["dPd"][sw]
+    dQlim = np.zeros(n)
+    dQlim[sw] = dQg_out[sw] - a["dQd"][sw]
+    return dict(dPd=a["dPd"], dQd=a["dQd"], dPg=dPg_in, dVset=a["dVset"], dQlim=dQlim)
+
+
 def solve_batch(Y, bus_type, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20):
     """Loop ``nr_solve`` over the rows of [n_scen, n_bus] inputs."""
     N = Pd.shape[0]

@@ -267,3 +267,35 @@ def test_bad_arguments_raise(PowerFlow):
         pf.solve(Pd.float(), Qd, Pg, Vset)
     with pytest.raises(RuntimeError):
         pf.adjoint(Pd, Pd)  # no preceding solve with keep_factors
+
+
+def test_new_entry_points_reject_bad_arguments(PowerFlow):
+    """The export, block-diagonal pattern, reactive-limit and multi-network entry points
+    refuse invalid arguments with an error code (no launch)."""
+    import ctypes as C
+    import torch
+    from paper_2606_07099_gb300 import _lib
+    from paper_2606_07099_gb300.powerflow import solve_multi
+    lib = _lib.load()
+    g, sc = workload("c0", 4)
+    pf = PowerFlow.from_grid(g)
+    Pd, Qd, Pg, Vset = to_dev(sc)
+    vals = torch.empty(4, pf.info()["nnz_j1"], dtype=torch.float64, device="cuda")
+    assert lib.pf_export_jacobian(pf._h, 0, Pd.data_ptr(), Pd.data_ptr(), vals.data_ptr(), None) == _lib.PF_EINVAL
+    assert lib.pf_export_jacobian(pf._h, 4, None, Pd.data_ptr(), vals.data_ptr(), None) == _lib.PF_EINVAL
+    ip = torch.empty(8, dtype=torch.int32, device="cuda")
+    # batch x nnz(J1) beyond int32 indices
+    assert lib.pf_bde_pattern(pf._h, 1 << 30, ip.data_ptr(), ip.data_ptr(), None) == _lib.PF_EINVAL
+    assert lib.pf_jacobian_pattern(pf._h, None, None) == _lib.PF_EINVAL
+    big = torch.full_like(Pd, 1e30)
+    with pytest.raises(_lib.PFError):
+        pf.solve_qlim(Pd, Qd, Pg, Vset, -big, big, max_rounds=-1)
+    opts = PowerFlow.make_opts("mixed", keep_factors=True)
+    n = C.c_size_t(0)
+    assert lib.pf_qlim_workspace_size(pf._h, 4, C.byref(opts), C.byref(n)) == _lib.PF_EINVAL
+    with pytest.raises(_lib.PFError):  # multi-network CTAs need 64..512 threads
+        solve_multi([(pf, Pd, Qd, Pg, Vset)], group_threads=32)
+    with pytest.raises(_lib.PFError):
+        solve_multi([(pf, Pd, Qd, Pg, Vset)], group_threads=1024)
+    torch.cuda.synchronize()
+    pf.close()

@@ -121,3 +121,56 @@ def test_round_limit_reports_maxiter_and_keeps_the_partition():
     a = O.nr_solve(Y, g.bus_type, sc.Pd[0], sc.Qd[0], sc.Pg[0], sc.Vset[0])
     assert np.array_equal(a["Vm"], r["Vm"]) and a["iters"] == r["iters"]
     assert SLACK in g.bus_type and PQ in g.bus_type
+
+
+def test_qlim_adjoint_matches_central_differences():
+    """Gradients of a switched solution (upper and lower limits binding) with respect to
+    every input coordinate -- loads, pg of kept and switched PV buses, Vset of kept
+    buses, and the binding limits -- against central differences of the switched solve
+    (h = 1e-6, small enough to keep the partition)."""
+    g = scale_loads(small_grid(14, 6, n_slack=1, n_pv=5), 0.8)
+    Y = ybus_of(g)
+    sc = make_scenarios(g, 1, 0.9, 1.1, 6)
+    base = _base(g, sc, 0, Y)
+    G = np.flatnonzero(g.bus_type == PV)
+    order = G[np.argsort(base["Qg"][G])]
+    Qmin, Qmax = np.full(g.n_bus, -INF), np.full(g.n_bus, INF)
+    Qmax[order[-1]] = base["Qg"][order[-1]] - 0.05
+    Qmin[order[0]] = base["Qg"][order[0]] + 0.05
+    x0 = {"Pd": sc.Pd[0], "Qd": sc.Qd[0], "Pg": sc.Pg[0], "Vset": sc.Vset[0],
+          "Qmin": Qmin, "Qmax": Qmax}
+
+    def solve(x):
+        r = O.nr_solve_qlim(Y, g.bus_type, x["Pd"], x["Qd"], x["Pg"], x["Vset"], x["Qmin"],
+                            x["Qmax"], tol=1e-13, max_iter=40)
+        assert r["status"] == O.CONVERGED
+        return r
+
+    r = solve(x0)
+    sw = np.flatnonzero((g.bus_type == PV) & (r["bus_type"] == PQ))
+    assert set(sw) == {order[0], order[-1]}
+    rng = np.random.default_rng(9)
+    w = {k: rng.normal(size=g.n_bus) for k in ("Vm", "Va", "Pg", "Qg")}
+    loss = lambda rr: (w["Vm"] @ rr["Vm"] + w["Va"] @ rr["Va"] + w["Pg"] @ rr["Pg"]
+                       + w["Qg"] @ rr["Qg"])
+    adj = O.adjoint_qlim(Y, g.bus_type, r["bus_type"], r["Vm"], r["Va"], w["Vm"], w["Va"],
+                         w["Pg"], w["Qg"])
+    kept = np.flatnonzero(r["bus_type"] != PQ)
+    coords = ([("Pd", i) for i in np.flatnonzero(sc.Pd[0] != 0)[:6]]
+              + [("Qd", i) for i in np.flatnonzero(sc.Qd[0] != 0)[:6]] + [("Qd", sw[0])]
+              + [("Pg", i) for i in G] + [("Vset", i) for i in kept]
+              + [("Qmax", order[-1]), ("Qmin", order[0])])
+    key = {"Pd": "dPd", "Qd": "dQd", "Pg": "dPg", "Vset": "dVset"}
+    h = 1e-6
+    for name, i in coords:
+        vals = []
+        for sgn in (1, -1):
+            x = {k: v.copy() for k, v in x0.items()}
+            x[name][i] += sgn * h
+            rr = solve(x)
+            assert np.array_equal(rr["bus_type"], r["bus_type"])
+            vals.append(loss(rr))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = adj["dQlim"][i] if name in ("Qmin", "Qmax") else adj[key[name]][i]
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, i, fd, an)
+    assert np.all(adj["dVset"][sw] == 0)
