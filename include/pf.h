@@ -261,9 +261,10 @@ pf_err pf_qlim_workspace_size(const pf_handle* h, int batch, const pf_solve_opts
  * rounds.  status: PF_CONVERGED when a converged round leaves no violator;
  * PF_MAXITER when a round ran out of steps or violators remain after max_rounds rounds
  * (the outputs are then the last converged point, on its partition); PF_DIVERGED /
- * PF_SINGULAR as pf_solve.  The workspace (pf_qlim_workspace_size) keeps no factors:
- * keep_factors must be 0 and pf_adjoint does not apply to this call.
- * Errors: as pf_solve, and PF_EINVAL for NULL limits, max_rounds < 0 or keep_factors.
+ * PF_SINGULAR as pf_solve.  With keep_factors the workspace (pf_qlim_workspace_size with
+ * the same options) keeps each scenario's factor and final partition for
+ * pf_adjoint_qlim (plain pf_adjoint refuses it with PF_ESTATE).
+ * Errors: as pf_solve, and PF_EINVAL for NULL limits or max_rounds < 0.
  */
 pf_err pf_solve_qlim(pf_handle* h, int batch,
                      const double* Pd, const double* Qd, const double* Pg, const double* Vset,
@@ -273,6 +274,25 @@ pf_err pf_solve_qlim(pf_handle* h, int batch,
                      int* iters, int* status, double* final_mismatch,
                      int* bus_type_out, int* rounds,
                      void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * pf_adjoint_qlim -- the implicit-differentiation backward pass (Sec. II-B.2) of the
+ * preceding pf_solve_qlim with keep_factors on this handle.  At a converged solution a
+ * switched bus k is a PQ bus with fixed reactive injection qlim_k - qd_k: the adjoint
+ * runs on each scenario's final partition, with qlim an input.  Cotangents and outputs as
+ * pf_adjoint, with: dPg_in nonzero on the network's PV buses (switched ones included),
+ * dVset zero at switched buses (their Vm is an unknown), and dQmin / dQmax (device,
+ * [batch][n_bus]) the gradients with respect to the limit each switched bus sits at
+ * (zero elsewhere; Qmax, the limits given to the solve, tells which one).  The paper has
+ * no counterpart (it has no reactive limits).  Errors: PF_EINVAL (NULL, sizes),
+ * PF_ESTATE (no matching preceding pf_solve_qlim with keep_factors), PF_ECUDA.
+ */
+pf_err pf_adjoint_qlim(pf_handle* h, int batch,
+                       const double* dVm, const double* dVa, const double* dPg, const double* dQg,
+                       const double* Qmax,
+                       double* dPd, double* dQd, double* dPg_in, double* dVset,
+                       double* dQmin, double* dQmax, int* adj_status,
+                       void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * pf_autotune -- picks the launch configuration (threads per scenario and placement

@@ -3,7 +3,8 @@
 Importing the package is cheap; the CUDA library ``libpf.so`` is loaded on first
 use by ``PowerFlow`` (and fails loudly if it has not been built).
 """
-__all__ = ["PowerFlow", "PFLayer", "build_ybus", "analyze", "SolveResult", "Gradients"]
+__all__ = ["PowerFlow", "PFLayer", "PFLayerQlim", "build_ybus", "analyze", "SolveResult",
+           "Gradients"]
 
 
 def __getattr__(name):

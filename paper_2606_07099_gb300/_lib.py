@@ -73,6 +73,8 @@ SIGNATURES = {
     "pf_qlim_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
     "pf_solve_qlim": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _d, _i, _i, C.POINTER(SolveOpts),
                            _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_adjoint_qlim": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz,
+                             _p]),
     "pf_destroy": (None, [_p]),
     "pf_error_string": (C.c_char_p, [_i]),
 }

@@ -33,6 +33,7 @@ struct pf_handle {
     const void* last_ws = nullptr;
     pf::SlotLayout last_layout{};
     size_t plan_bytes = 0;  // the device plan buffer
+    int last_qlim = 0;      // the last solve ran under reactive limits (pf_adjoint_qlim)
 };
 
 namespace {
@@ -302,7 +303,7 @@ pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, c
         h->last_batch = -1;
         return PF_ECUDA;
     }
-    // a solve under reactive limits leaves no state for pf_adjoint (keep_factors is 0)
+    h->last_qlim = q ? 1 : 0;
     h->last_batch = batch;
     h->last_ft = ft;
     h->last_keep = A.keep_factors;
@@ -317,6 +318,51 @@ pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, c
 namespace pf {
 int handle_device(const pf_handle* h) { return h->device; }
 }  // namespace pf
+
+namespace {
+pf_err adjoint_impl(pf_handle* h, int batch, const double* dVm, const double* dVa,
+                    const double* dPg, const double* dQg, double* dPd, double* dQd,
+                    double* dPg_in, double* dVset, int* adj_status, void* workspace,
+                    size_t workspace_bytes, void* stream, const double* Qmax, double* dQmin,
+                    double* dQmax) {
+    if (!h || batch < 1 || !dVm || !dVa || !dPd || !dQd || !dPg_in || !dVset || !workspace)
+        return PF_EINVAL;
+    const bool ql = Qmax != nullptr;
+    if (h->last_batch != batch || !h->last_keep || h->last_ws != workspace ||
+        h->last_qlim != (ql ? 1 : 0))
+        return PF_ESTATE;
+    const pf::SlotLayout& L = h->last_layout;
+    if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    pf::AdjArgs A{};
+    A.batch = batch;
+    A.ir_max = 8;
+    A.ir_rtol = 1e-12;
+    A.dVm = dVm;
+    A.dVa = dVa;
+    A.dPg = dPg;
+    A.dQg = dQg;
+    A.dPd = dPd;
+    A.dQd = dQd;
+    A.dPg_in = dPg_in;
+    A.dVset = dVset;
+    A.adj_status = adj_status;
+    A.ws = static_cast<char*>(workspace);
+    A.L = L;
+    A.Qmax = Qmax;
+    A.dQmin = dQmin;
+    A.dQmax = dQmax;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (ql)
+        e = h->last_ft == 4 ? pf::launch_adjoint_qlim<float>(h->dp, A, h->last_threads, s)
+                            : pf::launch_adjoint_qlim<double>(h->dp, A, h->last_threads, s);
+    else
+        e = h->last_ft == 4 ? pf::launch_adjoint<float>(h->dp, A, h->last_threads, s)
+                            : pf::launch_adjoint<double>(h->dp, A, h->last_threads, s);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+}  // namespace
 
 extern "C" {
 
@@ -537,9 +583,10 @@ pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, con
 
 pf_err pf_qlim_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts,
                               size_t* bytes) {
-    if (!h || !bytes || batch < 1 || !opts_ok(opts) || opts->keep_factors) return PF_EINVAL;
+    if (!h || !bytes || batch < 1 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    *bytes = make_layout(h, ft, 0, resolve(h, opts).placement, true).slot_bytes * (size_t)batch;
+    *bytes = make_layout(h, ft, opts->keep_factors, resolve(h, opts).placement, true).slot_bytes *
+             (size_t)batch;
     return PF_OK;
 }
 
@@ -549,40 +596,27 @@ pf_err pf_solve_qlim(pf_handle* h, int batch, const double* Pd, const double* Qd
                      double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters,
                      int* status, double* final_mismatch, int* bus_type_out, int* rounds,
                      void* workspace, size_t workspace_bytes, void* stream) {
-    if (!Qmin || !Qmax || max_rounds < 0 || !opts || opts->keep_factors) return PF_EINVAL;
+    if (!Qmin || !Qmax || max_rounds < 0 || !opts) return PF_EINVAL;
     QlimIn q{Qmin, Qmax, max_rounds, bus_type_out, rounds};
     return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
                       iters, status, final_mismatch, workspace, workspace_bytes, stream, &q);
 }
 
+
 pf_err pf_adjoint(pf_handle* h, int batch, const double* dVm, const double* dVa, const double* dPg,
                   const double* dQg, double* dPd, double* dQd, double* dPg_in, double* dVset,
                   int* adj_status, void* workspace, size_t workspace_bytes, void* stream) {
-    if (!h || batch < 1 || !dVm || !dVa || !dPd || !dQd || !dPg_in || !dVset || !workspace)
-        return PF_EINVAL;
-    if (h->last_batch != batch || !h->last_keep || h->last_ws != workspace) return PF_ESTATE;
-    const pf::SlotLayout& L = h->last_layout;
-    if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
-    DeviceGuard guard(h->device);
-    pf::AdjArgs A{};
-    A.batch = batch;
-    A.ir_max = 8;
-    A.ir_rtol = 1e-12;
-    A.dVm = dVm;
-    A.dVa = dVa;
-    A.dPg = dPg;
-    A.dQg = dQg;
-    A.dPd = dPd;
-    A.dQd = dQd;
-    A.dPg_in = dPg_in;
-    A.dVset = dVset;
-    A.adj_status = adj_status;
-    A.ws = static_cast<char*>(workspace);
-    A.L = L;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = h->last_ft == 4 ? pf::launch_adjoint<float>(h->dp, A, h->last_threads, s)
-                                    : pf::launch_adjoint<double>(h->dp, A, h->last_threads, s);
-    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+    return adjoint_impl(h, batch, dVm, dVa, dPg, dQg, dPd, dQd, dPg_in, dVset, adj_status,
+                        workspace, workspace_bytes, stream, nullptr, nullptr, nullptr);
+}
+
+pf_err pf_adjoint_qlim(pf_handle* h, int batch, const double* dVm, const double* dVa,
+                       const double* dPg, const double* dQg, const double* Qmax, double* dPd,
+                       double* dQd, double* dPg_in, double* dVset, double* dQmin, double* dQmax,
+                       int* adj_status, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!Qmax || !dQmin || !dQmax) return PF_EINVAL;
+    return adjoint_impl(h, batch, dVm, dVa, dPg, dQg, dPd, dQd, dPg_in, dVset, adj_status,
+                        workspace, workspace_bytes, stream, Qmax, dQmin, dQmax);
 }
 
 pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
@@ -812,6 +846,7 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
         h->last_ft = ft;
         h->last_keep = M.args[k].keep_factors;
         h->last_threads = M.warp_form[k] ? 32 : threads;  // the adjoint: one CTA per scenario
+        h->last_qlim = 0;
         h->last_ws = M.args[k].ws;
         h->last_layout = M.args[k].L;
     }

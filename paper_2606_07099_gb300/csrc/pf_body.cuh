@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(512, 1) nr_solve_multi_kernel(MultiArgs M) {
 // All Jacobian-transpose products are taken matrix-free through Ybus^T (phase_jvt);
 // the transposed solve uses the stored factor of the last Newton step and refines
 // with the FP64 residual of J1 at the solution.
-template <typename FT, bool VSM, bool FSM>
+template <typename FT, bool VSM, bool FSM, bool QL = false>
 __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
@@ -826,6 +826,10 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     FT* fac = FSM ? reinterpret_cast<FT*>(smem + K.smem_fac_off) : gfac;
     Arrays a;
     carve(vbase, P.n_bus, P.n, (int)sizeof(FT), true, &a);
+    if (QL) {  // the scenario's final partition under reactive limits (left by the solve)
+        a.stype = reinterpret_cast<signed char*>(slot + L.off_qlim);
+        a.qfix = reinterpret_cast<double*>(slot + L.off_qlim + align_up((size_t)P.n_bus, 16));
+    }
     FT* x = ftptr<FT>(a.x);
     const size_t row = (size_t)b * P.n_bus;
     const int* fl = reinterpret_cast<const int*>(slot + L.off_flags);
@@ -838,6 +842,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             A.dQd[row + i] = 0.0;
             A.dPg_in[row + i] = 0.0;
             A.dVset[row + i] = 0.0;
+            if (QL) A.dQmin[row + i] = A.dQmax[row + i] = 0.0;
         }
         if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = fwd_status;
         return;
@@ -863,9 +868,10 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         a.Iim[i] = ii;
         store_bus_f32(a, i, ir, ii);
     }
-    // Step-2 weights: c_P on R (dL/dpg_R), c_Q on B\D (dL/dqg)
+    // Step-2 weights: c_P on R (dL/dpg_R), c_Q on B\D (dL/dqg; under reactive limits the
+    // final B\D: a switched bus's qg is its limit, not a recovered output)
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = __ldg(P.bus_type + i);
+        const int t = ntype<QL>(P, a, i);
         a.Psp[i] = (t == 2 && A.dPg) ? A.dPg[row + i] : 0.0;
         a.Qsp[i] = (t != 0 && A.dQg) ? A.dQg[row + i] : 0.0;
     }
@@ -880,7 +886,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         const int p = __ldg(P.bus2pos + i);
         if (p >= 0) {
             a.F[2 * p] = gva;                                   // theta component of g_z1
-            a.F[2 * p + 1] = (__ldg(P.bus_type + i) == 0) ? gvm : 0.0;  // Vm component (PQ only)
+            a.F[2 * p + 1] = (ntype<QL>(P, a, i) == 0) ? gvm : 0.0;  // Vm component (PQ only)
             lg = fmax(lg, fmax(absinf(gva), absinf(a.F[2 * p + 1])));
         }
     }
@@ -897,7 +903,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     bool refactored = false;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (!have) {
-            phase_fill<false>(P, a, fac);
+            phase_fill<false, QL>(P, a, fac);
             gsync<false>();
             if (phase_lu<FT, false>(P, fac, &s_bad)) { astat = 3; break; }
             have = true;
@@ -914,7 +920,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
                 const int p = __ldg(P.bus2pos + i);
                 a.Psp[i] = (p >= 0) ? a.dz[2 * p] : 0.0;
-                a.Qsp[i] = (p >= 0 && __ldg(P.bus_type + i) == 0) ? a.dz[2 * p + 1] : 0.0;
+                a.Qsp[i] = (p >= 0 && ntype<QL>(P, a, i) == 0) ? a.dz[2 * p + 1] : 0.0;
             }
             gsync<false>();
             phase_jvt<false>(P, a);
@@ -923,7 +929,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
                 const int i = __ldg(P.pos2bus + p);
                 const double r0 = a.F[2 * p] + a.w1[i];
-                const double r1 = (__ldg(P.bus_type + i) == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
+                const double r1 = (ntype<QL>(P, a, i) == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
                 a.r[2 * p] = r0;
                 a.r[2 * p + 1] = r1;
                 lr = fmax(lr, fmax(absinf(r0), absinf(r1)));
@@ -943,7 +949,8 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     }
     // gradients; w0 holds (Jv^T m1)_Vm for the final lambda
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        const int t = __ldg(P.bus_type + i);
+        const int t = ntype<QL>(P, a, i);        // the partition of the solution
+        const int t0 = __ldg(P.bus_type + i);    // the network's (pg is an input on its G)
         const int p = __ldg(P.bus2pos + i);
         const double lP = (p >= 0) ? a.dz[2 * p] : 0.0;
         const double lQ = (p >= 0 && t == 0) ? a.dz[2 * p + 1] : 0.0;
@@ -951,8 +958,14 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         const double cQ = A.dQg ? A.dQg[row + i] : 0.0;
         A.dPd[row + i] = (t == 2) ? cP : lP;
         A.dQd[row + i] = (t == 0) ? lQ : cQ;
-        A.dPg_in[row + i] = (t == 1) ? cP - lP : 0.0;
+        A.dPg_in[row + i] = (t0 == 1) ? cP - lP : 0.0;
         A.dVset[row + i] = (t != 0) ? a.gV[i] + a.w0[i] : 0.0;
+        if (QL) {  // a switched bus: Qg_out = qlim, and qlim enters F1 like minus a load
+            const double dq = (t0 == 1 && t == 0) ? cQ - lQ : 0.0;
+            const bool at_max = a.qfix[i] == A.Qmax[row + i];
+            A.dQmax[row + i] = at_max ? dq : 0.0;
+            A.dQmin[row + i] = at_max ? 0.0 : dq;
+        }
     }
     if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = astat;
 }

@@ -123,6 +123,11 @@ struct AdjArgs {
     int* adj_status;
     char* ws;
     SlotLayout L;
+    // after a solve under reactive limits: the upper limits (to tell which limit a
+    // switched bus sits at) and the gradients with respect to the limits
+    const double* Qmax;
+    double* dQmin;
+    double* dQmax;
 };
 
 // Vector arena carved from one base pointer (shared or global memory).

@@ -13,6 +13,8 @@ cudaError_t multi_blocks_per_sm(int threads, size_t smem, int* out);
 template <typename FT>
 cudaError_t launch_solve_qlim(const DevPlan& P, const SolveArgs& A, int threads, cudaStream_t s);
 template <typename FT>
+cudaError_t launch_adjoint_qlim(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s);
+template <typename FT>
 cudaError_t launch_adjoint(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s);
 cudaError_t launch_export_jacobian(const DevPlan& P, int batch, const double* Vm, const double* Va,
                                    double* values, cudaStream_t s);

@@ -1,5 +1,6 @@
-// pf_qlim.cu -- the Newton solve under reactive-power limits (pf_solve_qlim): the solve
-// body instantiated with each scenario's own bus partition (PV buses switching to PQ),
+// pf_qlim.cu -- the Newton solve under reactive-power limits (pf_solve_qlim) and its
+// adjoint (pf_adjoint_qlim): the solve body and the adjoint kernel instantiated with each
+// scenario's own bus partition (PV buses switching to PQ),
 // in a translation unit of its own so that the plain solve keeps its code and the two
 // compile in parallel.
 #include "pf_body.cuh"
@@ -27,6 +28,19 @@ cudaError_t launch_solve_qlim(const DevPlan& P, const SolveArgs& A, int threads,
                        : launch_q<FT, false, false, false>(P, A, threads, s);
 }
 
+// The adjoint of a solve under reactive limits (one CTA per scenario, as pf_adjoint).
+template <typename FT>
+cudaError_t launch_adjoint_qlim(const DevPlan& P, const AdjArgs& A, int threads, cudaStream_t s) {
+    const KernelSmem& K = A.L.adj;
+    if (K.vec_in_smem && K.fac_in_smem)
+        return launch_one(adjoint_kernel<FT, true, true, true>, P, A, K, threads, s);
+    if (K.vec_in_smem) return launch_one(adjoint_kernel<FT, true, false, true>, P, A, K, threads, s);
+    if (K.fac_in_smem) return launch_one(adjoint_kernel<FT, false, true, true>, P, A, K, threads, s);
+    return launch_one(adjoint_kernel<FT, false, false, true>, P, A, K, threads, s);
+}
+
+template cudaError_t launch_adjoint_qlim<float>(const DevPlan&, const AdjArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint_qlim<double>(const DevPlan&, const AdjArgs&, int, cudaStream_t);
 template cudaError_t launch_solve_qlim<float>(const DevPlan&, const SolveArgs&, int, cudaStream_t);
 template cudaError_t launch_solve_qlim<double>(const DevPlan&, const SolveArgs&, int, cudaStream_t);
 

@@ -108,6 +108,8 @@ class Gradients:
     dPg: torch.Tensor
     dVset: torch.Tensor
     status: torch.Tensor
+    dQmin: torch.Tensor | None = None   # adjoint_qlim: gradient w.r.t. the lower limits
+    dQmax: torch.Tensor | None = None   # adjoint_qlim: gradient w.r.t. the upper limits
 
 
 def _check_bus_tensor(x: torch.Tensor, name: str, n_bus: int, batch: int | None = None):
@@ -220,16 +222,16 @@ class PowerFlow:
 
     def solve_qlim(self, Pd, Qd, Pg, Vset, Qmin, Qmax, tol=1e-8, max_iter=20, max_rounds=10,
                    precision="mixed", ir_steps=2, ir_rtol=1e-3, group_threads=0, placement=0,
-                   instances_per_cta=0, ir_gate=0.0) -> SolveResult:
+                   instances_per_cta=0, ir_gate=0.0, keep_factors=False) -> SolveResult:
         """Newton-Raphson with reactive-power limits at the PV buses (pf_solve_qlim):
         violating PV buses switch to PQ with qg at the limit, between Newton rounds.
         The result also carries ``bus_type`` (final partition per scenario) and
-        ``rounds``."""
+        ``rounds``.  With ``keep_factors``, ``adjoint_qlim`` differentiates it."""
         batch = Pd.shape[0]
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset), ("Qmin", Qmin),
                       ("Qmax", Qmax)):
             _check_bus_tensor(v, nm, self.n_bus, batch)
-        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, False, placement,
+        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
                               instances_per_cta, ir_gate)
         n = C.c_size_t(0)
         L.check(self._lib.pf_qlim_workspace_size(self._h, batch, C.byref(opts), C.byref(n)),
@@ -256,7 +258,8 @@ class PowerFlow:
             out.final_mismatch.data_ptr(), out.bus_type.data_ptr(), out.rounds.data_ptr(),
             ws.data_ptr(), ws.numel(), stream), "pf_solve_qlim")
         self._solve_id += 1
-        self._last = None   # nothing for pf_adjoint to differentiate
+        # pf_adjoint_qlim (not pf_adjoint) differentiates this solve
+        self._last = (batch, ws, bool(keep_factors), Qmax) if keep_factors else None
         return out
 
     def jacobian_pattern(self):
@@ -321,7 +324,7 @@ class PowerFlow:
 
     def adjoint(self, dVm, dVa, dPg=None, dQg=None) -> Gradients:
         """Implicit-differentiation backward pass (pf_adjoint) of the last solve."""
-        if self._last is None or not self._last[2]:
+        if self._last is None or not self._last[2] or len(self._last) != 3:
             raise RuntimeError("adjoint needs a preceding solve(..., keep_factors=True)")
         batch, ws, _ = self._last
         for nm, v in (("dVm", dVm), ("dVa", dVa), ("dPg", dPg), ("dQg", dQg)):
@@ -338,6 +341,33 @@ class PowerFlow:
             dQg.data_ptr() if dQg is not None else None,
             g.dPd.data_ptr(), g.dQd.data_ptr(), g.dPg.data_ptr(), g.dVset.data_ptr(),
             g.status.data_ptr(), ws.data_ptr(), ws.numel(), stream), "pf_adjoint")
+        return g
+
+    def adjoint_qlim(self, dVm, dVa, dPg=None, dQg=None) -> Gradients:
+        """Backward pass of the last solve_qlim(..., keep_factors=True) (pf_adjoint_qlim):
+        Gradients plus ``dQmin`` / ``dQmax`` (nonzero where a switched bus sits at that
+        limit)."""
+        if self._last is None or len(self._last) != 4:
+            raise RuntimeError("adjoint_qlim needs a preceding solve_qlim(..., keep_factors=True)")
+        batch, ws, _, Qmax = self._last
+        for nm, v in (("dVm", dVm), ("dVa", dVa), ("dPg", dPg), ("dQg", dQg)):
+            if v is not None:
+                _check_bus_tensor(v, nm, self.n_bus, batch)
+        e = dict(dtype=torch.float64, device=dVm.device)
+        g = Gradients(dPd=torch.empty(batch, self.n_bus, **e), dQd=torch.empty(batch, self.n_bus, **e),
+                      dPg=torch.empty(batch, self.n_bus, **e), dVset=torch.empty(batch, self.n_bus, **e),
+                      status=torch.empty(batch, dtype=torch.int32, device=dVm.device))
+        dQmin = torch.empty(batch, self.n_bus, **e)
+        dQmax = torch.empty(batch, self.n_bus, **e)
+        stream = torch.cuda.current_stream(dVm.device).cuda_stream
+        L.check(self._lib.pf_adjoint_qlim(
+            self._h, batch, dVm.data_ptr(), dVa.data_ptr(),
+            dPg.data_ptr() if dPg is not None else None,
+            dQg.data_ptr() if dQg is not None else None, Qmax.data_ptr(),
+            g.dPd.data_ptr(), g.dQd.data_ptr(), g.dPg.data_ptr(), g.dVset.data_ptr(),
+            dQmin.data_ptr(), dQmax.data_ptr(), g.status.data_ptr(), ws.data_ptr(), ws.numel(),
+            stream), "pf_adjoint_qlim")
+        g.dQmin, g.dQmax = dQmin, dQmax
         return g
 
     def close(self):
@@ -389,6 +419,39 @@ class PFLayer(torch.autograd.Function):
         g = pf.adjoint(dense(gVm), dense(gVa), None if gPg is None else gPg.contiguous(),
                        None if gQg is None else gQg.contiguous())
         return None, g.dPd, g.dQd, g.dPg, g.dVset, None, None, None, None, None, None
+
+
+class PFLayerQlim(torch.autograd.Function):
+    """The implicit layer with reactive limits at the PV buses:
+    (Pd, Qd, Pg, Vset, Qmin, Qmax) -> (Vm, Va, Pg_out, Qg_out, status, bus_type).
+    Forward is pf_solve_qlim (keeping the factors), backward pf_adjoint_qlim on each
+    scenario's final partition; the binding limits receive gradients."""
+
+    @staticmethod
+    def forward(ctx, pf: PowerFlow, Pd, Qd, Pg, Vset, Qmin, Qmax, tol=1e-8, max_iter=20,
+                max_rounds=10, precision="mixed", ir_steps=2, ir_rtol=1e-3, ir_gate=0.0):
+        res = pf.solve_qlim(Pd.contiguous(), Qd.contiguous(), Pg.contiguous(), Vset.contiguous(),
+                            Qmin.contiguous(), Qmax.contiguous(), tol, max_iter, max_rounds,
+                            precision, ir_steps, ir_rtol, ir_gate=ir_gate, keep_factors=True)
+        ctx.pf = pf
+        ctx.solve_id = pf._solve_id
+        ctx.mark_non_differentiable(res.status, res.bus_type)
+        return res.Vm, res.Va, res.Pg, res.Qg, res.status, res.bus_type
+
+    @staticmethod
+    def backward(ctx, gVm, gVa, gPg, gQg, _gs, _gt):
+        pf = ctx.pf
+        if pf._solve_id != ctx.solve_id:
+            raise RuntimeError("PFLayerQlim.backward: the network handle solved again after "
+                               "this forward; run backward first")
+        batch = pf._last[0]
+        zero = lambda: torch.zeros(batch, pf.n_bus, dtype=torch.float64, device=pf.device)
+        g = pf.adjoint_qlim(gVm.contiguous() if gVm is not None else zero(),
+                            gVa.contiguous() if gVa is not None else zero(),
+                            None if gPg is None else gPg.contiguous(),
+                            None if gQg is None else gQg.contiguous())
+        return (None, g.dPd, g.dQd, g.dPg, g.dVset, g.dQmin, g.dQmax,
+                None, None, None, None, None, None, None)
 
 
 def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,

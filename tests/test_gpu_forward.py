@@ -290,9 +290,14 @@ def test_new_entry_points_reject_bad_arguments(PowerFlow):
     big = torch.full_like(Pd, 1e30)
     with pytest.raises(_lib.PFError):
         pf.solve_qlim(Pd, Qd, Pg, Vset, -big, big, max_rounds=-1)
-    opts = PowerFlow.make_opts("mixed", keep_factors=True)
-    n = C.c_size_t(0)
-    assert lib.pf_qlim_workspace_size(pf._h, 4, C.byref(opts), C.byref(n)) == _lib.PF_EINVAL
+    n, n_keep = C.c_size_t(0), C.c_size_t(0)
+    assert lib.pf_qlim_workspace_size(pf._h, 0, C.byref(PowerFlow.make_opts("mixed")),
+                                      C.byref(n)) == _lib.PF_EINVAL
+    assert lib.pf_qlim_workspace_size(pf._h, 4, C.byref(PowerFlow.make_opts("mixed")),
+                                      C.byref(n)) == _lib.PF_OK
+    assert lib.pf_qlim_workspace_size(pf._h, 4, C.byref(PowerFlow.make_opts("mixed", keep_factors=True)),
+                                      C.byref(n_keep)) == _lib.PF_OK
+    assert n_keep.value > n.value  # the kept factors and solution
     with pytest.raises(_lib.PFError):  # multi-network CTAs need 64..512 threads
         solve_multi([(pf, Pd, Qd, Pg, Vset)], group_threads=32)
     with pytest.raises(_lib.PFError):

@@ -121,3 +121,75 @@ def test_qlim_round_limit_and_bad_arguments(pm):
     with pytest.raises(_lib.PFError):
         pf.solve_qlim(*dev, *tq, max_rounds=-1)
     pf.close()
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_qlim_adjoint_matches_oracle(pm, precision):
+    """pf_adjoint_qlim on each scenario's final partition against the oracle's
+    adjoint_qlim (itself pinned by central differences), random cotangents, 1e-6."""
+    import torch
+    g = configs.grid("c1")
+    sc = configs.scenarios("c1", 96, g)
+    Qmin, Qmax, Y = limits(g, sc, 4)
+    pf = pm.PowerFlow.from_grid(g)
+    dev = to_dev(sc)
+    tq = [torch.as_tensor(a, device="cuda") for a in (Qmin, Qmax)]
+    r = pf.solve_qlim(*dev, *tq, tol=1e-10, max_iter=30, precision=precision, keep_factors=True)
+    rng = np.random.default_rng(2)
+    cts = [rng.normal(size=sc.Pd.shape) for _ in range(4)]
+    gr = pf.adjoint_qlim(*[torch.as_tensor(c, device="cuda") for c in cts])
+    with pytest.raises(RuntimeError):
+        pf.adjoint(*[torch.as_tensor(c, device="cuda") for c in cts])  # not a plain solve
+    torch.cuda.synchronize()
+    bt = r.bus_type.cpu().numpy()
+    Vm, Va = r.Vm.cpu().numpy(), r.Va.cpu().numpy()
+    got = {k: getattr(gr, k).cpu().numpy() for k in ("dPd", "dQd", "dPg", "dVset", "dQmin", "dQmax")}
+    ok = r.status.cpu().numpy() == 0
+    assert ok.mean() >= 0.9 and np.all(gr.status.cpu().numpy()[ok] == 0)
+    switched = 0
+    for s in range(0, 96, 6):
+        if not ok[s]:
+            continue
+        o = O.adjoint_qlim(Y, g.bus_type, bt[s], Vm[s], Va[s], cts[0][s], cts[1][s], cts[2][s],
+                           cts[3][s])
+        for k in ("dPd", "dQd", "dPg", "dVset"):
+            assert _rel(got[k][s], o[k]) <= 1e-6, (s, k)
+        assert _rel(got["dQmin"][s] + got["dQmax"][s], o["dQlim"]) <= 1e-6, s
+        sw = (g.bus_type == 1) & (bt[s] == 0)
+        switched += int(sw.sum())
+        assert np.all(got["dQmax"][s][~sw] == 0) and np.all(got["dQmin"][s][~sw] == 0)
+    assert switched > 0
+    pf.close()
+
+
+def test_qlim_layer_autograd(pm):
+    """PFLayerQlim: gradients reach the loads, generation, set points and the binding
+    upper limits through torch.autograd, matching the oracle."""
+    import torch
+    g = configs.grid("c1")
+    sc = configs.scenarios("c1", 24, g)
+    Qmin, Qmax, Y = limits(g, sc, 4)
+    pf = pm.PowerFlow.from_grid(g)
+    Pd, Qd, Pg, Vset = [t.clone().requires_grad_(True) for t in to_dev(sc)]
+    tQmin = torch.as_tensor(Qmin, device="cuda").requires_grad_(True)
+    tQmax = torch.as_tensor(Qmax, device="cuda").requires_grad_(True)
+    Vm, Va, Pgo, Qgo, st, bt = pm.PFLayerQlim.apply(pf, Pd, Qd, Pg, Vset, tQmin, tQmax, 1e-10, 30)
+    w = [torch.randn_like(Vm) for _ in range(4)]
+    L = (w[0] * Vm).sum() + (w[1] * Va).sum() + (w[2] * Pgo).sum() + (w[3] * Qgo).sum()
+    grads = torch.autograd.grad(L, [Pd, Qd, Pg, Vset, tQmin, tQmax])
+    wn = [x.cpu().numpy() for x in w]
+    btn, Vmn, Van = bt.cpu().numpy(), Vm.detach().cpu().numpy(), Va.detach().cpu().numpy()
+    gn = [x.cpu().numpy() for x in grads]
+    ok = st.cpu().numpy() == 0
+    assert ok.mean() >= 0.9
+    for s in np.flatnonzero(ok):
+        o = O.adjoint_qlim(Y, g.bus_type, btn[s], Vmn[s], Van[s], wn[0][s], wn[1][s], wn[2][s],
+                           wn[3][s])
+        for k, v in zip(("dPd", "dQd", "dPg", "dVset"), gn[:4]):
+            assert _rel(v[s], o[k]) <= 1e-6, (s, k)
+        assert _rel(gn[4][s] + gn[5][s], o["dQlim"]) <= 1e-6
+    pf.close()
