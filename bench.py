@@ -425,6 +425,19 @@ def gpu_leg(args, rank, world):
             outj = pfj.export_jacobian(rj.Vm, rj.Va)
             jac_cases.append((jname, jn, gj, pfj, rj, outj))
 
+    bde_cases = []
+    if "bde" in secs:  # the same FP64 solve run as one block-diagonal matrix, phase by phase
+        for bname in ("c1", "c2", "c3"):
+            if bname == "c1":
+                gb_, pfb_, inb_ = g, pf, [Pd, Qd, Pg, Vset]
+            else:
+                gb_ = configs.grid(bname)
+                scb_ = configs.scenarios(bname, g=gb_)
+                pfb_ = large[bname][2] if bname in large else PowerFlow.from_grid(gb_)
+                inb_ = [torch.as_tensor(np.ascontiguousarray(a), device=dev)
+                        for a in (scb_.Pd, scb_.Qd, scb_.Pg, scb_.Vset)]
+            bde_cases.append((bname, gb_, pfb_, inb_))
+
     sweep_cases = []
     if "sweep" in secs:  # solve time vs batch size on the large grids (the shape of Table II)
         for sname, sizes in (("c1", (256, 1024, 2048, 4096)), ("c2", (4, 16, 64, 256, 1024)),
@@ -536,6 +549,18 @@ def gpu_leg(args, rank, world):
         t_jac = [timed(lambda c=c: c[3].export_jacobian(c[4].Vm, c[4].Va, out=c[5]), args.steps,
                        args.warmup, f"jacobian_{c[0]}_{c[1]}")
                  for c in (jac_cases if "jacobian" in secs else [])]
+        bde_out = {}
+        for bname, gb_, pfb_, inb_ in bde_cases:
+            rb_ = pfb_.solve_bde(*inb_)
+            tb_ = timed(lambda: pfb_.solve_bde(*inb_, out=rb_), 5, 3, f"bde_{bname}")
+            rf_ = pfb_.solve(*inb_, precision="fp64")
+            tf_ = timed(lambda: pfb_.solve(*inb_, precision="fp64", out=rf_), 5, 3, f"bde_fused_{bname}")
+            bde_out[bname] = {
+                "n_bus": gb_.n_bus, "batch": int(inb_[0].shape[0]),
+                "one_big_matrix_ms": statistics.median(tb_), "fused_fp64_ms": statistics.median(tf_),
+                "fused_speedup": statistics.median(tb_) / statistics.median(tf_),
+                "converged": [int((rb_.status == 0).sum().item()), int((rf_.status == 0).sum().item())],
+                "iters_max": [int(rb_.iters.max().item()), int(rf_.iters.max().item())]}
         sweep_out = {}
         for sname, gs_, pfs_, ins_, sizes in sweep_cases:
             rows_ = []
@@ -623,6 +648,18 @@ def gpu_leg(args, rank, world):
             "what": "pf_export_jacobian: J1 values of every scenario at its solution, written "
                     "in FP64 into the fixed block-diagonal (BDE) template",
             "cases": rows}
+    if "bde" in secs and "c1" in bde_out and "fp64" in secs:
+        # the mixed form against the faster of the two FP64 executions of the same solve
+        best64 = min(T_fp64 / K, bde_out["c1"]["one_big_matrix_ms"])
+        extra_fp64 = {"best_fp64_ms": best64, "mixed_speedup_vs_best_fp64": best64 / (T_mixed / K)}
+    else:
+        extra_fp64 = {}
+    if "bde" in secs:
+        extra["one_big_matrix"] = {
+            "what": "FP64 solve as one block-diagonal matrix (pf_solve_bde: batch-wide kernels "
+                    "per phase and elimination level, host convergence check per iteration) "
+                    "against the fused one-launch FP64 solve on the same plan; median of 5",
+            **bde_out}
     if "sweep" in secs:
         extra["batch_sweep"] = {
             "what": "one pf_solve per batch size (launch shape autotuned at that size, except "
@@ -678,7 +715,7 @@ def gpu_leg(args, rank, world):
                    "parallelism": f"replicas x{world} (scenarios sharded, no collective)"},
         "converged": conv, "max_final_mismatch": fmax, "mean_iters": float(its.mean()),
         "fp64_form": {"value": world * conv64 * K / (T_fp64 / 1e3), "unit": UNIT,
-                      "ms_per_step": T_fp64 / K, "mixed_speedup": T_fp64 / T_mixed},
+                      "ms_per_step": T_fp64 / K, "mixed_speedup": T_fp64 / T_mixed, **extra_fp64},
         "fwd_bwd": {"value": world * N * K / (T_fb / 1e3), "unit": "fwd+bwd/s",
                     "ms_per_step": T_fb / K},
         "fwd_bwd_c2": {"value": world * 1024 * K / (T_fb2 / 1e3), "unit": "fwd+bwd/s",
@@ -719,7 +756,7 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
-    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3,c5,qlim,jacobian,memory,sweep,train",
+    ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3,c5,qlim,jacobian,memory,bde,sweep,train",
                     help="timed sections to run (the first one, mixed, always runs)")
     ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
     args = ap.parse_args()

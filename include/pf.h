@@ -276,6 +276,25 @@ pf_err pf_solve_qlim(pf_handle* h, int batch,
                      void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * pf_bde_workspace_size / pf_solve_bde -- the same Newton-Raphson solve (Step 1 + Step 2,
+ * FP64 form: inputs, outputs, flags and iteration semantics as pf_solve) run the way the
+ * paper runs a batch: as ONE block-diagonal matrix (Sec. III-A), with one batch-wide
+ * kernel per phase and, for the factorisation and the triangular sweeps, one per
+ * elimination-tree level, the host checking convergence after every mismatch.  Values are
+ * stored scenario-interleaved in the workspace (pf_bde_workspace_size bytes, 256-byte
+ * aligned).  It exists to measure that execution model beside the fused one-launch
+ * pf_solve on the same plan and arithmetic; it is stream-synchronous (one host read per
+ * Newton iteration) and leaves no state for pf_adjoint.  Errors: PF_EINVAL, PF_ECUDA.
+ */
+pf_err pf_bde_workspace_size(const pf_handle* h, int batch, size_t* bytes);
+pf_err pf_solve_bde(pf_handle* h, int batch,
+                    const double* Pd, const double* Qd, const double* Pg, const double* Vset,
+                    double tol, int max_iter,
+                    double* Vm, double* Va, double* Pg_out, double* Qg_out,
+                    int* iters, int* status, double* final_mismatch,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * pf_adjoint_qlim -- the implicit-differentiation backward pass (Sec. II-B.2) of the
  * preceding pf_solve_qlim with keep_factors on this handle.  At a converged solution a
  * switched bus k is a PQ bus with fixed reactive injection qlim_k - qd_k: the adjoint

@@ -75,6 +75,8 @@ SIGNATURES = {
                            _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "pf_adjoint_qlim": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz,
                              _p]),
+    "pf_bde_workspace_size": (_i, [_p, _i, C.POINTER(_sz)]),
+    "pf_solve_bde": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "pf_destroy": (None, [_p]),
     "pf_error_string": (C.c_char_p, [_i]),
 }

@@ -581,6 +581,29 @@ pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, con
                       iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr);
 }
 
+pf_err pf_bde_workspace_size(const pf_handle* h, int batch, size_t* bytes) {
+    if (!h || !bytes || batch < 1) return PF_EINVAL;
+    *bytes = pf::bde_workspace_bytes(h->dp, batch);
+    return PF_OK;
+}
+
+pf_err pf_solve_bde(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
+                    const double* Vset, double tol, int max_iter, double* Vm, double* Va,
+                    double* Pg_out, double* Qg_out, int* iters, int* status,
+                    double* final_mismatch, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+    if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
+        return PF_EINVAL;
+    if (!(tol > 0.0) || max_iter < 0) return PF_EINVAL;
+    if (workspace_bytes < pf::bde_workspace_bytes(h->dp, batch)) return PF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    h->last_batch = -1;  // leaves no state for pf_adjoint
+    return pf::solve_bde(h->dp, batch, Pd, Qd, Pg, Vset, tol, max_iter, Vm, Va, Pg_out, Qg_out,
+                         iters, status, final_mismatch, workspace,
+                         static_cast<cudaStream_t>(stream)) == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
 pf_err pf_qlim_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts,
                               size_t* bytes) {
     if (!h || !bytes || batch < 1 || !opts_ok(opts)) return PF_EINVAL;

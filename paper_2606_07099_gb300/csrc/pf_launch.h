@@ -20,4 +20,9 @@ cudaError_t launch_export_jacobian(const DevPlan& P, int batch, const double* Vm
                                    double* values, cudaStream_t s);
 cudaError_t launch_bde_pattern(const DevPlan& P, int batch, int* row_ptr, int* col_idx,
                                cudaStream_t s);
+size_t bde_workspace_bytes(const DevPlan& P, int batch);
+cudaError_t solve_bde(const DevPlan& P, int batch, const double* Pd, const double* Qd,
+                      const double* Pg, const double* Vset, double tol, int max_iter, double* Vm,
+                      double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
+                      double* fmis, void* ws, cudaStream_t s);
 }  // namespace pf

@@ -146,6 +146,7 @@ class PowerFlow:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._ws = None
         self._ws_q = None
+        self._ws_bde = None
         self._ws_key = None
         self._solve_id = 0
         self._last = None
@@ -260,6 +261,37 @@ class PowerFlow:
         self._solve_id += 1
         # pf_adjoint_qlim (not pf_adjoint) differentiates this solve
         self._last = (batch, ws, bool(keep_factors), Qmax) if keep_factors else None
+        return out
+
+    def solve_bde(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20,
+                  out: SolveResult | None = None) -> SolveResult:
+        """The FP64 solve run as one block-diagonal matrix with batch-wide kernels per
+        phase and level and a host convergence check per iteration (pf_solve_bde): the
+        paper's execution model, for comparison with ``solve``.  Stream-synchronous."""
+        batch = Pd.shape[0]
+        for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
+            _check_bus_tensor(v, nm, self.n_bus, batch)
+        n = C.c_size_t(0)
+        L.check(self._lib.pf_bde_workspace_size(self._h, batch, C.byref(n)), "pf_bde_workspace_size")
+        if self._ws_bde is None or self._ws_bde.numel() < n.value:
+            self._ws_bde = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+        if out is None:
+            e = dict(dtype=torch.float64, device=Pd.device)
+            out = SolveResult(
+                Vm=torch.empty(batch, self.n_bus, **e), Va=torch.empty(batch, self.n_bus, **e),
+                Pg=torch.empty(batch, self.n_bus, **e), Qg=torch.empty(batch, self.n_bus, **e),
+                iters=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                status=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                final_mismatch=torch.empty(batch, dtype=torch.float64, device=Pd.device))
+        stream = torch.cuda.current_stream(Pd.device).cuda_stream
+        L.check(self._lib.pf_solve_bde(
+            self._h, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(), Vset.data_ptr(),
+            float(tol), int(max_iter), out.Vm.data_ptr(), out.Va.data_ptr(), out.Pg.data_ptr(),
+            out.Qg.data_ptr(), out.iters.data_ptr(), out.status.data_ptr(),
+            out.final_mismatch.data_ptr(), self._ws_bde.data_ptr(), self._ws_bde.numel(),
+            stream), "pf_solve_bde")
+        self._solve_id += 1
+        self._last = None
         return out
 
     def jacobian_pattern(self):
