@@ -300,14 +300,14 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
     }
 
     // lanes per gathered row.  One thread gathers a row, except on levels of few rows
-    // (<= 64) whose longest gather exceeds 32 blocks: the top of the elimination tree,
-    // where a level is a handful of long, nearly dense rows and one thread per row would
+    // (<= 128) whose longest gather exceeds 8 blocks: towards the top of the elimination
+    // tree a level is a handful of long, nearly dense rows, and one thread per row would
     // make the whole level wait on one long sequential gather.  There a row is split over
     // a power-of-two group of lanes (about four blocks each) and reduced by shuffles.  The
     // choice depends on the plan only, so the summation order (and every result) is the
     // same for any number of threads per scenario.
     auto lanes = [](int len, int rows) {
-        if (len <= 32 || rows > 64) return 1;
+        if (len <= 8 || rows > 128) return 1;
         int g = 1;
         while (g * 4 < len && g < 32) g <<= 1;
         return g;
