@@ -520,18 +520,22 @@ def gpu_leg(args, rank, world):
         return tot
 
     # end to end through the public API with host buffers
-    out_host = [torch.empty(N, nb, dtype=torch.float64).pin_memory() for _ in range(2)]
+    # (the step's four input arrays travel in one pinned buffer, one copy; Vm and Va come
+    # back in one; the solve reads and writes contiguous views of them)
+    host_in = torch.stack(host).pin_memory()
+    dev_in_all = torch.empty(host_in.shape, dtype=torch.float64, device=dev)
+    dev_in = [dev_in_all[k] for k in range(4)]
+    out_dev = torch.empty(2, N, nb, dtype=torch.float64, device=dev)
+    out_host = torch.empty(2, N, nb, dtype=torch.float64).pin_memory()
     st_host = torch.empty(N, dtype=torch.int32).pin_memory()
-    dev_in = [torch.empty_like(Pd) for _ in range(4)]
     if "e2e" in secs:
         rese = pf.solve(Pd, Qd, Pg, Vset, **opts)
+        rese.Vm, rese.Va = out_dev[0], out_dev[1]
 
     def e2e():
-        for d, h in zip(dev_in, host):
-            d.copy_(h, non_blocking=True)
+        dev_in_all.copy_(host_in, non_blocking=True)
         pf.solve(*dev_in, out=rese, **opts)
-        out_host[0].copy_(rese.Vm, non_blocking=True)
-        out_host[1].copy_(rese.Va, non_blocking=True)
+        out_host.copy_(out_dev, non_blocking=True)
         st_host.copy_(rese.status, non_blocking=True)
 
     none = [float("nan")]
