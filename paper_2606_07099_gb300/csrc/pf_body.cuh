@@ -89,6 +89,10 @@ __device__ __forceinline__ double absinf(double v) {
     double a = fabs(v);
     return (a <= DBL_MAX) ? a : INFINITY;
 }
+__device__ __forceinline__ float absinf(float v) {
+    float a = fabsf(v);
+    return (a <= FLT_MAX) ? a : INFINITY;
+}
 
 // Group-wide max; every thread gets the result.  `red` holds one double per warp.
 template <bool W>
@@ -122,16 +126,20 @@ __device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
 }
 
 // e^{j d} for a Newton angle step |d| <= 1/8 from the Maclaurin series of sin and cos,
-// truncated after d^9 and d^10: the first omitted terms are below 3e-18 relative.
-// (Horner form; the factors are 1/(k(k+1)) of consecutive terms, as products so that no
-// division is emitted.)
+// truncated after d^9 and d^10: the first omitted terms, d^11/11! and d^12/12!, are below
+// 2.4e-17 and 3.1e-20 relative.  Horner form in d^2 with the series' own coefficients
+// (constants folded at compile time): 11 FP64 operations, each a scarce FP64-pipe slot.
 __device__ __forceinline__ void small_angle_phasor(double d, double* c, double* s) {
     const double d2 = d * d;
-    *s = d * (1.0 - d2 * (1.0 / 6.0) *
-                        (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0) * (1.0 - d2 * (1.0 / 72.0)))));
-    *c = 1.0 - d2 * 0.5 *
-                   (1.0 - d2 * (1.0 / 12.0) *
-                              (1.0 - d2 * (1.0 / 30.0) * (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0)))));
+    const double ps =
+        fma(d2, fma(d2, fma(d2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0);
+    *s = fma(d * d2, ps, d);
+    *c = fma(d2,
+             fma(d2,
+                 fma(d2, fma(d2, fma(d2, -1.0 / 3628800.0, 1.0 / 40320.0), -1.0 / 720.0),
+                     1.0 / 24.0),
+                 -0.5),
+             1.0);
 }
 
 // Newton update of one bus (FP64) that also advances u = e^{j theta} and V = Vm u: small
@@ -165,16 +173,19 @@ __device__ __forceinline__ int ntype(const DevPlan& P, const Arrays& a, int i) {
 }
 
 // FP32 copies of the per-bus quantities the FP32 Jacobian fill reads:
-// V, u, Vm and (pu, qu) = u conj(I), so that S = Vm (pu + j qu).
+// V, u, Vm and (pu, qu) = u conj(I), so that S = Vm (pu + j qu).  Five conversions, the
+// products formed in FP32: the FP32 Jacobian is the refinement's preconditioner, and an
+// FP64 operation costs a warp 64 cycles of this GPU's FP64 pipe (an FP32 one, 1-2).
 __device__ __forceinline__ void store_bus_f32(const Arrays& a, int i, double ir, double ii) {
-    const double c = a.Uc[i], s = a.Us[i];
-    a.fvr[i] = float(a.Vre[i]);
-    a.fvi[i] = float(a.Vim[i]);
-    a.fur[i] = float(c);
-    a.fui[i] = float(s);
-    a.fvm[i] = float(a.Vm[i]);
-    a.fpu[i] = float(c * ir + s * ii);
-    a.fqu[i] = float(s * ir - c * ii);
+    const float c = float(a.Uc[i]), s = float(a.Us[i]), vm = float(a.Vm[i]);
+    const float fir = float(ir), fii = float(ii);
+    a.fvr[i] = vm * c;
+    a.fvi[i] = vm * s;
+    a.fur[i] = c;
+    a.fui[i] = s;
+    a.fvm[i] = vm;
+    a.fpu[i] = fmaf(c, fir, s * fii);
+    a.fqu[i] = fmaf(s, fir, -(c * fii));
 }
 
 // I = Y V, S = V conj(I), F1 at pivot positions; returns ||F1||_inf (inf if non-finite).
@@ -200,15 +211,15 @@ __device__ double phase_mismatch(const DevPlan& P, const Arrays& a, const double
         const int p = __ldg(P.bus2pos + i);
         if (p >= 0) {
             const double vr = a.Vre[i], vi = a.Vim[i];
-            const double Pi = vr * ir + vi * ii;
-            const double Qi = vi * ir - vr * ii;
             const int t = ntype<QL>(P, a, i);
             // pg enters at every generator bus that is not a reference bus: PV buses and
             // PV buses switched to PQ under reactive limits (whose network type is still 1)
             const double psp = (__ldg(P.bus_type + i) == 1 ? __ldg(Pg + i) : 0.0) - __ldg(Pd + i);
-            const double fP = psp - Pi;
             const double qsp = (QL ? a.qfix[i] : 0.0) - __ldg(Qd + i);
-            const double fQ = (t == 0) ? qsp - Qi : 0.0;
+            // F = spec - S with S = V conj(I) = (vr ir + vi ii) + j (vi ir - vr ii), as FMA
+            // chains onto the specified values
+            const double fP = fma(-vr, ir, fma(-vi, ii, psp));
+            const double fQ = (t == 0) ? fma(-vi, ir, fma(vr, ii, qsp)) : 0.0;
             a.F[2 * p] = fP;
             a.F[2 * p + 1] = fQ;
             lmax = fmax(lmax, fmax(absinf(fP), absinf(fQ)));
@@ -549,7 +560,7 @@ __device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
 // r = -F1 - J1 dz with J1 dz = -[Re dS; Im dS] linearised through Ybus (FP64):
 // dV_i = u_i dVm_i + j V_i dtheta_i, dS_i = dV_i conj(I_i) + V_i conj(sum_k Y_ik dV_k).
 // r is rounded straight into the solve vector x (the next right-hand side).  Returns
-// ||r||_inf over the true (unpadded) rows.
+// ||r||_inf over the true (unpadded) rows, of r as rounded into x.
 template <typename FT, bool W, bool QL = false>
 __device__ double phase_residual(const DevPlan& P, const Arrays& a, FT* x, double* red) {
     for (int i = GTID; i < P.n_bus; i += GSZ) {
@@ -565,7 +576,7 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, FT* x, doubl
         a.dVim[i] = di;
     }
     gsync<W>();
-    double lmax = 0.0;
+    FT lmax = FT(0);
     for (int i = GTID; i < P.n_bus; i += GSZ) {
         const int p = __ldg(P.bus2pos + i);
         if (p < 0) continue;
@@ -579,16 +590,19 @@ __device__ double phase_residual(const DevPlan& P, const Arrays& a, FT* x, doubl
         }
         const double vr = a.Vre[i], vi = a.Vim[i], Ir = a.Ire[i], Ii = a.Iim[i];
         const double dvr = a.dVre[i], dvi = a.dVim[i];
-        // dS = dV conj(I) + V conj(dI)
-        const double dSr = dvr * Ir + dvi * Ii + vr * ir + vi * ii;
-        const double dSi = dvi * Ir - dvr * Ii + vi * ir - vr * ii;
-        const double rP = -a.F[2 * p] + dSr;
-        const double rQ = (ntype<QL>(P, a, i) == 0) ? -a.F[2 * p + 1] + dSi : 0.0;
-        x[2 * p] = FT(rP);
-        x[2 * p + 1] = FT(rQ);
-        lmax = fmax(lmax, fmax(absinf(rP), absinf(rQ)));
+        // r = -F + dS, dS = dV conj(I) + V conj(dI), as FMA chains onto -F
+        const double rP = fma(dvr, Ir, fma(dvi, Ii, fma(vr, ir, fma(vi, ii, -a.F[2 * p]))));
+        const double rQ =
+            (ntype<QL>(P, a, i) == 0)
+                ? fma(dvi, Ir, fma(-dvr, Ii, fma(vi, ir, fma(-vr, ii, -a.F[2 * p + 1]))))
+                : 0.0;
+        const FT xr = FT(rP), xq = FT(rQ);
+        x[2 * p] = xr;
+        x[2 * p + 1] = xq;
+        // the refinement's stopping norm is taken on the residual as the solve receives it
+        lmax = fmax(lmax, fmax(absinf(xr), absinf(xq)));
     }
-    return group_max<W>(lmax, red);
+    return group_max<W>(double(lmax), red);
 }
 
 // Reactive limits at a converged point: every bus still PV whose recovered reactive
