@@ -84,31 +84,40 @@ __device__ __forceinline__ void gsync() {
     else __syncthreads();
 }
 
-// |v| with non-finite values mapped to +inf (so that max-reductions see them)
-__device__ __forceinline__ double absinf(double v) {
-    double a = fabs(v);
-    return (a <= DBL_MAX) ? a : INFINITY;
+// |v| as an ordered integer key: for non-negative doubles the IEEE order is the order of
+// their bit patterns, so a max over keys is an exact FP64 max done on the integer pipe
+// (an FP64 compare costs a warp 64 cycles of this GPU's FP64 pipe).  NaN keys exceed the
+// key of +inf; key_to_norm maps them (and +inf) to +inf.
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
 }
+__device__ __forceinline__ double key_to_norm(unsigned long long k) {
+    return k < 0x7ff0000000000000ULL ? __longlong_as_double((long long)k) : INFINITY;
+}
+// |v| with non-finite values mapped to +inf (so that max-reductions see them)
 __device__ __forceinline__ float absinf(float v) {
     float a = fabsf(v);
     return (a <= FLT_MAX) ? a : INFINITY;
 }
 
-// Group-wide max; every thread gets the result.  `red` holds one double per warp.
+// Group-wide max of non-negative, non-NaN values (norms, flags); every thread gets the
+// result.  For such values the order of the bit patterns is the order of the values, so
+// the max runs on the integer pipe.  `red` holds one double per warp.
 template <bool W>
 __device__ double group_max(double v, double* red) {
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    unsigned long long k = (unsigned long long)__double_as_longlong(v);
+    for (int o = 16; o; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
     if (W || blockDim.x == 32) {
         __syncwarp();  // also orders the shared-memory writes of the phase that reduced
-        return v;
+        return __longlong_as_double((long long)k);
     }
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
+    if ((threadIdx.x & 31) == 0) red[w] = __longlong_as_double((long long)k);
     __syncthreads();
-    double r = red[0];
-    for (int i = 1; i < nw; ++i) r = fmax(r, red[i]);
-    return r;
+    unsigned long long r = (unsigned long long)__double_as_longlong(red[0]);
+    for (int i = 1; i < nw; ++i) r = max(r, (unsigned long long)__double_as_longlong(red[i]));
+    return __longlong_as_double((long long)r);
 }
 
 // ---------------------------------------------------------------- FP64 network kernels
@@ -150,7 +159,7 @@ __device__ __forceinline__ void update_bus(const Arrays& a, int i, double dth, d
     const double vm = pq ? a.Vm[i] + dvm : a.Vm[i];
     a.Vm[i] = vm;
     double c, s;
-    if (fabs(dth) <= 0.125) {
+    if (abs_key(dth) <= 0x3fc0000000000000ULL) {  // |dth| <= 1/8 (false for NaN)
         double rc, rs;
         small_angle_phasor(dth, &rc, &rs);
         const double uc = a.Uc[i], us = a.Us[i];
@@ -195,7 +204,7 @@ __device__ __forceinline__ void store_bus_f32(const Arrays& a, int i, double ir,
 template <bool F32COPY, bool W, bool QL = false>
 __device__ double phase_mismatch(const DevPlan& P, const Arrays& a, const double* Pd,
                                  const double* Qd, const double* Pg, double* red) {
-    double lmax = 0.0;
+    unsigned long long kmax = 0;
     for (int i = GTID; i < P.n_bus; i += GSZ) {
         double ir = 0.0, ii = 0.0;
         for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
@@ -222,10 +231,10 @@ __device__ double phase_mismatch(const DevPlan& P, const Arrays& a, const double
             const double fQ = (t == 0) ? fma(-vi, ir, fma(vr, ii, qsp)) : 0.0;
             a.F[2 * p] = fP;
             a.F[2 * p + 1] = fQ;
-            lmax = fmax(lmax, fmax(absinf(fP), absinf(fQ)));
+            kmax = max(kmax, max(abs_key(fP), abs_key(fQ)));
         }
     }
-    return group_max<W>(lmax, red);
+    return group_max<W>(key_to_norm(kmax), red);
 }
 
 // G_j = conj(m_j I_j) + sum_i m_i conj(V_i) Y_ij;  w0_j = Re(G_j u_j) = d(m.S)/dVm_j,
@@ -892,7 +901,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     gsync<false>();
     phase_jvt<false>(P, a);  // v_bar2 = -J2^T c = (d[P_R; Q_{B\D}]/dv)^T c
     gsync<false>();
-    double lg = 0.0;
+    unsigned long long kg = 0;
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
         const double gvm = A.dVm[row + i] + a.w0[i];
         const double gva = A.dVa[row + i] + a.w1[i];
@@ -901,10 +910,10 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         if (p >= 0) {
             a.F[2 * p] = gva;                                   // theta component of g_z1
             a.F[2 * p + 1] = (ntype<QL>(P, a, i) == 0) ? gvm : 0.0;  // Vm component (PQ only)
-            lg = fmax(lg, fmax(absinf(gva), absinf(a.F[2 * p + 1])));
+            kg = max(kg, max(abs_key(gva), abs_key(a.F[2 * p + 1])));
         }
     }
-    const double gnorm = group_max<false>(lg, red);
+    const double gnorm = group_max<false>(key_to_norm(kg), red);
 
     // stage the stored factor
     bool have = has_factor != 0;
@@ -939,16 +948,16 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             gsync<false>();
             phase_jvt<false>(P, a);
             gsync<false>();
-            double lr = 0.0;
+            unsigned long long kr = 0;
             for (int p = threadIdx.x; p < P.n; p += blockDim.x) {
                 const int i = __ldg(P.pos2bus + p);
                 const double r0 = a.F[2 * p] + a.w1[i];
                 const double r1 = (ntype<QL>(P, a, i) == 0) ? a.F[2 * p + 1] + a.w0[i] : 0.0;
                 a.r[2 * p] = r0;
                 a.r[2 * p + 1] = r1;
-                lr = fmax(lr, fmax(absinf(r0), absinf(r1)));
+                kr = max(kr, max(abs_key(r0), abs_key(r1)));
             }
-            const double rmax = group_max<false>(lr, red);
+            const double rmax = group_max<false>(key_to_norm(kr), red);
             if (rmax <= A.ir_rtol * gnorm) { conv = true; break; }
             if (s >= A.ir_max || !(rmax <= 1e300)) break;
             for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
