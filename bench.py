@@ -252,7 +252,7 @@ def gpu_leg(args, rank, world):
     import torch
     import torch.distributed as dist
 
-    from paper_2606_07099_gb300.powerflow import PowerFlow
+    from paper_2606_07099_gb300.powerflow import PowerFlow, SolveResult
     from synthgrid import configs
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -519,24 +519,19 @@ def gpu_leg(args, rank, world):
             tot = float(t.item())
         return tot
 
-    # end to end through the public API with host buffers
-    # (the step's four input arrays travel in one pinned buffer, one copy; Vm and Va come
-    # back in one; the solve reads and writes contiguous views of them)
+    # end to end through the C ABI with host buffers (pf_solve_host): every step the solve
+    # kernel reads the step's four input arrays from page-locked host memory and writes
+    # Vm, Va and the status flags back there, in place (over NVLink-C2C on GB300); the
+    # step ends when the stream has finished, with the results in host memory
     host_in = torch.stack(host).pin_memory()
-    dev_in_all = torch.empty(host_in.shape, dtype=torch.float64, device=dev)
-    dev_in = [dev_in_all[k] for k in range(4)]
-    out_dev = torch.empty(2, N, nb, dtype=torch.float64, device=dev)
+    host_views = [host_in[k] for k in range(4)]
     out_host = torch.empty(2, N, nb, dtype=torch.float64).pin_memory()
     st_host = torch.empty(N, dtype=torch.int32).pin_memory()
-    if "e2e" in secs:
-        rese = pf.solve(Pd, Qd, Pg, Vset, **opts)
-        rese.Vm, rese.Va = out_dev[0], out_dev[1]
+    rese = SolveResult(Vm=out_host[0], Va=out_host[1], Pg=None, Qg=None, iters=None,
+                       status=st_host, final_mismatch=None)
 
     def e2e():
-        dev_in_all.copy_(host_in, non_blocking=True)
-        pf.solve(*dev_in, out=rese, **opts)
-        out_host.copy_(out_dev, non_blocking=True)
-        st_host.copy_(rese.status, non_blocking=True)
+        pf.solve_host(*host_views, out=rese, **opts)
 
     none = [float("nan")]
     with ClockSampler(dev.index) as clk:
@@ -726,7 +721,9 @@ def gpu_leg(args, rank, world):
                        "ms_per_step": T_fb2 / K,
                        "workload": "1354-bus grid, 1024 scenarios, config-2 loss cotangents"},
         "e2e": {"value": over_ranks(world, dev, 0.0, conve)[1] * K / (T_e2e / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N},
+                "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N,
+                "api": "pf_solve_host: the solve kernel reads the inputs from and writes Vm, Va "
+                       "and status to page-locked host memory in place"},
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": achieved_eq, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_eq / FP64_PEAK_TFLOPS,

@@ -235,6 +235,37 @@ pf_err pf_solve(pf_handle* h, int batch,
                 void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * pf_solve_host -- pf_solve whose per-scenario arrays may live in host memory: each of
+ * Pd, Qd, Pg, Vset, Vm, Va, Pg_out, Qg_out, iters, status, final_mismatch (same layouts
+ * and NULL rules as pf_solve) may be page-locked host memory (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister) or device memory of the handle's device.  The solve
+ * kernel reads and writes them in place through the unified address space: on a
+ * coherent CPU-GPU link (NVLink-C2C) every scenario's rows move while other scenarios
+ * compute, with no separate copy before or after the launch.  The outputs are complete
+ * once `stream` has been synchronised.  Every array (and the device workspace) is checked
+ * before anything is launched: it must lie, for all the bytes the call touches, inside
+ * one allocation that CUDA knows and that kernels on the handle's device address at the
+ * same pointer value; otherwise (pageable memory, a range past the end of an allocation,
+ * another device's memory) the call returns PF_EINVAL and does nothing.  Errors: those
+ * of pf_solve.
+ */
+pf_err pf_solve_host(pf_handle* h, int batch,
+                     const double* Pd, const double* Qd, const double* Pg, const double* Vset,
+                     double tol, int max_iter, const pf_solve_opts* opts,
+                     double* Vm, double* Va, double* Pg_out, double* Qg_out,
+                     int* iters, int* status, double* final_mismatch,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * pf_addressable -- whether [ptr, ptr + bytes) lies inside one allocation that CUDA knows
+ * (page-locked host memory, or device memory of the handle's device) and that kernels
+ * on that device address at the same pointer value: the check pf_solve_host applies to
+ * each of its arrays.  Writes 1 or 0 to *ok; launches nothing.  Errors: PF_EINVAL (NULL
+ * h or ok).
+ */
+pf_err pf_addressable(const pf_handle* h, const void* ptr, size_t bytes, int* ok);
+
+/*
  * pf_qlim_workspace_size -- device bytes pf_solve_qlim needs for `batch` scenarios with
  * these options (the pf_solve workspace plus the scenario's own bus partition).
  * opts->keep_factors must be 0.  Errors: PF_EINVAL.

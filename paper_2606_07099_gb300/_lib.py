@@ -62,6 +62,9 @@ SIGNATURES = {
     "pf_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
     "pf_solve": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
                       _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_solve_host": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts),
+                           _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_addressable": (_i, [_p, _p, _sz, _ip]),
     "pf_autotune": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, C.POINTER(SolveOpts), _p, _sz, _p,
                          C.POINTER(TuneResult)]),
     "pf_adjoint": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),

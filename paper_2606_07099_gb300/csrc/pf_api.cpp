@@ -3,6 +3,7 @@
 // Host-side responsibilities only: argument checks, the one-time plan
 // (pf_plan.cpp), its upload, the shared-memory/workspace layout of a solve, and
 // the kernel launches (pf_kernels.cu).  No numerical work runs here.
+#include <cuda.h>  // pointer-attribute types only; the driver function is fetched at run time
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -313,6 +314,45 @@ pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, c
     return PF_OK;
 }
 
+// cuPointerGetAttribute, looked up through the runtime (no link-time driver dependency)
+using PtrAttrFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+PtrAttrFn ptr_attr_fn() {
+    static const PtrAttrFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return static_cast<PtrAttrFn>(nullptr);
+        return reinterpret_cast<PtrAttrFn>(f);
+    }();
+    return fn;
+}
+
+// [p, p + bytes) inside one allocation known to CUDA (page-locked host memory, or device
+// memory of `device`) that kernels address at the pointer value p itself.  Any query that
+// fails counts as "no": nothing unproven is handed to a kernel.
+bool addressable(const void* p, size_t bytes, int device) {
+    const PtrAttrFn fn = ptr_attr_fn();
+    if (!fn || !p) return false;
+    const CUdeviceptr d = static_cast<CUdeviceptr>(reinterpret_cast<uintptr_t>(p));
+    unsigned int type = 0;
+    if (fn(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, d) != CUDA_SUCCESS) return false;
+    if (type != CU_MEMORYTYPE_HOST && type != CU_MEMORYTYPE_DEVICE) return false;
+    CUdeviceptr dp = 0;
+    if (fn(&dp, CU_POINTER_ATTRIBUTE_DEVICE_POINTER, d) != CUDA_SUCCESS || dp != d) return false;
+    if (type == CU_MEMORYTYPE_DEVICE) {
+        int ord = -1;
+        if (fn(&ord, CU_POINTER_ATTRIBUTE_DEVICE_ORDINAL, d) != CUDA_SUCCESS || ord != device)
+            return false;
+    }
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (fn(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, d) != CUDA_SUCCESS) return false;
+    if (fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, d) != CUDA_SUCCESS) return false;
+    return d >= start && bytes <= size && static_cast<size_t>(d - start) <= size - bytes;
+}
+
 }  // namespace
 
 namespace pf {
@@ -577,6 +617,41 @@ pf_err pf_solve(pf_handle* h, int batch, const double* Pd, const double* Qd, con
                 const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
                 double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
                 double* final_mismatch, void* workspace, size_t workspace_bytes, void* stream) {
+    return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
+                      iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr);
+}
+
+pf_err pf_addressable(const pf_handle* h, const void* ptr, size_t bytes, int* ok) {
+    if (!h || !ok) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    *ok = addressable(ptr, bytes, h->device) ? 1 : 0;
+    return PF_OK;
+}
+
+pf_err pf_solve_host(pf_handle* h, int batch, const double* Pd, const double* Qd,
+                     const double* Pg, const double* Vset, double tol, int max_iter,
+                     const pf_solve_opts* opts, double* Vm, double* Va, double* Pg_out,
+                     double* Qg_out, int* iters, int* status, double* final_mismatch,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+    if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
+        return PF_EINVAL;
+    if (!opts_ok(opts)) return PF_EINVAL;
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    const LaunchCfg cfg = resolve(h, opts);
+    const pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, cfg.placement);
+    const size_t row = sizeof(double) * (size_t)batch * (size_t)h->plan.n_bus;
+    DeviceGuard guard(h->device);
+    const void* in[] = {Pd, Qd, Pg, Vset, Vm, Va};
+    for (const void* p : in)
+        if (!addressable(p, row, h->device)) return PF_EINVAL;
+    if ((Pg_out && !addressable(Pg_out, row, h->device)) ||
+        (Qg_out && !addressable(Qg_out, row, h->device)) ||
+        (iters && !addressable(iters, sizeof(int) * (size_t)batch, h->device)) ||
+        !addressable(status, sizeof(int) * (size_t)batch, h->device) ||
+        (final_mismatch && !addressable(final_mismatch, sizeof(double) * (size_t)batch, h->device)))
+        return PF_EINVAL;
+    const size_t ws_need = L.slot_bytes * (size_t)batch;
+    if (workspace_bytes < ws_need || !addressable(workspace, ws_need, h->device)) return PF_EINVAL;
     return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
                       iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr);
 }

@@ -221,6 +221,52 @@ class PowerFlow:
         self._last = (batch, ws, bool(keep_factors))
         return out
 
+    def solve_host(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
+                   ir_rtol=1e-3, group_threads=0, keep_factors=False,
+                   out: SolveResult | None = None, placement=0, instances_per_cta=0,
+                   ir_gate=0.0) -> SolveResult:
+        """pf_solve_host: the solve reading its inputs from, and writing its outputs to,
+        page-locked host tensors (``pin_memory()``) in place; device tensors are accepted
+        too.  The outputs (page-locked host tensors unless ``out`` is given) are complete
+        once the current stream is synchronised.  The library refuses (PFError EINVAL) any
+        buffer it cannot prove kernels may address."""
+        batch = Pd.shape[0]
+        for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
+            if not isinstance(v, torch.Tensor) or v.dtype != torch.float64 or v.dim() != 2 \
+                    or v.shape != (batch, self.n_bus) or not v.is_contiguous():
+                raise ValueError(f"{nm} must be a contiguous float64 [batch, {self.n_bus}] tensor")
+            if not v.is_cuda and not v.is_pinned():
+                raise ValueError(f"{nm} must be page-locked (pin_memory()) or on the device")
+        opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
+                              instances_per_cta, ir_gate)
+        ws = self.workspace(batch, opts)
+        if out is None:
+            e = dict(dtype=torch.float64, pin_memory=True)
+            out = SolveResult(
+                Vm=torch.empty(batch, self.n_bus, **e), Va=torch.empty(batch, self.n_bus, **e),
+                Pg=torch.empty(batch, self.n_bus, **e), Qg=torch.empty(batch, self.n_bus, **e),
+                iters=torch.empty(batch, dtype=torch.int32, pin_memory=True),
+                status=torch.empty(batch, dtype=torch.int32, pin_memory=True),
+                final_mismatch=torch.empty(batch, dtype=torch.float64, pin_memory=True))
+        ptr = lambda t: t.data_ptr() if t is not None else None
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        L.check(self._lib.pf_solve_host(
+            self._h, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(), Vset.data_ptr(),
+            float(tol), int(max_iter), C.byref(opts), out.Vm.data_ptr(), out.Va.data_ptr(),
+            ptr(out.Pg), ptr(out.Qg), ptr(out.iters), out.status.data_ptr(),
+            ptr(out.final_mismatch), ws.data_ptr(), ws.numel(), stream), "pf_solve_host")
+        self._solve_id += 1
+        self._last = (batch, ws, bool(keep_factors))
+        return out
+
+    def addressable(self, t: torch.Tensor, nbytes: int | None = None) -> bool:
+        """pf_addressable: whether the library would hand ``t``'s first ``nbytes`` bytes
+        (default: all of them) to a kernel."""
+        ok = C.c_int(0)
+        n = t.numel() * t.element_size() if nbytes is None else int(nbytes)
+        L.check(self._lib.pf_addressable(self._h, t.data_ptr(), n, C.byref(ok)), "pf_addressable")
+        return bool(ok.value)
+
     def solve_qlim(self, Pd, Qd, Pg, Vset, Qmin, Qmax, tol=1e-8, max_iter=20, max_rounds=10,
                    precision="mixed", ir_steps=2, ir_rtol=1e-3, group_threads=0, placement=0,
                    instances_per_cta=0, ir_gate=0.0, keep_factors=False) -> SolveResult:
