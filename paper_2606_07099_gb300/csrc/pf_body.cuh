@@ -376,6 +376,46 @@ __device__ __forceinline__ Blk<FT> schur_gather(const DevPlan& P, const FT* fac,
     return acc;
 }
 
+// Two targets' gathers interleaved (A over ca..ea, B over cb..eb), half a batch of each
+// per round so that both chains of loads are in flight at once.  Each target still sums
+// its pairs in order from zero, as schur_gather does (the zero blocks of a short round
+// add +0, which leaves every partial sum unchanged).
+template <typename FT>
+__device__ __forceinline__ void schur_gather2(const DevPlan& P, const FT* fac, int ca, int ea,
+                                              int cb, int eb, Blk<FT>& A, Blk<FT>& B) {
+    A = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
+    B = A;
+    constexpr int NB = kBatch<FT> / 2 > 0 ? kBatch<FT> / 2 : 1;
+    for (; ca < ea || cb < eb; ca += NB, cb += NB) {
+        int2 la[NB], lb[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            la[k] = (ca + k < ea) ? __ldg(P.sch + ca + k) : make_int2(-1, -1);
+            lb[k] = (cb + k < eb) ? __ldg(P.sch + cb + k) : make_int2(-1, -1);
+        }
+        Blk<FT> xa[NB], ya[NB], xb[NB], yb[NB];
+        const Blk<FT> z{FT(0), FT(0), FT(0), FT(0)};
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            xa[k] = la[k].x >= 0 ? ldb(fac, la[k].x) : z;
+            ya[k] = la[k].x >= 0 ? ldb(fac, la[k].y) : z;
+            xb[k] = lb[k].x >= 0 ? ldb(fac, lb[k].x) : z;
+            yb[k] = lb[k].x >= 0 ? ldb(fac, lb[k].y) : z;
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            A.a += xa[k].a * ya[k].a + xa[k].b * ya[k].c;
+            A.b += xa[k].a * ya[k].b + xa[k].b * ya[k].d;
+            A.c += xa[k].c * ya[k].a + xa[k].d * ya[k].c;
+            A.d += xa[k].c * ya[k].b + xa[k].d * ya[k].d;
+            B.a += xb[k].a * yb[k].a + xb[k].b * yb[k].c;
+            B.b += xb[k].a * yb[k].b + xb[k].b * yb[k].d;
+            B.c += xb[k].c * yb[k].a + xb[k].d * yb[k].c;
+            B.d += xb[k].c * yb[k].b + xb[k].d * yb[k].d;
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ Blk<T> sub_blk(Blk<T> m, Blk<T> s) {
     return {m.a - s.a, m.b - s.b, m.c - s.c, m.d - s.d};
@@ -392,21 +432,49 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
     int bad = 0;
     if (!W && threadIdx.x == 0) *s_bad = 0;
     for (int l = 0; l < P.n_levels; ++l) {
+        // FP32 factor: two items per thread and round, so that two chains of loads are in
+        // flight (within a level the pivots read, the L blocks scaled and the Schur
+        // targets written are disjoint sets of blocks).  The FP64 factor keeps one: its
+        // block arithmetic is bound by the FP64 pipe, and the pairing measured slower.
+        constexpr int IPT = sizeof(FT) == 4 ? 2 : 1;
         const int a0 = __ldg(P.la_ptr + l), a1 = __ldg(P.la_ptr + l + 1);
-        for (int c = a0 + GTID; c < a1; c += GSZ) {
+        for (int c = a0 + GTID; c < a1; c += IPT * GSZ) {
             const int2 ld = __ldg(P.la + c);
             int dummy = 0;
-            stb(fac, ld.x, mul(ldb(fac, ld.x), inv2(ldb(fac, ld.y), &dummy)));
+            if constexpr (IPT == 2) {
+                const bool two = c + GSZ < a1;
+                const int2 ld2 = two ? __ldg(P.la + c + GSZ) : ld;
+                const Blk<FT> m1 = ldb(fac, ld.x), q1 = ldb(fac, ld.y);
+                const Blk<FT> m2 = ldb(fac, ld2.x), q2 = ldb(fac, ld2.y);
+                stb(fac, ld.x, mul(m1, inv2(q1, &dummy)));
+                if (two) stb(fac, ld2.x, mul(m2, inv2(q2, &dummy)));
+            } else {
+                stb(fac, ld.x, mul(ldb(fac, ld.x), inv2(ldb(fac, ld.y), &dummy)));
+            }
         }
         gsync<W>();
         const int t0 = __ldg(P.sch_tptr + l), t1 = __ldg(P.sch_tptr + l + 1);
         const int G = __ldg(P.lev_g + l).z;  // lanes per target (a power of two <= 32; uniform)
-        if (G == 1) {  // one thread per target
-            for (int t = t0 + GTID; t < t1; t += GSZ) {
-                const Blk<FT> acc = schur_gather(P, fac, __ldg(P.sch_cptr + t),
-                                                 __ldg(P.sch_cptr + t + 1), 1);
-                const int tg = __ldg(P.sch_tgt + t);
-                stb(fac, tg, sub_blk(ldb(fac, tg), acc));
+        if (G == 1) {  // one thread per target (IPT targets per round)
+            for (int t = t0 + GTID; t < t1; t += IPT * GSZ) {
+                if constexpr (IPT == 2) {
+                    const int t2 = t + GSZ;
+                    const bool two = t2 < t1;
+                    Blk<FT> acc, acc2;
+                    schur_gather2(P, fac, __ldg(P.sch_cptr + t), __ldg(P.sch_cptr + t + 1),
+                                  two ? __ldg(P.sch_cptr + t2) : 0,
+                                  two ? __ldg(P.sch_cptr + t2 + 1) : 0, acc, acc2);
+                    const int tg = __ldg(P.sch_tgt + t);
+                    const int tg2 = two ? __ldg(P.sch_tgt + t2) : tg;
+                    const Blk<FT> o1 = ldb(fac, tg), o2 = ldb(fac, tg2);
+                    stb(fac, tg, sub_blk(o1, acc));
+                    if (two) stb(fac, tg2, sub_blk(o2, acc2));
+                } else {
+                    const Blk<FT> acc = schur_gather(P, fac, __ldg(P.sch_cptr + t),
+                                                     __ldg(P.sch_cptr + t + 1), 1);
+                    const int tg = __ldg(P.sch_tgt + t);
+                    stb(fac, tg, sub_blk(ldb(fac, tg), acc));
+                }
             }
         } else {  // G lanes per target; every lane runs the same rounds
             const int sub = GTID & (G - 1), nrg = GSZ / G;
@@ -427,9 +495,18 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
                 }
             }
         }
-        for (int p = __ldg(P.lev_ptr + l) + GTID; p < __ldg(P.lev_ptr + l + 1); p += GSZ) {
+        const int r1 = __ldg(P.lev_ptr + l + 1);
+        for (int p = __ldg(P.lev_ptr + l) + GTID; p < r1; p += IPT * GSZ) {
             const int dk = __ldg(P.lu_diag + p);
-            stb(fac, dk, inv2(ldb(fac, dk), &bad));
+            if constexpr (IPT == 2) {
+                const bool two = p + GSZ < r1;
+                const int dk2 = two ? __ldg(P.lu_diag + p + GSZ) : dk;
+                const Blk<FT> d1 = ldb(fac, dk), d2 = ldb(fac, dk2);
+                stb(fac, dk, inv2(d1, &bad));
+                if (two) stb(fac, dk2, inv2(d2, &bad));
+            } else {
+                stb(fac, dk, inv2(ldb(fac, dk), &bad));
+            }
         }
         gsync<W>();
     }
