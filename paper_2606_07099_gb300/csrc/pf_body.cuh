@@ -303,17 +303,29 @@ __device__ __forceinline__ Blk<T> pad_pv(Blk<T> m, bool diag, int ti, int tj) {
 
 template <bool W, bool QL = false>
 __device__ void phase_fill(const DevPlan& P, const Arrays& a, float* fac) {
-    for (int e = GTID; e < P.nnzb; e += GSZ) {
-        const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
-        const int yi = __ldg(P.fill_y + e);
-        const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
+    // two blocks per thread and round: both blocks' loads are issued before either store
+    // (the stores to the factor could otherwise alias the next block's bus reads)
+    auto block = [&](int e, int p, int q, int yi, int i, int j) {
         Blk<float> m{0.f, 0.f, 0.f, 0.f};
         if (yi >= 0) {
             const float2 y = __ldg(P.y_gb32 + yi);
             m = jac_block<float>(p == q, y.x, y.y, a.fvr[i], a.fvi[i], a.fur[j], a.fui[j],
                                  a.fvm[j], a.fvm[i], a.fpu[i], a.fqu[i]);
         }
-        stb(fac, e, pad_pv(m, p == q, ntype<QL>(P, a, i), ntype<QL>(P, a, j)));
+        return pad_pv(m, p == q, ntype<QL>(P, a, i), ntype<QL>(P, a, j));
+    };
+    for (int e = GTID; e < P.nnzb; e += 2 * GSZ) {
+        const int e2 = e + GSZ;
+        const bool two = e2 < P.nnzb;
+        const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e);
+        const int p2 = two ? __ldg(P.lu_row + e2) : p, q2 = two ? __ldg(P.lu_col + e2) : q;
+        const int yi = __ldg(P.fill_y + e), yi2 = two ? __ldg(P.fill_y + e2) : -1;
+        const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
+        const int i2 = __ldg(P.pos2bus + p2), j2 = __ldg(P.pos2bus + q2);
+        const Blk<float> m1 = block(e, p, q, yi, i, j);
+        const Blk<float> m2 = block(e2, p2, q2, yi2, i2, j2);
+        stb(fac, e, m1);
+        if (two) stb(fac, e2, m2);
     }
 }
 
