@@ -137,8 +137,8 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int place
     if (!L.fwd.vec_in_smem) vec_global = std::max(vec_global, L.fwd.vec_bytes);
     if (keep && !L.adj.vec_in_smem) vec_global = std::max(vec_global, L.adj.vec_bytes);
     size_t o = 0;
-    L.off_state = o;
-    o = pf::align_up(o + sizeof(double) * 2 * (size_t)P.n_bus, 256);
+    L.off_state = o;  // kept factors: Vm, Va, Uc, Us, Ire, Iim at the solution; else Vm, Va
+    o = pf::align_up(o + sizeof(double) * (keep ? 6 : 2) * (size_t)P.n_bus, 256);
     L.off_flags = o;
     o = pf::align_up(o + 16, 256);
     if (L.fac_global) {

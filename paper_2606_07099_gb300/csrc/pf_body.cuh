@@ -121,19 +121,6 @@ __device__ double group_max(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- FP64 network kernels
-// u = e^{j theta}, V = Vm u
-template <bool W>
-__device__ void phase_voltage(const DevPlan& P, const Arrays& a) {
-    for (int i = GTID; i < P.n_bus; i += GSZ) {
-        double s, c;
-        sincos(a.Va[i], &s, &c);
-        a.Uc[i] = c;
-        a.Us[i] = s;
-        a.Vre[i] = a.Vm[i] * c;
-        a.Vim[i] = a.Vm[i] * s;
-    }
-}
-
 // e^{j d} for a Newton angle step |d| <= 1/8 from the Maclaurin series of sin and cos,
 // truncated after d^9 and d^10: the first omitted terms, d^11/11! and d^12/12!, are below
 // 2.4e-17 and 3.1e-20 relative.  Horner form in d^2 with the series' own coefficients
@@ -260,8 +247,9 @@ __device__ void phase_jvt(const DevPlan& P, const Arrays& a) {
         }
         const double mr = a.Psp[j], mi = a.Qsp[j];
         const double Ir = a.Ire[j], Ii = a.Iim[j];
-        gr += mr * Ir - mi * Ii;      // conj(m I) = (mr Ir - mi Ii) - j(mr Ii + mi Ir)
-        gi -= mr * Ii + mi * Ir;
+        // conj(m I) = (mr Ir - mi Ii) - j(mr Ii + mi Ir), as FMA chains onto the sums
+        gr = fma(mr, Ir, fma(-mi, Ii, gr));
+        gi = fma(-mr, Ii, fma(-mi, Ir, gi));
         const double vr = a.Vre[j], vi = a.Vim[j];
         a.w0[j] = gr * a.Uc[j] - gi * a.Us[j];
         a.w1[j] = -(gr * vi + gi * vr);
@@ -830,9 +818,13 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         const double Pi = vr * ir + vi * ii, Qi = vi * ir - vr * ii;
         A.Vm[row + i] = a.Vm[i];
         A.Va[row + i] = a.Va[i];
-        if (A.keep_factors) {  // the solution the adjoint differentiates at
-            st[i] = a.Vm[i];
+        if (A.keep_factors) {  // the solution the adjoint differentiates at, with its
+            st[i] = a.Vm[i];     // phasor and injected current (from the final mismatch)
             st[P.n_bus + i] = a.Va[i];
+            st[2 * P.n_bus + i] = a.Uc[i];
+            st[3 * P.n_bus + i] = a.Us[i];
+            st[4 * P.n_bus + i] = ir;
+            st[5 * P.n_bus + i] = ii;
         }
         if (A.Pg_out) A.Pg_out[row + i] = (t == 1) ? A.Pg[row + i] : (t == 2 ? Pi + A.Pd[row + i] : 0.0);
         if (A.Qg_out) A.Qg_out[row + i] = (t == 0) ? 0.0 : Qi + A.Qd[row + i];
@@ -959,27 +951,21 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
         if (threadIdx.x == 0 && A.adj_status) A.adj_status[b] = fwd_status;
         return;
     }
+    // the solution z* with u = e^{j theta} and I = Y V as the forward's final mismatch
+    // evaluated them (no FP64 sincos or SpMV here)
     const double* st = reinterpret_cast<const double*>(slot + L.off_state);
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
-        a.Vm[i] = st[i];
+        const double vm = st[i], c = st[2 * P.n_bus + i], s = st[3 * P.n_bus + i];
+        a.Vm[i] = vm;
         a.Va[i] = st[P.n_bus + i];
+        a.Uc[i] = c;
+        a.Us[i] = s;
+        a.Vre[i] = vm * c;
+        a.Vim[i] = vm * s;
+        a.Ire[i] = st[4 * P.n_bus + i];
+        a.Iim[i] = st[5 * P.n_bus + i];
     }
     if (threadIdx.x == 0) s_bad = 0;
-    gsync<false>();
-    phase_voltage<false>(P, a);
-    gsync<false>();
-    for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {  // I = Y V
-        double ir = 0.0, ii = 0.0;
-        for (int k = __ldg(P.y_ptr + i); k < __ldg(P.y_ptr + (i + 1)); ++k) {
-            const int j = __ldg(P.y_idx + k);
-            const double2 y = __ldg(P.y_gb + k);
-            ir = fma(y.x, a.Vre[j], fma(-y.y, a.Vim[j], ir));
-            ii = fma(y.x, a.Vim[j], fma(y.y, a.Vre[j], ii));
-        }
-        a.Ire[i] = ir;
-        a.Iim[i] = ii;
-        store_bus_f32(a, i, ir, ii);
-    }
     // Step-2 weights: c_P on R (dL/dpg_R), c_Q on B\D (dL/dqg; under reactive limits the
     // final B\D: a switched bus's qg is its limit, not a recovered output)
     for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x) {
@@ -1014,7 +1000,12 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
     int astat = 0;
     bool refactored = false;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        if (!have) {
+        if (!have) {  // refactor at z*: the FP32 fill copies first
+            if (sizeof(FT) == 4) {
+                for (int i = threadIdx.x; i < P.n_bus; i += blockDim.x)
+                    store_bus_f32(a, i, a.Ire[i], a.Iim[i]);
+                gsync<false>();
+            }
             phase_fill<false, QL>(P, a, fac);
             gsync<false>();
             if (phase_lu<FT, false>(P, fac, &s_bad)) { astat = 3; break; }

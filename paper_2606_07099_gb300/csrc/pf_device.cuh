@@ -53,7 +53,8 @@ struct KernelSmem {
 // Per-scenario workspace slot (global memory), offsets in bytes from the slot base.
 struct SlotLayout {
     size_t slot_bytes;
-    size_t off_state;   // double Vm[n_bus], Va[n_bus]: the solution, for pf_adjoint
+    size_t off_state;   // doubles [n_bus] each: Vm, Va (and with kept factors u = e^{j Va}
+                        // as Uc, Us and I = Y V as Ire, Iim): the solution, for pf_adjoint
     size_t off_flags;   // int status, iters, has_factor, pad
     size_t off_fac;     // factor values (if stored in global memory), or 0
     size_t off_vec;     // vector arena (if a kernel keeps it in global memory), or 0
