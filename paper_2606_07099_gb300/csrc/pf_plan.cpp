@@ -5,7 +5,9 @@
 //   2. check that every bus reaches a slack bus through nonzero Ybus entries;
 //   3. order the non-slack buses by minimum degree on the bus graph (the J1
 //      block pattern inherits the Ybus pattern, Sec. III-B.1), so that the 2x2
-//      block LU of J1 has little fill;
+//      block LU of J1 has little fill, breaking ties and near-ties (degree within
+//      kOrderSlack of the minimum) towards a shallower elimination tree: every tree
+//      level is a barrier-separated step of the factorisation and of each sweep;
 //   4. build the elimination tree, group the pivots by tree level and renumber
 //      them level by level (any topological order of the tree gives the same
 //      fill, so this keeps the fill of step 3);
@@ -49,30 +51,47 @@ int find_in_row(const std::vector<int>& ptr, const std::vector<int>& col, int r,
 }  // namespace
 
 void minimum_degree(const std::vector<std::vector<int>>& adj0, std::vector<int>& order,
-                    std::vector<std::vector<int>>& structs) {
+                    std::vector<std::vector<int>>& structs, int slack) {
     const int n = (int)adj0.size();
     std::vector<std::vector<int>> adj = adj0;
-    std::vector<char> done(n, 0);
-    std::set<std::pair<int, int>> queue;  // (current degree, node): lowest degree, then lowest id
-    for (int v = 0; v < n; ++v) queue.insert({(int)adj[v].size(), v});
+    // lvl[v]: a lower bound of v's elimination-tree level (every eliminated neighbour of
+    // v is a descendant of v).  The next pivot is, among the nodes whose current degree
+    // is within `slack` of the minimum, the one of lowest lvl (then lowest degree, then
+    // lowest id): ties, and near-ties, are broken towards a shallower tree.
+    std::vector<int> lvl(n, 0);
+    std::vector<std::set<std::pair<int, int>>> bucket(n + 1);  // by degree: (lvl, node)
+    for (int v = 0; v < n; ++v) bucket[adj[v].size()].insert({0, v});
     order.clear();
     order.reserve(n);
     structs.assign(n, {});
     std::vector<int> tmp;
-    while (!queue.empty()) {
-        int v = queue.begin()->second;
-        queue.erase(queue.begin());
-        done[v] = 1;
+    int dmin = 0;
+    for (int left = n; left > 0; --left) {
+        while (bucket[dmin].empty()) ++dmin;
+        int v = -1, bd = 0, bl = 0;
+        for (int d = dmin; d <= std::min(n, dmin + slack); ++d) {
+            if (bucket[d].empty()) continue;
+            const auto& c = *bucket[d].begin();
+            if (v < 0 || c.first < bl || (c.first == bl && d < bd) ||
+                (c.first == bl && d == bd && c.second < v)) {
+                v = c.second;
+                bd = d;
+                bl = c.first;
+            }
+        }
+        bucket[bd].erase({bl, v});
         order.push_back(v);
         const std::vector<int> nb = adj[v];  // all alive (eliminated nodes are removed)
         structs[v] = nb;
         for (int u : nb) {
-            queue.erase({(int)adj[u].size(), u});
+            bucket[adj[u].size()].erase({lvl[u], u});
             merge_without(adj[u], nb, u, v, tmp);  // u joins the clique of v's neighbours
             adj[u].swap(tmp);
-            queue.insert({(int)adj[u].size(), u});
+            lvl[u] = std::max(lvl[u], lvl[v] + 1);
+            bucket[adj[u].size()].insert({lvl[u], u});
         }
         adj[v].clear();
+        dmin = std::max(0, dmin - 1);  // a neighbour's degree drops by at most one (it loses v)
     }
 }
 
@@ -181,7 +200,7 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
     }
     std::vector<int> order;
     std::vector<std::vector<int>> structs;
-    minimum_degree(adj, order, structs);
+    minimum_degree(adj, order, structs, kOrderSlack);
     std::vector<int> elim(n);  // node -> elimination index
     for (int k = 0; k < n; ++k) elim[order[k]] = k;
 
