@@ -81,6 +81,10 @@ typedef struct {
     int n_levels;      /* depth of the elimination tree */
     long long schur_block_ops; /* 2x2 multiply-subtracts of one factorisation */
     long long plan_bytes;      /* the network's device plan (shared by every scenario) */
+    int dense_tail;            /* blocks in the dense tail: the last dense_tail elimination
+                                  levels hold one pivot each and their trailing block is
+                                  full, so the LU factors it densely in shared memory
+                                  (0: none) */
 } pf_plan_info;
 
 /* Tunables of a solve; zero-initialise and set what you need. */

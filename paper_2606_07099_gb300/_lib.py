@@ -25,7 +25,8 @@ class PlanInfo(C.Structure):
     _fields_ = [("n_bus", C.c_int), ("n_slack", C.c_int), ("n_pv", C.c_int), ("n_pq", C.c_int),
                 ("n_unknowns", C.c_int), ("n_block", C.c_int), ("nnz_ybus", C.c_int),
                 ("nnz_j1", C.c_int), ("nnzb_lu", C.c_int), ("n_levels", C.c_int),
-                ("schur_block_ops", C.c_longlong), ("plan_bytes", C.c_longlong)]
+                ("schur_block_ops", C.c_longlong), ("plan_bytes", C.c_longlong),
+                ("dense_tail", C.c_int)]
 
 
 class SolveOpts(C.Structure):

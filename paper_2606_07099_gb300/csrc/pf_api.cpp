@@ -127,11 +127,19 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int place
     const pf::Plan& P = h->plan;
     pf::SlotLayout L{};
     L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
-    const size_t budget = smem_budget(h);
+    // the dense tail's staging area comes out of the budget first, then follows the
+    // placement's own arrays (a multiple of 16 bytes: warp arenas are laid end to end)
+    const size_t dense = pf::align_up((size_t)P.dense_s * P.dense_s * 4 * ft_bytes, 16);
+    const size_t full = smem_budget(h);
+    const size_t budget = full > dense ? full - dense : 0;
     L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes, budget,
                   placement, (size_t)ft_bytes * 2 * (size_t)P.n);
     L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes, budget,
                   placement);
+    for (pf::KernelSmem* k : {&L.fwd, &L.adj}) {
+        k->smem_dense_off = pf::align_up(k->smem_bytes, 16);
+        k->smem_bytes = k->smem_dense_off + dense;
+    }
     L.fac_global = (!L.fwd.fac_in_smem || keep) ? 1 : 0;
     size_t vec_global = 0;
     if (!L.fwd.vec_in_smem) vec_global = std::max(vec_global, L.fwd.vec_bytes);
@@ -506,6 +514,8 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     d.n = P.n;
     d.nnzb = P.nnzb();
     d.n_levels = P.n_levels;
+    d.dense_s = P.dense_s;
+    d.dense_l0 = P.dense_l0;
     d.y_ptr = I(po.yptr);
     d.y_idx = I(po.yidx);
     d.y_gb = reinterpret_cast<const double2*>(base + po.ygb);
@@ -552,6 +562,7 @@ static void fill_info(const pf::Plan& P, size_t plan_bytes, pf_plan_info* info) 
     info->n_levels = P.n_levels;
     info->schur_block_ops = P.schur_ops;
     info->plan_bytes = (long long)plan_bytes;
+    info->dense_tail = P.dense_s;
 }
 
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info) {
@@ -827,9 +838,10 @@ JobForm multi_form(const pf_handle* h, const pf_solve_opts* opts) {
     const size_t vec = pf::carve(nullptr, P.n_bus, P.n, ft, false, nullptr);
     const size_t fac = pf::align_up((size_t)P.nnzb() * 4 * ft, 16);
     const size_t wpc = (size_t)multi_threads(opts) / 32;
+    const size_t dense = pf::align_up((size_t)P.dense_s * P.dense_s * 4 * ft, 16);
     if (wpc >= 2 && P.n_bus <= kWarpFormBuses)
-        return {1, (vec + fac) * wpc <= budget ? PF_PLACE_ONCHIP : PF_PLACE_GLOBAL};
-    return {0, fac + (size_t)ft * 2 * P.n <= budget ? PF_PLACE_FACTOR : PF_PLACE_GLOBAL};
+        return {1, (vec + fac + dense) * wpc <= budget ? PF_PLACE_ONCHIP : PF_PLACE_GLOBAL};
+    return {0, fac + (size_t)ft * 2 * P.n + dense <= budget ? PF_PLACE_FACTOR : PF_PLACE_GLOBAL};
 }
 
 pf::SlotLayout multi_layout(const pf_handle* h, const pf_solve_opts* opts) {

@@ -421,17 +421,61 @@ __device__ __forceinline__ Blk<T> sub_blk(Blk<T> m, Blk<T> s) {
     return {m.a - s.a, m.b - s.b, m.c - s.c, m.d - s.d};
 }
 
+// The plan's dense tail: the last s levels hold one row each and rows p0 = n - s .. n - 1
+// are full from column p0 on (block (a, b) of the tail sits at lu_diag[p0 + a] - a + b).
+// It is staged in shared memory (D, s x s blocks, row-major) and factored densely with the
+// level schedule's own steps in its order -- L column scaling by the pivot's inverse,
+// Schur updates, the pivot replaced by its inverse -- so that its s steps cost
+// shared-memory round trips instead of the schedule's index chains through global memory.
+template <typename FT, bool W>
+__device__ void dense_tail_lu(const DevPlan& P, FT* fac, FT* D, int* bad) {
+    const int s = P.dense_s, p0 = P.n - s;
+    for (int t = GTID; t < s * s; t += GSZ) {
+        const int a = t / s, b = t - a * s;
+        stb(D, t, ldb(fac, __ldg(P.lu_diag + p0 + a) - a + b));
+    }
+    gsync<W>();
+    for (int k = 0; k < s; ++k) {
+        const int m = s - 1 - k;
+        for (int i = GTID; i < m; i += GSZ) {  // L(k+1+i, k) <- A(k+1+i, k) A(k, k)^-1
+            const int r = (k + 1 + i) * s + k;
+            int dummy = 0;
+            stb(D, r, mul(ldb(D, r), inv2(ldb(D, k * s + k), &dummy)));
+        }
+        gsync<W>();
+        for (int t = GTID; t < m * m; t += GSZ) {  // A(i, j) -= L(i, k) U(k, j), i, j > k
+            const int i = k + 1 + t / m, j = k + 1 + t % m;
+            const Blk<FT> x = ldb(D, i * s + k), y = ldb(D, k * s + j);
+            Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+            acc.a += x.a * y.a + x.b * y.c;
+            acc.b += x.a * y.b + x.b * y.d;
+            acc.c += x.c * y.a + x.d * y.c;
+            acc.d += x.c * y.b + x.d * y.d;
+            stb(D, i * s + j, sub_blk(ldb(D, i * s + j), acc));
+        }
+        if (GTID == 0) stb(D, k * s + k, inv2(ldb(D, k * s + k), bad));  // no target touches it
+        gsync<W>();
+    }
+    for (int t = GTID; t < s * s; t += GSZ) {
+        const int a = t / s, b = t - a * s;
+        stb(fac, __ldg(P.lu_diag + p0 + a) - a + b, ldb(D, t));
+    }
+    gsync<W>();
+}
+
 // Right-looking, one elimination-tree level at a time.  Phase A scales the L columns of
 // the level's pivots; phase B gathers every Schur update of the level into its target
 // block (no two threads write the same block) and replaces the level's pivot blocks by
 // their inverses.  (A variant with one barrier per level, recomputing L(i,k) inside each
 // Schur update, measured slower: the extra 2x2 inverse per update costs more than the
-// barrier it saves.)  Returns nonzero if a pivot was singular.
+// barrier it saves.)  The plan's dense tail, if any, is factored by dense_tail_lu in
+// `dense` (shared memory).  Returns nonzero if a pivot was singular.
 template <typename FT, bool W>
-__device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
+__device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad, FT* dense) {
     int bad = 0;
     if (!W && threadIdx.x == 0) *s_bad = 0;
-    for (int l = 0; l < P.n_levels; ++l) {
+    const int n_sparse = P.dense_s ? P.dense_l0 : P.n_levels;
+    for (int l = 0; l < n_sparse; ++l) {
         // FP32 factor: two items per thread and round, so that two chains of loads are in
         // flight (within a level the pivots read, the L blocks scaled and the Schur
         // targets written are disjoint sets of blocks).  The FP64 factor keeps one: its
@@ -510,6 +554,7 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad) {
         }
         gsync<W>();
     }
+    if (P.dense_s) dense_tail_lu<FT, W>(P, fac, dense, &bad);
     if (W) return __any_sync(0xffffffffu, bad);
     if (bad) *s_bad = 1;
     gsync<W>();
@@ -778,7 +823,11 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         if (it_round >= A.max_iter) { status = 1; break; }
         phase_fill<W, QL>(P, a, fac);
         gsync<W>();
-        if (phase_lu<FT, W>(P, fac, &s_bad)) { status = 3; factored = false; break; }
+        if (phase_lu<FT, W>(P, fac, &s_bad, reinterpret_cast<FT*>(smem + K.smem_dense_off))) {
+            status = 3;
+            factored = false;
+            break;
+        }
         factored = true;
         // first solve with the FT factor
         for (int k = GTID; k < 2 * P.n; k += GSZ) x[k] = FT(-a.F[k]);
@@ -1008,7 +1057,11 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             }
             phase_fill<false, QL>(P, a, fac);
             gsync<false>();
-            if (phase_lu<FT, false>(P, fac, &s_bad)) { astat = 3; break; }
+            if (phase_lu<FT, false>(P, fac, &s_bad,
+                                    reinterpret_cast<FT*>(smem + K.smem_dense_off))) {
+                astat = 3;
+                break;
+            }
             have = true;
             refactored = true;
         }

@@ -9,6 +9,7 @@ namespace pf {
 // Read-only plan arrays on the device (see pf_plan.h for their meaning).
 struct DevPlan {
     int n_bus, n, nnzb, n_levels;
+    int dense_s, dense_l0;  // dense tail: its size in blocks and first level (0: none)
     const int* y_ptr;
     const int* y_idx;
     const double2* y_gb;  // (G, B) of every Ybus entry
@@ -48,6 +49,7 @@ struct KernelSmem {
     int x_in_smem;        // the solve vector in shared memory although the vectors are not
     size_t smem_x_off;    // its offset inside the dynamic shared memory
     size_t vec_bytes;     // size of this kernel's vector arena
+    size_t smem_dense_off;  // the dense tail's staging area (dense_s^2 blocks), if any
 };
 
 // Per-scenario workspace slot (global memory), offsets in bytes from the slot base.

@@ -349,6 +349,26 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         P.lev_gS[l] = lanes(mS, targets);
     }
 
+    // dense tail: the most trailing levels (at most kDenseMax) that hold one row each and
+    // whose rows are full from the tail's first position on.  The factorisation stages
+    // that block in shared memory and factors it densely instead of level by level.
+    {
+        int s = 0;
+        while (s < kDenseMax && s < n_levels &&
+               P.lev_ptr[n_levels - s] - P.lev_ptr[n_levels - s - 1] == 1) {
+            const int c = s + 1, p0 = n - c;
+            bool full = true;
+            for (int p = p0; p < n && full; ++p) {
+                const auto b = P.lu_col.begin() + P.lu_ptr[p], e = P.lu_col.begin() + P.lu_ptr[p + 1];
+                full = (e - std::lower_bound(b, e, p0)) == c;
+            }
+            if (!full) break;
+            s = c;
+        }
+        P.dense_s = s >= kDenseMin ? s : 0;
+        P.dense_l0 = n_levels - P.dense_s;
+    }
+
     // scalar nonzeros of J1 (rows dP_{B\R}, dQ_D; columns theta_{B\R}, Vm_D)
     long long nnz = 0;
     for (int i = 0; i < n_bus; ++i) {

@@ -38,6 +38,9 @@ struct Plan {
     // lanes per gathered row (a power of two <= 32) for each level: forward (L part),
     // backward (U part) and Schur-target gathers
     std::vector<int> lev_gL, lev_gU, lev_gS;
+    // dense tail: the last dense_s levels (from dense_l0 on) hold one row each and the
+    // trailing dense_s x dense_s block of the filled pattern is full (0 = none)
+    int dense_s = 0, dense_l0 = 0;
 
     // block CSR of the filled L+U pattern in position order
     std::vector<int> lu_ptr, lu_col, lu_row, lu_diag, lu_mirror;
@@ -83,5 +86,10 @@ void minimum_degree(const std::vector<std::vector<int>>& adj,
 // The ordering's degree slack: 1 gave 24-30 % fewer elimination levels than exact
 // minimum degree on the 118- to 2000-bus grids for 1-3 % more fill.
 constexpr int kOrderSlack = 1;
+
+// Largest dense tail the factorisation stages in shared memory (16 x 16 blocks: 4 KB in
+// FP32, 8 KB in FP64 per scenario), and the smallest worth it.
+constexpr int kDenseMax = 16;
+constexpr int kDenseMin = 3;
 
 }  // namespace pf

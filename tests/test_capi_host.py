@@ -210,3 +210,29 @@ def test_jacobian_template_is_the_oracle_pattern(pfm, name):
     assert np.array_equal(J.indptr, j1_ptr)
     assert np.array_equal(J.indices, j1_col)
     assert info["plan_bytes"] > 0
+
+
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c4b", "c4c"])
+def test_dense_tail_is_the_largest_full_single_row_tail(pfm, name):
+    """The plan's dense tail (factored densely in shared memory): its levels hold one
+    pivot each, its rows are full from the tail's first position on, it is as long as
+    those two rules and the 16-block cap allow, and shorter than 3 it is not used."""
+    g = configs.raw_grid(name)
+    ip, ix, gg, bb = _ybus(pfm, g)
+    info, pos2bus, lu_ptr, lu_col, lev_ptr = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)
+    n, L, s = info["n_block"], info["n_levels"], info["dense_tail"]
+    sizes = np.diff(lev_ptr)
+
+    def ok(c):
+        if c > L or np.any(sizes[L - c:] != 1):
+            return False
+        p0 = n - c
+        return all(np.count_nonzero(lu_col[lu_ptr[p]:lu_ptr[p + 1]] >= p0) == c
+                   for p in range(p0, n))
+
+    longest = 0
+    while longest < 16 and ok(longest + 1):
+        longest += 1
+    assert s == (longest if longest >= 3 else 0)
+    if s:
+        assert ok(s)
