@@ -516,6 +516,7 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     d.n_levels = P.n_levels;
     d.dense_s = P.dense_s;
     d.dense_l0 = P.dense_l0;
+    d.dense_g = P.dense_g;
     d.y_ptr = I(po.yptr);
     d.y_idx = I(po.yidx);
     d.y_gb = reinterpret_cast<const double2*>(base + po.ygb);

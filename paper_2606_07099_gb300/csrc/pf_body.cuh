@@ -660,15 +660,93 @@ __device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT*
     }
 }
 
-// x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
-// then U x = y by descending levels.
+// The forward sweep over the plan's dense tail (rows p0 = n - s .. n - 1; D: the factored
+// tail left in shared memory by phase_lu): first every tail row's part left of the tail
+// (those x are final: one gather over all tail rows, dense_g lanes per row), then the
+// unit-lower dense substitution, one shared-memory step per tail row.
 template <typename FT, bool W>
-__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x) {
-    for (int l = 0; l < P.n_levels; ++l) {
+__device__ void dense_tail_lower(const DevPlan& P, const FT* fac, const FT* D, FT* x) {
+    const int s = P.dense_s, p0 = P.n - s, G = P.dense_g;
+    if (G == 1) {
+        for (int p = p0 + GTID; p < P.n; p += GSZ) {
+            FT s0 = FT(0), s1 = FT(0);
+            row_gather<FT, false>(P, fac, x, __ldg(P.lu_ptr + p), __ldg(P.lu_diag + p) - (p - p0),
+                                  1, s0, s1);
+            x[2 * p] -= s0;
+            x[2 * p + 1] -= s1;
+        }
+    } else {  // G lanes per row; every lane runs the same rounds (the shuffles need whole warps)
+        const int sub = GTID & (G - 1), nrg = GSZ / G;
+        for (int pb = p0; pb < P.n; pb += nrg) {
+            const int p = pb + GTID / G;
+            const bool act = p < P.n;
+            FT s0 = FT(0), s1 = FT(0);
+            if (act)
+                row_gather<FT, false>(P, fac, x, __ldg(P.lu_ptr + p) + sub,
+                                      __ldg(P.lu_diag + p) - (p - p0), G, s0, s1);
+            for (int o = G >> 1; o; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            if (act && sub == 0) {
+                x[2 * p] -= s0;
+                x[2 * p + 1] -= s1;
+            }
+        }
+    }
+    gsync<W>();
+    for (int k = 0; k < s; ++k) {  // x_i -= L(i, k) x_k for the tail rows i > k
+        const FT x0 = x[2 * (p0 + k)], x1 = x[2 * (p0 + k) + 1];
+        for (int i = k + 1 + GTID; i < s; i += GSZ) {
+            const Blk<FT> m = ldb(D, i * s + k);
+            x[2 * (p0 + i)] -= m.a * x0 + m.b * x1;
+            x[2 * (p0 + i) + 1] -= m.c * x0 + m.d * x1;
+        }
+        gsync<W>();
+    }
+}
+
+// The backward sweep over the dense tail (its U entries all lie inside the tail):
+// x_k <- P_k^-1 x_k (the stored pivot is the inverse; every thread forms it), then
+// x_i -= U(i, k) x_k for the tail rows i < k.  x_k itself is stored after the step's
+// barrier, once every thread has read it; no later tail step reads it.
+template <typename FT, bool W>
+__device__ void dense_tail_upper(const DevPlan& P, const FT* D, FT* x) {
+    const int s = P.dense_s, p0 = P.n - s;
+    for (int k = s - 1; k >= 0; --k) {
+        const Blk<FT> d = ldb(D, k * s + k);
+        const FT y0 = x[2 * (p0 + k)], y1 = x[2 * (p0 + k) + 1];
+        const FT x0 = d.a * y0 + d.b * y1, x1 = d.c * y0 + d.d * y1;
+        for (int i = GTID; i < k; i += GSZ) {
+            const Blk<FT> m = ldb(D, i * s + k);
+            x[2 * (p0 + i)] -= m.a * x0 + m.b * x1;
+            x[2 * (p0 + i) + 1] -= m.c * x0 + m.d * x1;
+        }
+        gsync<W>();
+        if (GTID == 0) {
+            x[2 * (p0 + k)] = x0;
+            x[2 * (p0 + k) + 1] = x1;
+        }
+    }
+    gsync<W>();
+}
+
+// x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
+// then U x = y by descending levels.  With `dense` (the dense tail as phase_lu left it in
+// shared memory) the tail's levels are swept densely there.
+template <typename FT, bool W>
+__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x, const FT* dense = nullptr) {
+    const bool dt = dense != nullptr && P.dense_s > 0;
+    const int nl = dt ? P.dense_l0 : P.n_levels;
+    for (int l = 0; l < nl; ++l) {
         sweep_level<FT, false, false, W>(P, fac, x, l);
         gsync<W>();
     }
-    for (int l = P.n_levels - 1; l >= 0; --l) {
+    if (dt) {
+        dense_tail_lower<FT, W>(P, fac, dense, x);
+        dense_tail_upper<FT, W>(P, dense, x);
+    }
+    for (int l = nl - 1; l >= 0; --l) {
         sweep_level<FT, true, false, W>(P, fac, x, l);
         gsync<W>();
     }
@@ -823,7 +901,9 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         if (it_round >= A.max_iter) { status = 1; break; }
         phase_fill<W, QL>(P, a, fac);
         gsync<W>();
-        if (phase_lu<FT, W>(P, fac, &s_bad, reinterpret_cast<FT*>(smem + K.smem_dense_off))) {
+        // the dense tail, factored by phase_lu, stays in shared memory for this step's sweeps
+        FT* const tail = reinterpret_cast<FT*>(smem + K.smem_dense_off);
+        if (phase_lu<FT, W>(P, fac, &s_bad, tail)) {
             status = 3;
             factored = false;
             break;
@@ -832,7 +912,7 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         // first solve with the FT factor
         for (int k = GTID; k < 2 * P.n; k += GSZ) x[k] = FT(-a.F[k]);
         gsync<W>();
-        phase_solve<FT, W>(P, fac, x);
+        phase_solve<FT, W>(P, fac, x, tail);
         if (mixed) {
             for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] = double(x[k]);
             gsync<W>();
@@ -842,7 +922,7 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
                 // forcing term min(ir_rtol, ||F1||): loose far from the solution, quadratic
                 // near it, so the inexact Newton steps keep the quadratic convergence
                 if (A.ir_rtol > 0.0 && rmax <= fmin(A.ir_rtol, norm) * norm) break;
-                phase_solve<FT, W>(P, fac, x);
+                phase_solve<FT, W>(P, fac, x, tail);
                 for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] += double(x[k]);
                 gsync<W>();
             }

@@ -10,6 +10,7 @@ namespace pf {
 struct DevPlan {
     int n_bus, n, nnzb, n_levels;
     int dense_s, dense_l0;  // dense tail: its size in blocks and first level (0: none)
+    int dense_g;            // lanes per tail row for its part left of the tail
     const int* y_ptr;
     const int* y_idx;
     const double2* y_gb;  // (G, B) of every Ybus entry

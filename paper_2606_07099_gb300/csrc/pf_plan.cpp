@@ -367,6 +367,10 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         }
         P.dense_s = s >= kDenseMin ? s : 0;
         P.dense_l0 = n_levels - P.dense_s;
+        int mT = 0;  // longest part of a tail row left of the tail
+        for (int p = n - P.dense_s; p < n; ++p)
+            mT = std::max(mT, P.lu_diag[p] - (p - (n - P.dense_s)) - P.lu_ptr[p]);
+        P.dense_g = P.dense_s ? lanes(mT, P.dense_s) : 1;
     }
 
     // scalar nonzeros of J1 (rows dP_{B\R}, dQ_D; columns theta_{B\R}, Vm_D)

@@ -41,6 +41,8 @@ struct Plan {
     // dense tail: the last dense_s levels (from dense_l0 on) hold one row each and the
     // trailing dense_s x dense_s block of the filled pattern is full (0 = none)
     int dense_s = 0, dense_l0 = 0;
+    // lanes per tail row for the gather of its part left of the tail (forward sweeps)
+    int dense_g = 1;
 
     // block CSR of the filled L+U pattern in position order
     std::vector<int> lu_ptr, lu_col, lu_row, lu_diag, lu_mirror;
