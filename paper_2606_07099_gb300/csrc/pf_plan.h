@@ -89,9 +89,9 @@ void minimum_degree(const std::vector<std::vector<int>>& adj,
 // minimum degree on the 118- to 2000-bus grids for 1-3 % more fill.
 constexpr int kOrderSlack = 1;
 
-// Largest dense tail the factorisation stages in shared memory (16 x 16 blocks: 4 KB in
-// FP32, 8 KB in FP64 per scenario), and the smallest worth it.
-constexpr int kDenseMax = 16;
+// Largest dense tail the factorisation stages in shared memory (32 x 32 blocks: 16 KB in
+// FP32, 32 KB in FP64 per scenario), and the smallest worth it.
+constexpr int kDenseMax = 32;
 constexpr int kDenseMin = 3;
 
 }  // namespace pf

@@ -216,7 +216,7 @@ def test_jacobian_template_is_the_oracle_pattern(pfm, name):
 def test_dense_tail_is_the_largest_full_single_row_tail(pfm, name):
     """The plan's dense tail (factored densely in shared memory): its levels hold one
     pivot each, its rows are full from the tail's first position on, it is as long as
-    those two rules and the 16-block cap allow, and shorter than 3 it is not used."""
+    those two rules and the 32-block cap allow, and shorter than 3 it is not used."""
     g = configs.raw_grid(name)
     ip, ix, gg, bb = _ybus(pfm, g)
     info, pos2bus, lu_ptr, lu_col, lev_ptr = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)
@@ -231,7 +231,7 @@ def test_dense_tail_is_the_largest_full_single_row_tail(pfm, name):
                    for p in range(p0, n))
 
     longest = 0
-    while longest < 16 and ok(longest + 1):
+    while longest < 32 and ok(longest + 1):
         longest += 1
     assert s == (longest if longest >= 3 else 0)
     if s:
