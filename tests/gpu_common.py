@@ -49,7 +49,8 @@ def regular(o):
     Newton iterates of the two implementations differ only by rounding, which the
     iteration damps inside the quadratic basin and amplifies elsewhere.  A scenario
     is regular if it converges with ||F1|| decreasing monotonically after the first
-    three iterates, or diverges within two Newton steps (or is non-finite from the start).
+    three iterates, or diverges or meets a singular Jacobian within two Newton steps (or
+    is non-finite from the start).
     Elsewhere -- scenarios that wander for many iterations without a solution -- the
     MAXITER / DIVERGED split (and a late convergence) depends on rounding.
     """
@@ -59,7 +60,7 @@ def regular(o):
     if o["status"] == O.CONVERGED:
         tail = h[2:]
         return all(b < a for a, b in zip(tail, tail[1:]))
-    if o["status"] == O.DIVERGED:
+    if o["status"] in (O.DIVERGED, O.SINGULAR):
         return o["iters"] <= 2
     return False
 
@@ -72,6 +73,19 @@ def mismatch_checker(g, sc):
         Psp, Qsp = O.specified_injections(g.bus_type, sc.Pd[s], sc.Qd[s], sc.Pg[s])
         return float(np.max(np.abs(O.F1_of(Y, g.bus_type, Vm, Va, Psp, Qsp))))
     return check
+
+
+def check_every_solution(gpu, g, sc, tol=1e-8):
+    """Every scenario the GPU reports converged is a true solution: the oracle's own
+    ||F1||_inf at the returned (Vm, theta) is within tol (one SpMV per scenario, so this
+    covers the whole batch, not a sample).  Returns the largest such mismatch."""
+    check = mismatch_checker(g, sc)
+    worst = 0.0
+    for s in np.flatnonzero(gpu["status"] == O.CONVERGED):
+        m = check(s, gpu["Vm"][s], gpu["Va"][s])
+        assert m <= 1.01 * tol + 1e-13, (s, m)
+        worst = max(worst, m)
+    return worst
 
 
 def compare(gpu, orc, tol=1e-8, iter_slack=0, max_iter=20, check=None):

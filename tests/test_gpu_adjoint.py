@@ -32,7 +32,7 @@ def cotangents(n, nb, seed):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name,idx", [("c0", range(0, 64, 3)), ("c1", [0, 7, 4095]),
-                                      ("c2", [0, 1023])])
+                                      ("c2", [0, 1023]), ("c3", [0, 85, 170, 255])])
 def test_adjoint_matches_oracle(mods, name, idx, precision):
     torch, pm = mods
     g, sc = workload(name)

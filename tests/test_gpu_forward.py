@@ -8,8 +8,8 @@ import pytest
 import oracle.pf_oracle as O
 from synthgrid import PQ, PV, SLACK, Scenarios, make_grid, make_scenarios, scale_loads
 
-from gpu_common import (compare, ensure_built, mismatch_checker, regular, run_gpu, run_oracle,
-                        to_dev, workload)
+from gpu_common import (check_every_solution, compare, ensure_built, mismatch_checker, regular,
+                        run_gpu, run_oracle, to_dev, workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,9 @@ def test_c0_all_scenarios_match_stored_oracle(PowerFlow, precision, ir):
     orc = {s: {k: (np.asarray(gold[k][s]) if isinstance(gold[k][s], list) else gold[k][s])
                for k in ("Vm", "Va", "Pg", "Qg", "iters", "status", "final_mismatch")}
            for s in range(sc.n)}
-    compare(gpu, orc, iter_slack=0 if precision == "fp64" else 1)
+    worst = compare(gpu, orc, iter_slack=0 if precision == "fp64" else 1,
+                    check=mismatch_checker(g, sc))
+    assert worst["irregular"] == 0
 
 
 @pytest.mark.parametrize("precision,ir,rtol,gate", [("fp64", 0, 0.0, 0.0), ("mixed", 1, 0.0, 0.0),
@@ -45,11 +47,14 @@ def test_c1_full_batch_sampled(PowerFlow, precision, ir, rtol, gate):
     gpu = run_gpu(pf, sc, precision=precision, ir_steps=ir, ir_rtol=rtol, ir_gate=gate)
     rng = np.random.default_rng(0)
     idx = sorted(set([0, sc.n - 1] + rng.choice(sc.n, 46, replace=False).tolist()))
-    compare(gpu, run_oracle(g, sc, idx), iter_slack=0 if precision == "fp64" else 1,
-            check=mismatch_checker(g, sc))
-    # every scenario converged within tol (property checked at full size)
+    worst = compare(gpu, run_oracle(g, sc, idx), iter_slack=0 if precision == "fp64" else 1,
+                    check=mismatch_checker(g, sc))
+    assert worst["irregular"] == 0
+    # every scenario converged within tol, and each returned voltage profile is a solution
+    # by the oracle's own mismatch (the whole batch, not a sample)
     assert np.all(gpu["status"] == 0)
     assert np.all(gpu["final_mismatch"] <= 1e-8)
+    check_every_solution(gpu, g, sc)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -57,9 +62,11 @@ def test_c2_sampled(PowerFlow, precision):
     g, sc = workload("c2")
     pf = PowerFlow.from_grid(g)
     gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
-    compare(gpu, run_oracle(g, sc, [0, 511, 1023]), iter_slack=0 if precision == "fp64" else 1,
-            check=mismatch_checker(g, sc))
+    worst = compare(gpu, run_oracle(g, sc, [0, 255, 511, 767, 1023]),
+                    iter_slack=0 if precision == "fp64" else 1, check=mismatch_checker(g, sc))
+    assert worst["irregular"] == 0
     assert np.all(gpu["status"] == 0)
+    check_every_solution(gpu, g, sc)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -67,8 +74,11 @@ def test_c3_sampled(PowerFlow, precision):
     g, sc = workload("c3")
     pf = PowerFlow.from_grid(g)
     gpu = run_gpu(pf, sc, precision=precision, ir_steps=1)
-    compare(gpu, run_oracle(g, sc, [0, 255]), iter_slack=0 if precision == "fp64" else 1)
+    worst = compare(gpu, run_oracle(g, sc, [0, 85, 170, 255]),
+                    iter_slack=0 if precision == "fp64" else 1, check=mismatch_checker(g, sc))
+    assert worst["irregular"] == 0
     assert np.all(gpu["status"] == 0)
+    check_every_solution(gpu, g, sc)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -78,9 +88,12 @@ def test_c5_25k_bus_sampled(PowerFlow, precision):
     g, sc = workload("c5")
     pf = PowerFlow.from_grid(g)
     gpu = run_gpu(pf, sc, precision=precision, ir_steps=2, ir_gate=1e-2)
-    compare(gpu, run_oracle(g, sc, [0, 255]), iter_slack=0 if precision == "fp64" else 1)
+    worst = compare(gpu, run_oracle(g, sc, [0, 255]), iter_slack=0 if precision == "fp64" else 1,
+                    check=mismatch_checker(g, sc))
+    assert worst["irregular"] == 0
     assert np.all(gpu["status"] == 0)
     assert np.all(gpu["final_mismatch"] <= 1e-8)
+    check_every_solution(gpu, g, sc)
 
 
 @pytest.mark.parametrize("name,n", [("c4a", 2048), ("c4b", 512), ("c4c", 64)])
@@ -229,6 +242,32 @@ def test_status_edge_cases(PowerFlow):
         one = Scenarios(Pd=sc.Pd[:1], Qd=sc.Qd[:1], Pg=sc.Pg[:1], Vset=sc.Vset[:1])
         out = run_gpu(pf, one, precision=prec)
         assert out["status"][0] == 0
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # the oracle's V/|V| at a zero voltage
+@pytest.mark.parametrize("name", ["c0", "c1"])
+def test_singular_flag_matches_oracle(PowerFlow, name):
+    """Vset = 0 at a PV bus makes the dP row and theta column of J1 exactly zero at the
+    flat start (every entry carries a factor V_k): both sides must report SINGULAR
+    before the first Newton step, in both precisions; the other scenarios are unaffected."""
+    g, sc = workload(name, 12)
+    pv = np.flatnonzero(g.bus_type == PV)
+    bad = Scenarios(Pd=sc.Pd.copy(), Qd=sc.Qd.copy(), Pg=sc.Pg.copy(), Vset=sc.Vset.copy())
+    hit = [1, 4, 5, 11]
+    for j, s in enumerate(hit):
+        bad.Vset[s, pv[(3 * j) % len(pv)]] = 0.0
+    pf = PowerFlow.from_grid(g)
+    orc = run_oracle(g, bad, range(12))
+    for s in range(12):
+        assert orc[s]["status"] == (O.SINGULAR if s in hit else O.CONVERGED), s
+        if s in hit:
+            assert orc[s]["iters"] == 0
+    for prec in ("fp64", "mixed"):
+        gpu = run_gpu(pf, bad, precision=prec, ir_steps=1)
+        assert np.all(gpu["status"][hit] == O.SINGULAR), (prec, gpu["status"])
+        assert np.all(gpu["iters"][hit] == 0)
+        worst = compare(gpu, orc, iter_slack=0 if prec == "fp64" else 1)
+        assert worst["irregular"] == 0
 
 
 def test_infeasible_load_flags_match_oracle(PowerFlow):

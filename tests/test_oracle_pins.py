@@ -279,6 +279,56 @@ def test_status_flags():
     assert r["status"] == O.CONVERGED and r["iters"] == 0
 
 
+# ---------------------------------------------------------------- linear-solve branches
+def _lu_grid():
+    """A grid whose J1 has more unknowns than the dense limit (n1 = 3538)."""
+    return make_grid("lu", 1800, 2500, 60, 180, 7)
+
+
+def test_sparse_lu_branch_matches_dense_solve():
+    """Above DENSE_LIMIT unknowns (the 9241- and 25k-bus workloads and their adjoints) the
+    oracle solves with SuperLU.  That branch must give the dense LAPACK solution, for J1
+    and for J1^T (the adjoint's system): a transposed operand or a lost permutation in
+    the sparse branch fails here."""
+    import scipy.sparse as sp
+    g = _lu_grid()
+    Y = ybus_of(g)
+    rng = np.random.default_rng(0)
+    Vm = 1.0 + rng.uniform(-0.05, 0.05, g.n_bus)
+    Va = rng.uniform(-0.2, 0.2, g.n_bus)
+    J1 = O.J1_of(Y, g.bus_type, Vm, Va)
+    assert J1.shape[0] > O.DENSE_LIMIT
+    b = rng.normal(size=J1.shape[0])
+    for M in (J1, sp.csr_matrix(J1.T)):
+        x = O._solve(M, b)
+        xd = np.linalg.solve(M.toarray(), b)
+        assert np.max(np.abs(x - xd)) <= 1e-12 * np.max(np.abs(xd))
+    # and the two systems differ (the check above would not see a swapped operand
+    # if J1 were symmetric)
+    assert np.max(np.abs(O._solve(J1, b) - O._solve(sp.csr_matrix(J1.T), b))) > 1e-3
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # V/|V| at the zero-voltage bus
+@pytest.mark.parametrize("big", [False, True])
+def test_zero_voltage_pv_bus_is_singular(big):
+    """A PV bus with Vset = 0 gives J1 an all-zero dP row (and theta column) at the flat
+    start, since every entry of both carries a factor V_k.  Both linear-solve branches
+    (dense LAPACK and SuperLU) report the exact singularity, and nr_solve returns SINGULAR
+    before its first step."""
+    g = _lu_grid() if big else small_grid(14, 3)
+    Y = ybus_of(g)
+    sc = make_scenarios(g, 1, 1.0, 1.0, 0)
+    k = int(np.flatnonzero(g.bus_type == PV)[0])
+    Vset = sc.Vset[0].copy()
+    Vset[k] = 0.0
+    J1 = O.J1_of(Y, g.bus_type, *O.flat_start(g.bus_type, Vset))
+    assert (J1.shape[0] > O.DENSE_LIMIT) == big
+    row = int(np.flatnonzero(np.flatnonzero(g.bus_type != SLACK) == k)[0])
+    assert np.all(J1.toarray()[row] == 0.0)
+    r = O.nr_solve(Y, g.bus_type, sc.Pd[0], sc.Qd[0], sc.Pg[0], Vset)
+    assert r["status"] == O.SINGULAR and r["iters"] == 0
+
+
 def test_multi_slack_requires_at_least_one():
     with pytest.raises(ValueError):
         O.bus_sets(np.array([PQ, PV]))
