@@ -440,14 +440,17 @@ pf_err pf_adjoint(pf_handle* h, int batch,
  * pf_solve minus the workspace: the per-scenario scratch lives in a static device
  * array of PF_NOALLOC_SCRATCH_BYTES that the library holds on every device it is
  * loaded on until the process exits.  No allocation of any kind happens inside.
- *   - The first call on a device looks up that array's address (once per device);
- *     make that first call before any stream capture that it should join.
+ *   - pf_create looks the array's device address up on the handle's device and
+ *     keeps it on the handle.  Under lazy module loading that lookup may be what
+ *     loads the module holding the array and commits its memory, so it happens in
+ *     pf_create (which allocates anyway), never in pf_solve_noalloc.  A device reset
+ *     ends the handle together with that address.
  *   - All calls share the array: calls whose kernels overlap on the GPU race and
  *     corrupt each other; order them on one stream.  Nothing in it needs clearing.
  *   - keep_factors must be 0 (pf_adjoint needs a caller-owned workspace).
  * Errors: PF_EINVAL when keep_factors is set or when the batch needs more scratch
- * than PF_NOALLOC_SCRATCH_BYTES (pf_workspace_size tells the need), plus every
- * error of pf_solve.
+ * than PF_NOALLOC_SCRATCH_BYTES (pf_workspace_size tells the need); PF_ECUDA when
+ * pf_create could not look the array up; plus every error of pf_solve.
  */
 #define PF_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 pf_err pf_solve_noalloc(pf_handle* h, int batch,

@@ -35,6 +35,8 @@ struct pf_handle {
     pf::SlotLayout last_layout{};
     size_t plan_bytes = 0;  // the device plan buffer
     int last_qlim = 0;      // the last solve ran under reactive limits (pf_adjoint_qlim)
+    void* noalloc_scratch = nullptr;  // device address of pf_solve_noalloc's static scratch
+                                      // array on this handle's device (null: lookup failed)
 };
 
 namespace {
@@ -365,6 +367,7 @@ bool addressable(const void* p, size_t bytes, int device) {
 
 namespace pf {
 int handle_device(const pf_handle* h) { return h->device; }
+void* handle_noalloc_scratch(const pf_handle* h) { return h->noalloc_scratch; }
 }  // namespace pf
 
 namespace {
@@ -507,6 +510,10 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
         return PF_ECUDA;
     }
     h->plan_bytes = buf.size();
+    // pf_solve_noalloc's scratch address on this device, looked up here (a call that may
+    // load the module holding the array), so that the no-allocation entry point itself
+    // never does; a failed lookup only disables that entry point
+    if (pf::noalloc_lookup(&h->noalloc_scratch) != cudaSuccess) h->noalloc_scratch = nullptr;
     auto* base = static_cast<unsigned char*>(h->d_buf);
     auto I = [&](size_t o) { return reinterpret_cast<const int*>(base + o); };
     pf::DevPlan& d = h->dp;

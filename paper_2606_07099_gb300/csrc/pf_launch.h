@@ -25,4 +25,7 @@ cudaError_t solve_bde(const DevPlan& P, int batch, const double* Pd, const doubl
                       const double* Pg, const double* Vset, double tol, int max_iter, double* Vm,
                       double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
                       double* fmis, void* ws, cudaStream_t s);
+// Device address of pf_solve_noalloc's static scratch array on the current device
+// (pf_noalloc.cu; called once per handle by pf_create).
+cudaError_t noalloc_lookup(void** out);
 }  // namespace pf

@@ -12,14 +12,21 @@
 // nothing needs clearing between calls.  Two calls whose kernels overlap on the GPU
 // (different streams, or different threads without ordering) race on the array and
 // corrupt each other's results: order them on one stream.
+//
+// In host code the array's name is only a host-side stand-in, so its device address
+// is looked up with cudaGetSymbolAddress.  pf_create does that once per handle, with
+// the handle's device current, and keeps the address on the handle: under lazy module
+// loading that lookup is what loads this module and commits the array, so it happens
+// in the call that allocates anyway, never inside pf_solve_noalloc.  A device reset
+// ends the handle and, with it, the address.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "pf.h"
+#include "pf_launch.h"
 
 namespace pf {
-int handle_device(const pf_handle* h);  // pf_api.cpp: the device the plan lives on
+int handle_device(const pf_handle* h);             // pf_api.cpp: the plan's device
+void* handle_noalloc_scratch(const pf_handle* h);  // pf_api.cpp: the address kept by pf_create
 }
 
 namespace {
@@ -30,24 +37,22 @@ namespace {
 constexpr size_t kScratchBytes = PF_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once per device).
-pf_err scratch_address(int device, void** out) {
-    if (device < 0 || device >= kMaxDevices) return PF_EINVAL;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PF_ECUDA;
-        g_scratch_addr[device] = p;
-    }
-    *out = g_scratch_addr[device];
-    return PF_OK;
-}
-
 }  // namespace
+
+namespace pf {
+cudaError_t noalloc_lookup(void** out) {
+    *out = nullptr;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // not sticky: keep it from surfacing at a later launch check
+        return e;
+    }
+    if (!p) return cudaErrorInvalidSymbol;
+    *out = p;
+    return cudaSuccess;
+}
+}  // namespace pf
 
 extern "C" {
 
@@ -61,16 +66,8 @@ pf_err pf_solve_noalloc(pf_handle* h, int batch, const double* Pd, const double*
     pf_err e = pf_workspace_size(h, batch, opts, &need);
     if (e != PF_OK) return e;
     if (need > kScratchBytes) return PF_EINVAL;  // beyond the static maximum
-    // pf_solve launches on the device the plan lives on: look the array up there, with
-    // that device current (the first call on a device does this one-time lookup)
-    const int dev = pf::handle_device(h);
-    int prev = -1;
-    if (cudaGetDevice(&prev) != cudaSuccess) return PF_ECUDA;
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return PF_ECUDA;
-    void* scratch = nullptr;
-    e = scratch_address(dev, &scratch);
-    if (prev != dev) cudaSetDevice(prev);
-    if (e != PF_OK) return e;
+    void* scratch = pf::handle_noalloc_scratch(h);
+    if (!scratch) return PF_ECUDA;  // pf_create could not look the array up on this device
     return pf_solve(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
                     iters, status, final_mismatch, scratch, kScratchBytes, stream);
 }
