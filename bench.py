@@ -37,10 +37,12 @@ METRIC = "PF solves/s at <=1e-8 pu mismatch (mixed precision form)"
 
 UNIT = "solves/s"
 L2_FLUSH_BYTES = 256 << 20
-# Peaks for the roofline.  HBM: measured copy bandwidth of this GPU family.
-# ALU: FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 = 1.25 TFLOP/s nominal.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# Peaks for the roofline.  HBM: the measured copy bandwidth of this GPU family
+# (MEASURED_PEAKS.json).  ALU: FP64 and FP32 FMA throughput measured by this run on its
+# own GPU (pf_measure_fma_peak, inside the clock-sampled region); the nominal figures
+# (unit counts x 2.07 GHz) are reported beside them.
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -90,6 +92,50 @@ def _oracle_chunk(args):
     return conv
 
 
+def _oracle_results(args):
+    """The oracle's full results on the listed scenarios of a workload (for the parity
+    block of the bench line)."""
+    name, idx = args
+    sys.path.insert(0, ROOT)
+    import oracle.pf_oracle as O
+    from synthgrid import configs
+    g = configs.grid(name)
+    sc = configs.scenarios(name, max(idx) + 1, g)
+    Y = O.build_ybus(g.n_bus, g.f, g.t, g.r, g.x, g.b, g.tap)
+    out = {k: [] for k in ("Vm", "Va", "Pg", "Qg", "iters", "status")}
+    for s in idx:
+        r = O.nr_solve(Y, g.bus_type, sc.Pd[s], sc.Qd[s], sc.Pg[s], sc.Vset[s], 1e-8, 20)
+        for k in out:
+            out[k].append(r[k])
+    return {k: np.asarray(v) for k, v in out.items()}
+
+
+def sig(x, d=3):
+    """x rounded to d significant digits (the bench line keeps its tail short)."""
+    if x is None or not np.isfinite(x) or x == 0:
+        return x
+    return float(f"{x:.{d}g}")
+
+
+def parity_stats(gpu: dict, orc: dict) -> dict:
+    """Per-result error of a GPU form against the FP64 oracle on the same scenarios:
+    n scenarios, flags equal, both converged, the iteration-count difference (GPU -
+    oracle) as a histogram, and the largest |dVm| (dV, pu), |dtheta| (dth, rad) and
+    max(|dPg|, |dQg|) (dPQ, pu) over the scenarios both sides solved."""
+    st_g, st_o = np.asarray(gpu["status"]), np.asarray(orc["status"])
+    both = (st_g == 0) & (st_o == 0)
+    d_it = (np.asarray(gpu["iters"]) - np.asarray(orc["iters"]))[both]
+    hist = {str(int(k)): int((d_it == k).sum()) for k in np.unique(d_it)}
+
+    def mx(*keys):
+        if not both.any():
+            return None
+        return sig(max(float(np.max(np.abs(np.asarray(gpu[k])[both] - np.asarray(orc[k])[both])))
+                       for k in keys), 2)
+    return {"n": int(st_g.shape[0]), "flags": int((st_g == st_o).sum()), "conv": int(both.sum()),
+            "it": hist, "dV": mx("Vm"), "dth": mx("Va"), "dPQ": mx("Pg", "Qg")}
+
+
 class OraclePool:
     """A spawn-started process pool (one BLAS thread per worker) running the oracle."""
 
@@ -110,19 +156,17 @@ class OraclePool:
         dt = time.perf_counter() - t0
         return conv / dt, dt, conv
 
+    def results(self, name: str, idx):
+        """The oracle's results on the scenarios idx of a workload, in idx order."""
+        idx = [int(i) for i in idx]
+        parts = [p.tolist() for p in np.array_split(np.asarray(idx), min(self.procs, len(idx)))
+                 if len(p)]
+        outs = self.pool.map(_oracle_results, [(name, p) for p in parts])
+        return {k: np.concatenate([o[k] for o in outs]) for k in outs[0]}
+
     def close(self):
         self.pool.close()
         self.pool.join()
-
-
-def oracle_rate(n_sample: int):
-    """Converged solves/s of the CPU oracle on the first n_sample scenarios, all cores."""
-    pool = OraclePool(n_sample)
-    try:
-        r, dt, conv = pool.rate(n_sample)
-    finally:
-        pool.close()
-    return r, pool.procs, dt, conv
 
 
 def cpu_model():
@@ -335,7 +379,7 @@ def gpu_leg(args, rank, world):
         sc2 = configs.scenarios("c2", g=g2)
         pf2 = PowerFlow.from_grid(g2)
         in2 = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (sc2.Pd, sc2.Qd, sc2.Pg, sc2.Vset)]
-        pf2.workspace(sc2.n, pf2.make_opts("mixed", keep_factors=True, placement=3))
+        pf2.workspace(sc2.n, pf2.make_opts("fp64", keep_factors=True, placement=3))
         if args.autotune:
             tuned["layer_c2"] = pf2.autotune(*in2, keep_factors=True, **opts)
         res2 = pf2.solve(*in2, keep_factors=True, **opts)
@@ -352,37 +396,33 @@ def gpu_leg(args, rank, world):
                              for a in (sc4.Pd, sc4.Qd, sc4.Pg, sc4.Vset)]))
             slacks4.append(torch.as_tensor(g4.bus_type == 2, device=dev))
         n4 = sum(it[1].shape[0] for it in items4)
-        # launch shape of the single launch: fastest of a few thread counts (setup, not timed)
-        # launch shape of the single launch: threads per CTA x per-network forms (auto) or
-        # every network from the global workspace (3); fastest of 3 timed runs (setup)
-        best4 = None
-        for th in (128, 256, 512):
-            for pl in (0, 3):
-                solve_multi(items4, group_threads=th, placement=pl, **opts)
-                torch.cuda.synchronize(dev)
-                ts4 = []
-                for _ in range(3):
-                    t0 = torch.cuda.Event(enable_timing=True)
-                    t1 = torch.cuda.Event(enable_timing=True)
-                    t0.record(stream)
-                    solve_multi(items4, group_threads=th, placement=pl, **opts)
-                    t1.record(stream)
-                    torch.cuda.synchronize(dev)
-                    ts4.append(t0.elapsed_time(t1))
-                if best4 is None or min(ts4) < best4[2]:
-                    best4 = (th, pl, min(ts4))
-        tuned["multi_c4"] = {"group_threads": best4[0], "placement": best4[1], "ms": best4[2]}
-        res4 = [None]
+        # launch shape of the single launch: pf_autotune_multi (threads per CTA x per-network
+        # forms or all-global placement), on these inputs (setup, not timed)
+        from paper_2606_07099_gb300.powerflow import autotune_multi, multi_workspace_bytes
+        tuned["multi_c4"] = autotune_multi(items4, keep_factors=True, **opts)
+        shape4 = dict(group_threads=tuned["multi_c4"]["group_threads"],
+                      placement=tuned["multi_c4"]["placement"])
+        # preallocated results, gradients and workspace: the captured steps allocate nothing
+        ws4 = torch.empty(multi_workspace_bytes(items4, PowerFlow.make_opts(
+            keep_factors=True, **shape4, **opts))[0], dtype=torch.uint8, device=dev)
+        res4 = solve_multi(items4, keep_factors=True, workspace=ws4, **shape4, **opts)
+        cts4 = []
+        for (pfx, *_), r, sl in zip(items4, res4, slacks4):
+            dVm = 2 * torch.relu(r.Vm - 1.06) - 2 * torch.relu(0.94 - r.Vm)
+            cts4.append((dVm, torch.zeros_like(r.Vm), 2 * r.Pg * sl))
+        grads4 = [pfx.adjoint(*ct, None) for (pfx, *_), ct in zip(items4, cts4)]
 
-        def multi_fwd():
-            res4[0] = solve_multi(items4, group_threads=best4[0], placement=best4[1], **opts)
+        def multi_fwd_step():
+            solve_multi(items4, workspace=ws4, out=res4, **shape4, **opts)
 
-        def multi_fwd_bwd():
-            rs = solve_multi(items4, group_threads=best4[0], placement=best4[1], keep_factors=True,
-                             **opts)
-            for (pfx, *_), r, sl in zip(items4, rs, slacks4):
-                dVm = 2 * torch.relu(r.Vm - 1.06) - 2 * torch.relu(0.94 - r.Vm)
-                pfx.adjoint(dVm, torch.zeros_like(r.Vm), 2 * r.Pg * sl, None)
+        def multi_fwd_bwd_step():
+            rs = solve_multi(items4, keep_factors=True, workspace=ws4, out=res4, **shape4, **opts)
+            for (pfx, *_), r, sl, (dVm, dVa, dPg), gr in zip(items4, rs, slacks4, cts4, grads4):
+                torch.sub(2 * torch.relu(r.Vm - 1.06), 2 * torch.relu(0.94 - r.Vm), out=dVm)
+                torch.mul(2 * r.Pg, sl, out=dPg)
+                pfx.adjoint(dVm, dVa, dPg, None, out=gr)
+        multi_fwd = graphed(multi_fwd_step)
+        multi_fwd_bwd = graphed(multi_fwd_bwd_step)
     large = {}  # the grids whose factors stream through memory: 9241 and 25,000 buses
     for lname in ("c3", "c5"):
         if lname not in secs:
@@ -391,7 +431,9 @@ def gpu_leg(args, rank, world):
         scl = configs.scenarios(lname, g=gl)
         pfl = PowerFlow.from_grid(gl)
         inl = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (scl.Pd, scl.Qd, scl.Pg, scl.Vset)]
-        pfl.workspace(scl.n, pfl.make_opts("mixed", placement=3))
+        # sized for the FP64 form too (the parity block solves it once, after the timing;
+        # captured graphs keep this buffer's address)
+        pfl.workspace(scl.n, pfl.make_opts("fp64", placement=3))
         if args.autotune:
             tuned[lname] = pfl.autotune(*inl, **opts)
         resl = pfl.solve(*inl, **opts)
@@ -586,6 +628,10 @@ def gpu_leg(args, rank, world):
             for tname, gt, pft, ldt, batches, lim in train_sets:
                 train_out[tname] = [train_run(gt, pft, ldt, B, lim, ksteps, max(3, args.warmup), gr)
                                     for B in batches for gr in (True, False)]
+        # the ALU roofline's denominators, measured on this GPU at these clocks (best of 3)
+        from paper_2606_07099_gb300 import _lib as pflib
+        peak64 = max(pflib.measure_fma_peak(True, 1 << 14, stream.cuda_stream) for _ in range(3))
+        peak32 = max(pflib.measure_fma_peak(False, 1 << 19, stream.cuda_stream) for _ in range(3))
     clocks = clk.summary()
     torch.cuda.synchronize(dev)
     st = res.status.cpu().numpy()
@@ -600,10 +646,11 @@ def gpu_leg(args, rank, world):
     K = args.steps
     extra = {}
     if "multi_c4" in secs:
-        conv4 = sum(int((r.status == 0).sum().item()) for r in res4[0])
+        conv4 = sum(int((r.status == 0).sum().item()) for r in res4)
         extra["multi_c4"] = {
             "workload": "2048 x 30-bus + 512 x 300-bus + 64 x 2000-bus scenarios, loads x U(0.6, 1.4), "
-                        "one persistent launch", "scenarios": n4, "converged": conv4,
+                        "one persistent launch (pf_solve_multi; fwd+bwd adds the three adjoints), "
+                        "CUDA-graph replay on preallocated buffers", "scenarios": n4, "converged": conv4,
             "solves_per_s": world * conv4 * K / (T_m4 / 1e3), "ms_per_step": T_m4 / K,
             "fwd_bwd_per_s": world * n4 * K / (T_m4b / 1e3), "fwd_bwd_ms_per_step": T_m4b / K}
     for lname, (gl, scl, pfl, resl, _, _) in large.items():
@@ -692,13 +739,35 @@ def gpu_leg(args, rank, world):
                          "(forward, implicit backward, optimiser) replayed from one CUDA graph, "
                          "else eager PyTorch around the libpf calls"),
             "unit": "samples/s", **train_out}
+    # GPU results for the parity block (per-result error against the oracle, computed on
+    # the host after the timing): the headline batch in both forms, and samples of the
+    # other workloads (their FP64 forms solved once here, untimed)
+    def arrays(r, idx=None):
+        sel = slice(None) if idx is None else torch.as_tensor(idx, device=dev)
+        return {k: getattr(r, k)[sel].cpu().numpy()
+                for k in ("Vm", "Va", "Pg", "Qg", "iters", "status")}
+    par_in = {}
+    if world == 1:
+        par_in["c1"] = {"idx": list(range(N)), "mixed": arrays(res)}
+        if "fp64" in secs:
+            par_in["c1"]["fp64"] = arrays(res64)
+        samples = {"c2": 32, "c3": 16, "c5": 8}
+        for pname, (pfx, inx, rx) in (
+                [("c2", (pf2, in2, res2))] if "layer_c2" in secs else []) + [
+                (k, (v[2], v[5], v[3])) for k, v in large.items()]:
+            idx = np.linspace(0, inx[0].shape[0] - 1, samples[pname]).astype(int).tolist()
+            r64 = pfx.solve(*inx, precision="fp64")
+            par_in[pname] = {"idx": idx, "mixed": arrays(rx, idx), "fp64": arrays(r64, idx)}
+        if "multi_c4" in secs:
+            for (pfx, *inx), rx, name4 in zip(items4, res4, ("c4a", "c4b", "c4c")):
+                idx = np.linspace(0, inx[0].shape[0] - 1, 16).astype(int).tolist()
+                par_in[name4] = {"idx": idx, "mixed": arrays(rx, idx)}
+        torch.cuda.synchronize(dev)
+
     T_job, conv_job = over_ranks(world, dev, sum(t_mixed), conv)
     value = conv_job * K / (T_job / 1e3)
     ms_launch = statistics.mean(t_mixed)
     f64, f32, hbm_bytes = alg_counts(info, nb, its, args.ir_steps, "mixed")
-    # ALU roofline: the kernel needs at least max(F64/peak64, F32/peak32) seconds
-    t_alu = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
-    achieved_eq = (t_alu * FP64_PEAK_TFLOPS * 1e12) / (ms_launch / 1e3) / 1e12
     hbm_peak_gbs, hbm_src = hbm_peak()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -725,21 +794,51 @@ def gpu_leg(args, rank, world):
                 "api": "pf_solve_host: the solve kernel reads the inputs from and writes Vm, Va "
                        "and status to page-locked host memory in place"},
         "gpu_launches": K,
-        "roofline": {"bound": "alu", "achieved": achieved_eq, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_eq / FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": f64 / (ms_launch / 1e3) / 1e12, "peak": peak64,
+                     "unit": "TFLOP/s", "frac": f64 / (ms_launch / 1e3) / 1e12 / peak64,
                      "traffic": profiled_traffic() if args.workload == WORKLOAD else None,
                      "kernel": "nr_solve_kernel<float>",
-                     "note": ("FP64-equivalent rate: F64 + F32*(peak64/peak32) flops per launch over "
-                              "the launch time; peaks derived from unit counts (FP32 "
-                              f"{FP32_PEAK_TFLOPS:.1f}, FP64 {FP64_PEAK_TFLOPS} TFLOP/s nominal)"),
-                     "flops_f64": f64, "flops_f32": f32},
+                     "note": ("FP64 pipe: achieved = algorithmic FP64 flops per launch / mean "
+                              "launch time; peak = FP64 FMA rate measured in this run "
+                              "(pf_measure_fma_peak, of measured); the FP32 work's share of its "
+                              "own measured peak is f32_frac"),
+                     "flops_f64": f64, "flops_f32": f32,
+                     "f32_frac": f32 / (ms_launch / 1e3) / 1e12 / peak32,
+                     "peak_fp32": peak32,
+                     "nominal": {"fp64": FP64_NOMINAL_TFLOPS, "fp32": FP32_NOMINAL_TFLOPS}},
         "hbm": {"achieved_gbs": hbm_bytes / (ms_launch / 1e3) / 1e9, "peak_gbs": hbm_peak_gbs,
                 "peak_source": hbm_src, "frac": hbm_bytes / (ms_launch / 1e3) / 1e9 / hbm_peak_gbs,
                 "bytes_per_launch": hbm_bytes},
         "clocks": clocks,
         **extra,
     }
-    return line
+    # the compact summary the tail of the line carries (3 significant digits)
+    summ = {"mixed_ms": sig(T_mixed / K)}
+    if "fp64" in secs:
+        summ.update(fp64_ms=sig(T_fp64 / K), mixed_speedup=sig(T_fp64 / T_mixed))
+    if "fwdbwd" in secs:
+        summ["fwd_bwd_per_s"] = sig(line["fwd_bwd"]["value"])
+    if "layer_c2" in secs:
+        summ["c2_fwd_bwd_per_s"] = sig(line["fwd_bwd_c2"]["value"])
+    for key in ("multi_c4", "c3", "c5", "qlim"):
+        if key in extra:
+            e = extra[key]
+            summ[key] = {k: sig(e[k]) for k in ("ms_per_step", "solves_per_s", "fwd_bwd_per_s",
+                                                 "fwd_bwd_ms_per_step", "hbm_frac") if k in e}
+    line["results"] = summ
+    return line, par_in
+
+
+# keys printed last: the driver's record keeps only the tail of the line, so the
+# compact results, the parity block, the roofline and the baselines go there
+TAIL_KEYS = ("results", "parity", "roofline", "e2e", "gpu_launches", "clocks", "cpu_baseline")
+
+
+def ordered(line: dict) -> dict:
+    """The bench line with the bulky sections first and the compact summary last."""
+    head = {k: v for k, v in line.items() if k not in TAIL_KEYS}
+    head.update({k: line[k] for k in TAIL_KEYS if k in line})
+    return head
 
 
 def main():
@@ -794,14 +893,45 @@ def main():
         import torch
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    line = gpu_leg(args, rank, world)
+    line, par_in = gpu_leg(args, rank, world)
     if rank == 0:
         if args.cpu_sample > 0:
-            r, procs, dt, conv = oracle_rate(args.cpu_sample)
-            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
-                                    "sample": f"first {args.cpu_sample} of the 4096 scenarios "
-                                              f"({dt:.1f} s wall)", "cpu": cpu_model()}
-        print(json.dumps(line), flush=True)
+            # the oracle on the host cores: the first cpu_sample scenarios of the headline
+            # batch (timed: cpu_baseline), whose results also give the per-result error of
+            # both GPU forms; then samples of the other workloads for the same comparison
+            n_c = min(args.cpu_sample, line["config"]["batch_per_gpu"])
+            pool = OraclePool(n_c)
+            try:
+                t0 = time.perf_counter()
+                orc = pool.results(args.workload, range(n_c))
+                dt = time.perf_counter() - t0
+                conv = int((orc["status"] == 0).sum())
+                parity = {}
+                for pname, d in par_in.items():
+                    o = orc if pname == args.workload else pool.results(pname, d["idx"])
+                    n_p = len(o["status"])
+                    parity[pname] = {form: parity_stats({k: v[:n_p] for k, v in d[form].items()}, o)
+                                     for form in ("mixed", "fp64") if form in d}
+            finally:
+                pool.close()
+            one = mp.get_context("spawn").Pool(1)
+            try:  # one core: the same oracle on a smaller sample
+                n1 = min(256, n_c)
+                one.map(_oracle_chunk, [(args.workload, 0, 1)])
+                t1 = time.perf_counter()
+                conv1 = one.map(_oracle_chunk, [(args.workload, 0, n1)])[0]
+                dt1 = time.perf_counter() - t1
+            finally:
+                one.close()
+                one.join()
+            if par_in:
+                line["parity"] = parity
+            line["cpu_baseline"] = {"value": conv / dt, "unit": UNIT, "cores": pool.procs,
+                                    "kind": "oracle", "single_core_value": conv1 / dt1,
+                                    "sample": f"first {n_c} of the 4096 scenarios ({dt:.1f} s "
+                                              f"wall); single core: first {n1}",
+                                    "cpu": cpu_model()}
+        print(json.dumps(ordered(line)), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

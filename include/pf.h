@@ -411,6 +411,23 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
                       void* stream);
 
 /*
+ * pf_autotune_multi -- picks the launch shape of pf_solve_multi for these jobs by timing
+ * it on their inputs (device, as pf_solve_multi) for every candidate: 128, 256 and 512
+ * threads per CTA, each with PF_PLACE_AUTO (per-network forms) and PF_PLACE_GLOBAL
+ * (every network from the global workspace); shapes whose shared memory does not fit
+ * are skipped.  Each candidate runs once to warm up and three times timed (CUDA events
+ * on `stream`); *out (host) receives the fastest: group_threads, placement,
+ * instances_per_cta = 1 and its best time in ms.  Pass those two fields in the opts of
+ * later pf_solve_multi calls.  The workspace must hold pf_multi_workspace_size of every
+ * candidate shape (the largest of the six).  Not the hot path: it waits for the
+ * device after every trial; the trial solves overwrite the jobs' outputs and leave no
+ * adjoint state.  Errors: PF_EINVAL, PF_ENOTSUP (no candidate fits), PF_ECUDA.
+ */
+pf_err pf_autotune_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
+                         const pf_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                         void* stream, pf_tune_result* out);
+
+/*
  * pf_adjoint -- implicit-differentiation backward pass of Sec. II-B.2 at the
  * solution returned by the preceding pf_solve on this handle (same batch, same
  * workspace, keep_factors set).  Cotangents (device, [batch][n_bus]; dPg and dQg
@@ -458,6 +475,17 @@ pf_err pf_solve_noalloc(pf_handle* h, int batch,
                         double tol, int max_iter, const pf_solve_opts* opts,
                         double* Vm, double* Va, double* Pg_out, double* Qg_out,
                         int* iters, int* status, double* final_mismatch, void* stream);
+
+/*
+ * pf_measure_fma_peak -- measured fused multiply-add throughput of the current device
+ * (not part of the paper's method: the denominator of the ALU roofline that the solve
+ * kernels are reported against, taken on the same GPU and at the same clocks).
+ * fp64 != 0 measures FP64 FMA, else FP32 FMA: 8 CTAs of 256 threads per SM, each thread
+ * running 8 independent FMA chains of `iters` steps (>= 16), timed with CUDA events on
+ * `stream` after one shorter warm-up launch.  Writes TFLOP/s (2 flop per FMA) to *tflops
+ * (host).  Synchronises on the stream.  Errors: PF_EINVAL, PF_ECUDA.
+ */
+pf_err pf_measure_fma_peak(int fp64, int iters, double* tflops, void* stream);
 
 /* pf_destroy -- frees the handle's host and device memory (waits for the device). */
 void pf_destroy(pf_handle* h);

@@ -74,6 +74,8 @@ SIGNATURES = {
     "pf_multi_workspace_size": (_i, [_i, C.POINTER(Job), C.POINTER(SolveOpts), C.POINTER(_sz),
                                      C.POINTER(_sz)]),
     "pf_solve_multi": (_i, [_i, C.POINTER(Job), _d, _i, C.POINTER(SolveOpts), _p, _sz, _p]),
+    "pf_autotune_multi": (_i, [_i, C.POINTER(Job), _d, _i, C.POINTER(SolveOpts), _p, _sz, _p,
+                               C.POINTER(TuneResult)]),
     "pf_qlim_workspace_size": (_i, [_p, _i, C.POINTER(SolveOpts), C.POINTER(_sz)]),
     "pf_solve_qlim": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _d, _i, _i, C.POINTER(SolveOpts),
                            _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
@@ -81,6 +83,7 @@ SIGNATURES = {
                              _p]),
     "pf_bde_workspace_size": (_i, [_p, _i, C.POINTER(_sz)]),
     "pf_solve_bde": (_i, [_p, _i, _p, _p, _p, _p, _d, _i, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "pf_measure_fma_peak": (_i, [_i, _i, C.POINTER(_d), _p]),
     "pf_destroy": (None, [_p]),
     "pf_error_string": (C.c_char_p, [_i]),
 }
@@ -121,3 +124,11 @@ def error_string(code: int) -> str:
 def check(code: int, where: str) -> None:
     if code != PF_OK:
         raise PFError(code, where)
+
+
+def measure_fma_peak(fp64: bool, iters: int = 1 << 16, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (pf_measure_fma_peak)."""
+    out = C.c_double(0.0)
+    check(load().pf_measure_fma_peak(1 if fp64 else 0, int(iters), C.byref(out), stream),
+          "pf_measure_fma_peak")
+    return out.value

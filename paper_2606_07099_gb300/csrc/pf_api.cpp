@@ -971,6 +971,63 @@ pf_err pf_solve_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
     return PF_OK;
 }
 
+pf_err pf_autotune_multi(int n_jobs, const pf_job* jobs, double tol, int max_iter,
+                         const pf_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                         void* stream, pf_tune_result* out) {
+    if (!multi_ok(n_jobs, jobs, opts) || !workspace || !out) return PF_EINVAL;
+    // the workspace must hold every candidate's layout
+    for (int th : {128, 256, 512}) {
+        for (int pl : {PF_PLACE_AUTO, PF_PLACE_GLOBAL}) {
+            pf_solve_opts o = *opts;
+            o.placement = pl;
+            o.group_threads = th;
+            if (workspace_bytes < multi_layout_offsets(n_jobs, jobs, &o, nullptr)) return PF_EINVAL;
+        }
+    }
+    DeviceGuard guard(jobs[0].h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return PF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return PF_ECUDA;
+    }
+    pf_tune_result best{0, 0, 0, 0.f};
+    pf_err err = PF_OK;
+    for (int th : {128, 256, 512}) {
+        for (int pl : {PF_PLACE_AUTO, PF_PLACE_GLOBAL}) {
+            pf_solve_opts o = *opts;
+            o.group_threads = th;
+            o.placement = pl;
+            o.instances_per_cta = 0;
+            float ms_best = 0.f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {  // rep 0 warms up
+                cudaEventRecord(e0, s);
+                const pf_err r = pf_solve_multi(n_jobs, jobs, tol, max_iter, &o, workspace,
+                                                workspace_bytes, stream);
+                cudaEventRecord(e1, s);
+                if (r == PF_ENOTSUP) { ok = false; break; }  // does not fit: not a candidate
+                if (r != PF_OK) { err = r; ok = false; break; }
+                if (cudaEventSynchronize(e1) != cudaSuccess) { err = PF_ECUDA; ok = false; break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && (ms_best == 0.f || ms < ms_best)) ms_best = ms;
+            }
+            if (err != PF_OK) break;
+            if (ok && (best.group_threads == 0 || ms_best < best.ms)) best = {th, pl, 1, ms_best};
+        }
+        if (err != PF_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int j = 0; j < n_jobs; ++j) jobs[j].h->last_batch = -1;  // trial solves: no adjoint state
+    if (err != PF_OK) return err;
+    if (best.group_threads == 0) return PF_ENOTSUP;
+    *out = best;
+    return PF_OK;
+}
+
 void pf_destroy(pf_handle* h) {
     if (!h) return;
     if (h->d_buf) {

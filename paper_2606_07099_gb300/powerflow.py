@@ -400,8 +400,9 @@ class PowerFlow:
         return {"group_threads": res.group_threads, "placement": res.placement,
                 "instances_per_cta": res.instances_per_cta, "ms": res.ms}
 
-    def adjoint(self, dVm, dVa, dPg=None, dQg=None) -> Gradients:
-        """Implicit-differentiation backward pass (pf_adjoint) of the last solve."""
+    def adjoint(self, dVm, dVa, dPg=None, dQg=None, out: Gradients | None = None) -> Gradients:
+        """Implicit-differentiation backward pass (pf_adjoint) of the last solve; ``out``
+        (optional) receives the gradients in place."""
         if self._last is None or not self._last[2] or len(self._last) != 3:
             raise RuntimeError("adjoint needs a preceding solve(..., keep_factors=True)")
         batch, ws, _ = self._last
@@ -409,9 +410,16 @@ class PowerFlow:
             if v is not None:
                 _check_bus_tensor(v, nm, self.n_bus, batch)
         e = dict(dtype=torch.float64, device=dVm.device)
-        g = Gradients(dPd=torch.empty(batch, self.n_bus, **e), dQd=torch.empty(batch, self.n_bus, **e),
-                      dPg=torch.empty(batch, self.n_bus, **e), dVset=torch.empty(batch, self.n_bus, **e),
-                      status=torch.empty(batch, dtype=torch.int32, device=dVm.device))
+        if out is None:
+            g = Gradients(dPd=torch.empty(batch, self.n_bus, **e), dQd=torch.empty(batch, self.n_bus, **e),
+                          dPg=torch.empty(batch, self.n_bus, **e), dVset=torch.empty(batch, self.n_bus, **e),
+                          status=torch.empty(batch, dtype=torch.int32, device=dVm.device))
+        else:
+            g = out
+            for nm in ("dPd", "dQd", "dPg", "dVset"):
+                _check_bus_tensor(getattr(g, nm), nm, self.n_bus, batch)
+            if g.status.numel() < batch or g.status.dtype != torch.int32:
+                raise ValueError("status: int32 tensor of the batch size")
         stream = torch.cuda.current_stream(dVm.device).cuda_stream
         L.check(self._lib.pf_adjoint(
             self._h, batch, dVm.data_ptr(), dVa.data_ptr(),
@@ -532,43 +540,80 @@ class PFLayerQlim(torch.autograd.Function):
                 None, None, None, None, None, None, None)
 
 
-def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,
-                group_threads=0, keep_factors=False, ir_gate=0.0, placement=0):
-    """Several networks in one persistent launch (pf_solve_multi).
-
-    ``items`` is a list of ``(PowerFlow, Pd, Qd, Pg, Vset)``; returns one SolveResult per
-    item.  With ``keep_factors`` each PowerFlow can run ``adjoint`` on its part afterwards.
-    ``placement`` 0 (auto) gives each network its own form (small ones one scenario per
-    warp, large ones the whole CTA with the factor on chip when it fits); PF_PLACE_GLOBAL
-    runs every network with the whole CTA from the global workspace.
-    """
+def _multi_jobs(items, out=None):
+    """pf_job array and the result tensors (out, or freshly allocated) of a multi launch."""
     if not 1 <= len(items) <= L.PF_MAX_JOBS:
         raise ValueError(f"1..{L.PF_MAX_JOBS} networks per launch")
-    lib = L.load()
-    opts = PowerFlow.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors,
-                               placement, 0, ir_gate)
+    if out is not None and len(out) != len(items):
+        raise ValueError("one result per network")
     jobs = (L.Job * len(items))()
     results = []
     for k, (pf, Pd, Qd, Pg, Vset) in enumerate(items):
         batch = Pd.shape[0]
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
             _check_bus_tensor(v, nm, pf.n_bus, batch)
-        e = dict(dtype=torch.float64, device=Pd.device)
-        r = SolveResult(Vm=torch.empty(batch, pf.n_bus, **e), Va=torch.empty(batch, pf.n_bus, **e),
-                        Pg=torch.empty(batch, pf.n_bus, **e), Qg=torch.empty(batch, pf.n_bus, **e),
-                        iters=torch.empty(batch, dtype=torch.int32, device=Pd.device),
-                        status=torch.empty(batch, dtype=torch.int32, device=Pd.device),
-                        final_mismatch=torch.empty(batch, **e))
+        if out is None:
+            e = dict(dtype=torch.float64, device=Pd.device)
+            r = SolveResult(Vm=torch.empty(batch, pf.n_bus, **e), Va=torch.empty(batch, pf.n_bus, **e),
+                            Pg=torch.empty(batch, pf.n_bus, **e), Qg=torch.empty(batch, pf.n_bus, **e),
+                            iters=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                            status=torch.empty(batch, dtype=torch.int32, device=Pd.device),
+                            final_mismatch=torch.empty(batch, **e))
+        else:
+            r = out[k]
+            for nm in ("Vm", "Va", "Pg", "Qg"):
+                _check_bus_tensor(getattr(r, nm), nm, pf.n_bus, batch)
         results.append(r)
         jobs[k] = L.Job(pf._h.value, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(), Vset.data_ptr(),
                         r.Vm.data_ptr(), r.Va.data_ptr(), r.Pg.data_ptr(), r.Qg.data_ptr(),
                         r.iters.data_ptr(), r.status.data_ptr(), r.final_mismatch.data_ptr())
+    return jobs, results
+
+
+def multi_workspace_bytes(items, opts: L.SolveOpts) -> tuple[int, list[int]]:
+    """(bytes, per-network offsets) of the workspace pf_solve_multi needs for these items
+    (only the handles and batch sizes matter)."""
+    if not 1 <= len(items) <= L.PF_MAX_JOBS:
+        raise ValueError(f"1..{L.PF_MAX_JOBS} networks per launch")
+    jobs = (L.Job * len(items))()
+    for k, (pf, Pd, *_rest) in enumerate(items):
+        jobs[k] = L.Job(pf._h.value, Pd.shape[0], 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
+    nbytes = C.c_size_t(0)
+    offs = (C.c_size_t * len(items))()
+    L.check(L.load().pf_multi_workspace_size(len(items), jobs, C.byref(opts), C.byref(nbytes), offs),
+            "pf_multi_workspace_size")
+    return int(nbytes.value), [int(o) for o in offs]
+
+
+def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,
+                group_threads=0, keep_factors=False, ir_gate=0.0, placement=0, out=None,
+                workspace: torch.Tensor | None = None):
+    """Several networks in one persistent launch (pf_solve_multi).
+
+    ``items`` is a list of ``(PowerFlow, Pd, Qd, Pg, Vset)``; returns one SolveResult per
+    item (``out``, if given: preallocated results, one per item, written in place).  With
+    ``keep_factors`` each PowerFlow can run ``adjoint`` on its part afterwards.
+    ``placement`` 0 (auto) gives each network its own form (small ones one scenario per
+    warp, large ones the whole CTA with the factor on chip when it fits); PF_PLACE_GLOBAL
+    runs every network with the whole CTA from the global workspace.  ``workspace`` (a
+    uint8 device tensor of at least ``multi_workspace_bytes``) makes the call free of
+    allocations, so that it can be captured in a CUDA graph and replayed.
+    """
+    lib = L.load()
+    opts = PowerFlow.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors,
+                               placement, 0, ir_gate)
+    jobs, results = _multi_jobs(items, out)
     nbytes = C.c_size_t(0)
     offs = (C.c_size_t * len(items))()
     L.check(lib.pf_multi_workspace_size(len(items), jobs, C.byref(opts), C.byref(nbytes), offs),
             "pf_multi_workspace_size")
     dev = items[0][1].device
-    ws = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    if workspace is None:
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    else:
+        if workspace.dtype != torch.uint8 or workspace.device != dev or workspace.numel() < nbytes.value:
+            raise ValueError(f"workspace: a uint8 tensor of >= {nbytes.value} bytes on {dev}")
+        ws = workspace
     stream = torch.cuda.current_stream(dev).cuda_stream
     L.check(lib.pf_solve_multi(len(items), jobs, float(tol), int(max_iter), C.byref(opts),
                                ws.data_ptr(), ws.numel(), stream), "pf_solve_multi")
@@ -577,3 +622,29 @@ def solve_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_
         pf._solve_id += 1
         pf._last = (Pd.shape[0], ws[offs[k]:ends[k]], bool(keep_factors))
     return results
+
+
+def autotune_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, ir_rtol=1e-3,
+                   keep_factors=False, ir_gate=0.0, workspace: torch.Tensor | None = None) -> dict:
+    """Launch shape of solve_multi for these items (pf_autotune_multi): threads per CTA and
+    placement, timed on the items' inputs.  Returns {group_threads, placement, ms}; pass
+    the first two to solve_multi.  ``workspace`` (optional) must cover every candidate."""
+    lib = L.load()
+    jobs, _ = _multi_jobs(items)
+    dev = items[0][1].device
+    need = max(multi_workspace_bytes(items, PowerFlow.make_opts(
+        precision, ir_steps, ir_rtol, th, keep_factors, pl, 0, ir_gate))[0]
+        for th in (128, 256, 512) for pl in (0, L.PF_PLACE_GLOBAL))
+    ws = torch.empty(need, dtype=torch.uint8, device=dev) if workspace is None else workspace
+    if ws.numel() < need:
+        raise ValueError(f"workspace: >= {need} bytes")
+    opts = PowerFlow.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, 0, 0, ir_gate)
+    res = L.TuneResult()
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    L.check(lib.pf_autotune_multi(len(items), jobs, float(tol), int(max_iter), C.byref(opts),
+                                  ws.data_ptr(), ws.numel(), stream, C.byref(res)),
+            "pf_autotune_multi")
+    for pf, *_ in items:
+        pf._solve_id += 1
+        pf._last = None
+    return {"group_threads": res.group_threads, "placement": res.placement, "ms": res.ms}
