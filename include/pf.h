@@ -106,6 +106,11 @@ typedef struct {
     double ir_gate;    /* PF_MIXED: check and refine a Newton step only once ||F1||_inf <=
                           ir_gate (far from the solution the Newton model error dwarfs the
                           FP32 solve error); 0 = every step */
+    int pack;          /* PF_PLACE_INTERLEAVED: scenarios per pack (8, 16 or 32; 0 = auto or
+                          the autotuned choice); ignored by the other placements */
+    int cluster;       /* PF_PLACE_INTERLEAVED: CTAs per pack, one thread-block cluster
+                          (1..16; 0 = auto or the autotuned choice); group_threads is then the
+                          threads per CTA (group_threads / pack a power of two >= 16) */
 } pf_solve_opts;
 
 typedef enum {
@@ -113,7 +118,16 @@ typedef enum {
     PF_PLACE_ONCHIP = 1,   /* vectors and factor in shared memory (if they fit) */
     PF_PLACE_VECTORS = 2,  /* vectors in shared memory, factor in the global workspace */
     PF_PLACE_GLOBAL = 3,   /* everything in the global workspace (most scenarios per SM) */
-    PF_PLACE_FACTOR = 4    /* factor in shared memory, vectors in the global workspace */
+    PF_PLACE_FACTOR = 4,   /* factor in shared memory, vectors in the global workspace */
+    PF_PLACE_INTERLEAVED = 5  /* scenario-interleaved packs: `pack` scenarios share one
+                          workspace region with every quantity stored [item][scenario], and one
+                          thread-block cluster of `cluster` CTAs runs the pack, each step of
+                          the Newton iteration (and each elimination level) spread over all its
+                          CTAs and separated by cluster barriers.  For networks whose factor
+                          does not fit on chip.  Forward solves only (pf_solve, pf_solve_host,
+                          pf_solve_noalloc): keep_factors and pf_solve_qlim get PF_ENOTSUP
+                          when this placement is asked for explicitly; PF_PLACE_AUTO then uses
+                          another placement */
 } pf_placement;
 
 /* Result of pf_autotune: the fastest launch configuration found for one precision. */
@@ -122,6 +136,8 @@ typedef struct {
     int placement;
     int instances_per_cta;
     float ms;              /* measured time of one pf_solve with that configuration */
+    int pack;              /* PF_PLACE_INTERLEAVED: scenarios per pack and CTAs per cluster */
+    int cluster;
 } pf_tune_result;
 
 /*
@@ -353,7 +369,9 @@ pf_err pf_adjoint_qlim(pf_handle* h, int batch,
  * of the scenario data) for this handle, `batch` and opts->precision by timing
  * pf_solve on the given inputs (device, as pf_solve) for every candidate: 32..1024
  * threads per scenario, or 2, 4 or 8 one-warp scenarios per CTA, times every placement
- * that fits (the best shape depends on the batch: a few scenarios of a large network
+ * that fits; and, on networks of 1000 buses or more without keep_factors, interleaved
+ * packs of 8, 16 or 32 scenarios on clusters of 4, 8 or 16 CTAs of 512 or 1024 threads
+ * whose workspace fits the one given (the best shape depends on the batch: a few scenarios of a large network
  * want the most threads each, thousands of small ones the most scenarios per SM).  The fastest one is kept in
  * the handle and used by later pf_solve calls with group_threads = 0 and placement =
  * PF_PLACE_AUTO at the same precision; *out (nullable) receives it.  The workspace

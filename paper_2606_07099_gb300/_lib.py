@@ -32,15 +32,18 @@ class PlanInfo(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("ir_steps", C.c_int), ("ir_rtol", C.c_double),
                 ("group_threads", C.c_int), ("keep_factors", C.c_int), ("placement", C.c_int),
-                ("instances_per_cta", C.c_int), ("ir_gate", C.c_double)]
+                ("instances_per_cta", C.c_int), ("ir_gate", C.c_double), ("pack", C.c_int),
+                ("cluster", C.c_int)]
 
 
 class TuneResult(C.Structure):
     _fields_ = [("group_threads", C.c_int), ("placement", C.c_int),
-                ("instances_per_cta", C.c_int), ("ms", C.c_float)]
+                ("instances_per_cta", C.c_int), ("ms", C.c_float), ("pack", C.c_int),
+                ("cluster", C.c_int)]
 
 
-PF_PLACE_AUTO, PF_PLACE_ONCHIP, PF_PLACE_VECTORS, PF_PLACE_GLOBAL, PF_PLACE_FACTOR = range(5)
+(PF_PLACE_AUTO, PF_PLACE_ONCHIP, PF_PLACE_VECTORS, PF_PLACE_GLOBAL, PF_PLACE_FACTOR,
+ PF_PLACE_INTERLEAVED) = range(6)
 PF_MAX_JOBS = 8
 
 

@@ -58,6 +58,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         [nvcc, "-c", os.path.join(CSRC, "pf_bde.cu"), "-o", os.path.join(BUILD, "pf_bde.o")] + cu_flags,
         [nvcc, "-c", os.path.join(CSRC, "pf_noalloc.cu"), "-o", os.path.join(BUILD, "pf_noalloc.o")] + cu_flags,
         [nvcc, "-c", os.path.join(CSRC, "pf_peak.cu"), "-o", os.path.join(BUILD, "pf_peak.o")] + cu_flags,
+        [nvcc, "-c", os.path.join(CSRC, "pf_si.cu"), "-o", os.path.join(BUILD, "pf_si.o")] + cu_flags,
         [cxx, "-c", os.path.join(CSRC, "pf_api.cpp"), "-o", os.path.join(BUILD, "pf_api.o")] + cxx_flags,
         [cxx, "-c", os.path.join(CSRC, "pf_plan.cpp"), "-o", os.path.join(BUILD, "pf_plan.o")] + cxx_flags,
     ]
@@ -66,7 +67,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     tmp = LIB + ".tmp"
     _run([nvcc, "-shared"] + ARCH + ["-o", tmp, os.path.join(BUILD, "pf_kernels.o"),
                                      os.path.join(BUILD, "pf_qlim.o"), os.path.join(BUILD, "pf_bde.o"),
-                                     os.path.join(BUILD, "pf_noalloc.o"), os.path.join(BUILD, "pf_peak.o"),
+                                     os.path.join(BUILD, "pf_noalloc.o"), os.path.join(BUILD, "pf_peak.o"), os.path.join(BUILD, "pf_si.o"),
                                      os.path.join(BUILD, "pf_api.o"), os.path.join(BUILD, "pf_plan.o"),
                                      "-cudart", "static", "-lpthread", "-ldl", "-lrt"])
     os.replace(tmp, LIB)

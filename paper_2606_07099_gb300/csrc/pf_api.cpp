@@ -169,11 +169,28 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int place
 
 struct LaunchCfg {
     int threads;
-    int placement;
+    int placement;   // -1: the interleaved placement was asked for where it does not apply
     int ipc;
+    int S, cluster;  // PF_PLACE_INTERLEAVED: scenarios per pack, CTAs per cluster
 };
 
-LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o) {
+// Interleaved packs without tuning data: 16 scenarios per pack from 256 scenarios up (8
+// below), and the largest cluster (at most 16 CTAs) that keeps every pack of the batch
+// resident at once.
+int auto_pack(int batch) { return batch >= 256 ? 16 : 8; }
+// The autotuner times interleaved packs from this network size up.
+constexpr int kSiMinBuses = 1000;
+int auto_cluster(const pf_handle* h, int batch, int S) {
+    const int packs = (batch + S - 1) / S;
+    int c = 16;
+    while (c > 1 && (long long)packs * c > h->num_sms) c >>= 1;
+    return c;
+}
+
+// The launch configuration of a solve.  `si_ok`: the interleaved placement may serve this
+// call (a forward solve without kept factors); where it may not, an automatic choice
+// falls back to the heuristic placement and an explicit request is refused (-1).
+LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o, int batch = 0, bool si_ok = true) {
     const int ft = o->precision == PF_MIXED ? 4 : 8;
     const pf_tune_result& t = h->tuned[o->precision == PF_MIXED ? 1 : 0];
     const bool use_tuned = o->group_threads == 0 && o->instances_per_cta == 0 && t.group_threads;
@@ -185,7 +202,72 @@ LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o) {
     if (c.ipc > 1) c.threads = 32;
     c.placement = o->placement ? o->placement
                                : (t.placement ? t.placement : heuristic_placement(h, ft));
+    c.S = c.cluster = 0;
+    if (c.placement == PF_PLACE_INTERLEAVED) {
+        if (!si_ok) {
+            if (o->placement == PF_PLACE_INTERLEAVED) {
+                c.placement = -1;
+                return c;
+            }
+            c.placement = heuristic_placement(h, ft);
+            c.threads = o->group_threads ? o->group_threads : auto_threads(h->plan.n);
+            c.ipc = 1;
+            return c;
+        }
+        const bool tuned_si = t.placement == PF_PLACE_INTERLEAVED;
+        c.ipc = 1;
+        c.S = o->pack ? o->pack : (tuned_si && t.pack ? t.pack : auto_pack(batch));
+        c.cluster = o->cluster ? o->cluster
+                               : (tuned_si && t.cluster ? t.cluster : auto_cluster(h, batch, c.S));
+        c.threads = o->group_threads ? o->group_threads
+                                     : (tuned_si && t.group_threads ? t.group_threads : 1024);
+    }
     return c;
+}
+
+// Interleaved-pack shape check: threads / S a power of two of at least 16 lane groups (a
+// split sweep row's groups then never straddle two rounds), at most 1024 threads.
+bool si_shape_ok(int S, int cluster, int threads) {
+    if (S != 8 && S != 16 && S != 32) return false;
+    if (cluster < 1 || cluster > 16 || threads < 32 || threads > 1024 || threads % S) return false;
+    const int ns = threads / S;
+    return ns >= 16 && (ns & (ns - 1)) == 0;
+}
+
+// Workspace layout of one interleaved pack.
+pf::SiLayout si_layout(const pf_handle* h, int ft, const LaunchCfg& c) {
+    const pf::Plan& P = h->plan;
+    pf::SiLayout L{};
+    L.S = c.S;
+    L.cluster = c.cluster;
+    L.threads = c.threads;
+    const size_t S = (size_t)c.S, nb = (size_t)P.n_bus, n = (size_t)P.n;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = pf::align_up(o + bytes, 256);
+        return at;
+    };
+    L.off_fac = take((size_t)P.nnzb() * S * 4 * ft);
+    L.off_V = take(nb * S * 16);
+    L.off_I = take(nb * S * 16);
+    L.off_U = take(nb * S * 16);
+    L.off_M = take(nb * S * 16);
+    L.off_SP = take(nb * S * 16);
+    L.off_DV = take(ft == 4 ? nb * S * 16 : 0);
+    L.off_FA = take(ft == 4 ? nb * S * 16 : 0);
+    L.off_FB = take(ft == 4 ? nb * S * 16 : 0);
+    L.off_F = take(n * S * 16);
+    L.off_DZ = take(ft == 4 ? n * S * 16 : 0);
+    L.off_X = take(n * S * 2 * ft);
+    L.off_ctl = take(3 * 32 * sizeof(unsigned long long) + 32 * sizeof(unsigned int));
+    L.pack_bytes = o;
+    L.smem_bytes = (size_t)c.threads * 2 * ft;  // one FT2 partial sum per thread
+    return L;
+}
+
+size_t si_workspace(const pf_handle* h, int ft, const LaunchCfg& c, int batch) {
+    return si_layout(h, ft, c).pack_bytes * (size_t)((batch + c.S - 1) / c.S);
 }
 
 bool opts_ok(const pf_solve_opts* o) {
@@ -195,7 +277,9 @@ bool opts_ok(const pf_solve_opts* o) {
     if (!(o->ir_rtol >= 0.0) || !(o->ir_gate >= 0.0)) return false;
     if (o->group_threads != 0 &&
         (o->group_threads < 32 || o->group_threads > 1024 || o->group_threads % 32)) return false;
-    if (o->placement < PF_PLACE_AUTO || o->placement > PF_PLACE_FACTOR) return false;
+    if (o->placement < PF_PLACE_AUTO || o->placement > PF_PLACE_INTERLEAVED) return false;
+    if (o->pack != 0 && o->pack != 8 && o->pack != 16 && o->pack != 32) return false;
+    if (o->cluster < 0 || o->cluster > 16) return false;
     if (o->instances_per_cta < 0 || o->instances_per_cta > 8) return false;
     if (o->instances_per_cta > 1 && o->group_threads != 0 && o->group_threads != 32) return false;
     return true;
@@ -256,6 +340,49 @@ struct QlimIn {
     int* rounds_out;
 };
 
+// The interleaved-pack solve (PF_PLACE_INTERLEAVED): one thread-block cluster per pack.
+pf_err solve_si(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
+                const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
+                const LaunchCfg& cfg, double* Vm, double* Va, double* Pg_out, double* Qg_out,
+                int* iters, int* status, double* final_mismatch, void* workspace,
+                size_t workspace_bytes, void* stream) {
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    if (!si_shape_ok(cfg.S, cfg.cluster, cfg.threads)) return PF_EINVAL;
+    const pf::SiLayout L = si_layout(h, ft, cfg);
+    if (workspace_bytes < L.pack_bytes * (size_t)((batch + cfg.S - 1) / cfg.S)) return PF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return PF_EINVAL;
+    DeviceGuard guard(h->device);
+    bool fits = false;
+    cudaError_t e = ft == 4 ? pf::si_shape_fits<float>(cfg.S, cfg.cluster, cfg.threads, L.smem_bytes, &fits)
+                            : pf::si_shape_fits<double>(cfg.S, cfg.cluster, cfg.threads, L.smem_bytes, &fits);
+    if (e != cudaSuccess) return PF_ECUDA;
+    if (!fits) return PF_ENOTSUP;  // no cluster of this shape can be resident on this GPU
+    pf::SiArgs A{};
+    A.batch = batch;
+    A.max_iter = max_iter;
+    A.ir_steps = opts->precision == PF_MIXED ? opts->ir_steps : 0;
+    A.tol = tol;
+    A.ir_rtol = opts->ir_rtol;
+    A.ir_gate = opts->ir_gate;
+    A.Pd = Pd;
+    A.Qd = Qd;
+    A.Pg = Pg;
+    A.Vset = Vset;
+    A.Vm = Vm;
+    A.Va = Va;
+    A.Pg_out = Pg_out;
+    A.Qg_out = Qg_out;
+    A.fmis = final_mismatch;
+    A.iters = iters;
+    A.status = status;
+    A.ws = static_cast<char*>(workspace);
+    A.L = L;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = ft == 4 ? pf::launch_solve_si<float>(h->dp, A, s) : pf::launch_solve_si<double>(h->dp, A, s);
+    h->last_batch = -1;  // leaves no state for pf_adjoint
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
 pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, const double* Pg,
                   const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
                   double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
@@ -265,7 +392,11 @@ pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, c
         return PF_EINVAL;
     if (!(tol > 0.0) || max_iter < 0 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    LaunchCfg cfg = resolve(h, opts);
+    LaunchCfg cfg = resolve(h, opts, batch, !opts->keep_factors && !q);
+    if (cfg.placement < 0) return PF_ENOTSUP;
+    if (cfg.placement == PF_PLACE_INTERLEAVED)
+        return solve_si(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, cfg, Vm, Va, Pg_out,
+                        Qg_out, iters, status, final_mismatch, workspace, workspace_bytes, stream);
     if (q) cfg.ipc = 1;  // reactive limits: one CTA per scenario (32 threads if tuned to warps)
     pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, cfg.placement, q != nullptr);
     if (workspace_bytes < L.slot_bytes * (size_t)batch) return PF_EINVAL;
@@ -627,7 +758,14 @@ pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices, const do
 pf_err pf_workspace_size(const pf_handle* h, int batch, const pf_solve_opts* opts, size_t* bytes) {
     if (!h || !bytes || batch < 1 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    const size_t slot = make_layout(h, ft, opts->keep_factors, resolve(h, opts).placement).slot_bytes;
+    const LaunchCfg cfg = resolve(h, opts, batch, !opts->keep_factors);
+    if (cfg.placement < 0) return PF_ENOTSUP;
+    if (cfg.placement == PF_PLACE_INTERLEAVED) {
+        if (!si_shape_ok(cfg.S, cfg.cluster, cfg.threads)) return PF_EINVAL;
+        *bytes = si_workspace(h, ft, cfg, batch);
+        return PF_OK;
+    }
+    const size_t slot = make_layout(h, ft, opts->keep_factors, cfg.placement).slot_bytes;
     *bytes = slot * (size_t)batch;
     return PF_OK;
 }
@@ -655,9 +793,11 @@ pf_err pf_solve_host(pf_handle* h, int batch, const double* Pd, const double* Qd
     if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
         return PF_EINVAL;
     if (!opts_ok(opts)) return PF_EINVAL;
-    const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    const LaunchCfg cfg = resolve(h, opts);
-    const pf::SlotLayout L = make_layout(h, ft, opts->keep_factors, cfg.placement);
+    size_t ws_need = 0;
+    {
+        const pf_err we = pf_workspace_size(h, batch, opts, &ws_need);
+        if (we != PF_OK) return we;
+    }
     const size_t row = sizeof(double) * (size_t)batch * (size_t)h->plan.n_bus;
     DeviceGuard guard(h->device);
     const void* in[] = {Pd, Qd, Pg, Vset, Vm, Va};
@@ -669,7 +809,6 @@ pf_err pf_solve_host(pf_handle* h, int batch, const double* Pd, const double* Qd
         !addressable(status, sizeof(int) * (size_t)batch, h->device) ||
         (final_mismatch && !addressable(final_mismatch, sizeof(double) * (size_t)batch, h->device)))
         return PF_EINVAL;
-    const size_t ws_need = L.slot_bytes * (size_t)batch;
     if (workspace_bytes < ws_need || !addressable(workspace, ws_need, h->device)) return PF_EINVAL;
     return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
                       iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr);
@@ -702,8 +841,9 @@ pf_err pf_qlim_workspace_size(const pf_handle* h, int batch, const pf_solve_opts
                               size_t* bytes) {
     if (!h || !bytes || batch < 1 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    *bytes = make_layout(h, ft, opts->keep_factors, resolve(h, opts).placement, true).slot_bytes *
-             (size_t)batch;
+    const LaunchCfg cfg = resolve(h, opts, batch, false);
+    if (cfg.placement < 0) return PF_ENOTSUP;
+    *bytes = make_layout(h, ft, opts->keep_factors, cfg.placement, true).slot_bytes * (size_t)batch;
     return PF_OK;
 }
 
@@ -794,6 +934,52 @@ pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, 
                 if (rep > 0 && (ms_best == 0.f || ms < ms_best)) ms_best = ms;  // rep 0 warms up
             }
             if (err == PF_OK && (best.group_threads == 0 || ms_best < best.ms)) best = {th, pl, ipc, ms_best};
+        }
+    }
+    // interleaved packs on thread-block clusters (forward solves without kept factors, on
+    // networks large enough for it): scenarios per pack x CTAs per cluster x threads
+    const int ft = opts->precision == PF_MIXED ? 4 : 8;
+    if (err == PF_OK && !opts->keep_factors && h->plan.n_bus >= kSiMinBuses) {
+        for (int S : {8, 16, 32}) {
+            if (S >= 2 * batch && S > 8) continue;  // packs mostly empty
+            for (int cl : {4, 8, 16}) {
+                for (int th : {512, 1024}) {
+                    const LaunchCfg c{th, PF_PLACE_INTERLEAVED, 1, S, cl};
+                    if (!si_shape_ok(S, cl, th) || si_workspace(h, ft, c, batch) > workspace_bytes)
+                        continue;
+                    bool fits = false;
+                    const size_t smem = si_layout(h, ft, c).smem_bytes;
+                    if ((ft == 4 ? pf::si_shape_fits<float>(S, cl, th, smem, &fits)
+                                 : pf::si_shape_fits<double>(S, cl, th, smem, &fits)) != cudaSuccess) {
+                        err = PF_ECUDA;
+                        break;
+                    }
+                    if (!fits) continue;
+                    pf_solve_opts o = *opts;
+                    o.group_threads = th;
+                    o.instances_per_cta = 0;
+                    o.placement = PF_PLACE_INTERLEAVED;
+                    o.pack = S;
+                    o.cluster = cl;
+                    float ms_best = 0.f;
+                    for (int rep = 0; rep < 3 && err == PF_OK; ++rep) {
+                        cudaEventRecord(e0, s);
+                        err = pf_solve(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, &o, dbuf,
+                                       dbuf + nd, nullptr, nullptr, ibuf, ibuf + batch,
+                                       dbuf + 2 * nd, workspace, workspace_bytes, stream);
+                        cudaEventRecord(e1, s);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) err = PF_ECUDA;
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0 && (ms_best == 0.f || ms < ms_best)) ms_best = ms;
+                    }
+                    if (err == PF_OK && ms_best < best.ms)
+                        best = {th, PF_PLACE_INTERLEAVED, 1, ms_best, S, cl};
+                    if (err != PF_OK) break;
+                }
+                if (err != PF_OK) break;
+            }
+            if (err != PF_OK) break;
         }
     }
     cudaEventDestroy(e0);

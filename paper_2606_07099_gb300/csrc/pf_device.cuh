@@ -134,6 +134,48 @@ struct AdjArgs {
     double* dQmax;
 };
 
+// Scenario-interleaved packs (placement PF_PLACE_INTERLEAVED): S scenarios share one
+// workspace region in which every per-scenario quantity is stored item-major, [item][S],
+// so that the S lanes of a slot touch S consecutive elements of each item; one
+// thread-block cluster of `cluster` CTAs runs the pack.  Offsets are in bytes from the
+// pack's base.
+struct SiLayout {
+    int S;              // scenarios per pack (8, 16 or 32)
+    int cluster;        // CTAs per pack (one thread-block cluster)
+    int threads;        // threads per CTA
+    size_t pack_bytes;  // workspace bytes per pack
+    size_t off_fac;     // factor: float4 [nnzb][S] (FP32) or double2 [nnzb][2][S] (FP64)
+    size_t off_V, off_I, off_U, off_M, off_SP, off_DV;  // double2 [n_bus][S] each:
+                        // V, I = Y V, u = e^{j theta}, (Vm, theta), (P_spec, Q_spec), dV
+    size_t off_FA, off_FB;  // float4 [n_bus][S]: FP32 fill copies (V, u) and (Vm, u conj(I), 0)
+    size_t off_F, off_DZ;   // double2 [n][S]: F1 and the accumulated Newton step
+    size_t off_X;       // FT2 [n][S]: the triangular-solve vector
+    size_t off_ctl;     // reduction buffers (3 x 32 u64) and singular flags (32 u32)
+    size_t smem_bytes;  // dynamic shared memory per CTA (lane-group reductions)
+};
+
+struct SiArgs {
+    int batch;
+    int max_iter;
+    int ir_steps;
+    double tol;
+    double ir_rtol;
+    double ir_gate;
+    const double* Pd;
+    const double* Qd;
+    const double* Pg;
+    const double* Vset;
+    double* Vm;
+    double* Va;
+    double* Pg_out;
+    double* Qg_out;
+    double* fmis;
+    int* iters;
+    int* status;
+    char* ws;
+    SiLayout L;
+};
+
 // Vector arena carved from one base pointer (shared or global memory).
 struct Arrays {
     // FP64, one entry per bus; (Uc, Us) = (cos theta, sin theta) is the unit phasor u

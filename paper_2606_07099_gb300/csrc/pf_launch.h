@@ -25,6 +25,12 @@ cudaError_t solve_bde(const DevPlan& P, int batch, const double* Pd, const doubl
                       const double* Pg, const double* Vset, double tol, int max_iter, double* Vm,
                       double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
                       double* fmis, void* ws, cudaStream_t s);
+// The scenario-interleaved solve (pf_si.cu): one thread-block cluster per pack.
+template <typename FT>
+cudaError_t launch_solve_si(const DevPlan& P, const SiArgs& A, cudaStream_t s);
+// Whether a pack shape can be scheduled on the current device (at least one cluster).
+template <typename FT>
+cudaError_t si_shape_fits(int S, int cluster, int threads, size_t smem, bool* fits);
 // Device address of pf_solve_noalloc's static scratch array on the current device
 // (pf_noalloc.cu; called once per handle by pf_create).
 cudaError_t noalloc_lookup(void** out);

@@ -169,7 +169,7 @@ class PowerFlow:
 
     @staticmethod
     def make_opts(precision="mixed", ir_steps=2, ir_rtol=1e-3, group_threads=0, keep_factors=False,
-                  placement=0, instances_per_cta=0, ir_gate=0.0):
+                  placement=0, instances_per_cta=0, ir_gate=0.0, pack=0, cluster=0):
         """Solve options.  Mixed precision refines with the FP64 residual until
         ||r|| <= min(ir_rtol, ||F1||) * ||F1|| (at most ir_steps sweeps; ir_rtol = 0 runs
         every sweep, ir_steps = 0 is the unrefined FP32 step), on the Newton steps taken
@@ -178,7 +178,7 @@ class PowerFlow:
             raise ValueError("precision must be 'fp64' or 'mixed'")
         return L.SolveOpts(_PREC[precision], int(ir_steps), float(ir_rtol), int(group_threads),
                            1 if keep_factors else 0, int(placement), int(instances_per_cta),
-                           float(ir_gate))
+                           float(ir_gate), int(pack), int(cluster))
 
     def workspace_bytes(self, batch: int, opts: L.SolveOpts) -> int:
         n = C.c_size_t(0)
@@ -195,13 +195,15 @@ class PowerFlow:
     def solve(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
               ir_rtol=1e-3, group_threads=0, keep_factors=False, out: SolveResult | None = None,
               workspace: torch.Tensor | None = None, placement=0,
-              instances_per_cta=0, ir_gate=0.0) -> SolveResult:
-        """Batched Newton-Raphson (pf_solve) on the current stream; returns device tensors."""
+              instances_per_cta=0, ir_gate=0.0, pack=0, cluster=0) -> SolveResult:
+        """Batched Newton-Raphson (pf_solve) on the current stream; returns device tensors.
+        ``placement`` PF_PLACE_INTERLEAVED (5) runs packs of ``pack`` scenarios on
+        thread-block clusters of ``cluster`` CTAs of ``group_threads`` threads."""
         batch = Pd.shape[0]
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
             _check_bus_tensor(v, nm, self.n_bus, batch)
         opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
-                              instances_per_cta, ir_gate)
+                              instances_per_cta, ir_gate, pack, cluster)
         ws = self.workspace(batch, opts) if workspace is None else workspace
         if out is None:
             e = dict(dtype=torch.float64, device=Pd.device)
@@ -388,8 +390,13 @@ class PowerFlow:
         for nm, v in (("Pd", Pd), ("Qd", Qd), ("Pg", Pg), ("Vset", Vset)):
             _check_bus_tensor(v, nm, self.n_bus, batch)
         opts = self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, 0, 0, ir_gate)
-        ws = self.workspace(batch, self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors,
-                                                  L.PF_PLACE_GLOBAL))
+        # room for every candidate: the per-scenario placements' largest slot, and the
+        # interleaved packs (timed on large networks without kept factors)
+        need = [self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, L.PF_PLACE_GLOBAL)]
+        if not keep_factors:
+            need += [self.make_opts(precision, ir_steps, ir_rtol, 1024, False,
+                                    L.PF_PLACE_INTERLEAVED, 0, ir_gate, S, 16) for S in (8, 16, 32)]
+        ws = self.workspace(batch, max(need, key=lambda o: self.workspace_bytes(batch, o)))
         res = L.TuneResult()
         stream = torch.cuda.current_stream(Pd.device).cuda_stream
         L.check(self._lib.pf_autotune(self._h, batch, Pd.data_ptr(), Qd.data_ptr(), Pg.data_ptr(),
@@ -398,7 +405,8 @@ class PowerFlow:
                 "pf_autotune")
         self._last = None
         return {"group_threads": res.group_threads, "placement": res.placement,
-                "instances_per_cta": res.instances_per_cta, "ms": res.ms}
+                "instances_per_cta": res.instances_per_cta, "ms": res.ms, "pack": res.pack,
+                "cluster": res.cluster}
 
     def adjoint(self, dVm, dVa, dPg=None, dQg=None, out: Gradients | None = None) -> Gradients:
         """Implicit-differentiation backward pass (pf_adjoint) of the last solve; ``out``
