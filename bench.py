@@ -47,7 +47,16 @@ HBM_FALLBACK_GBS = 6800.0
 
 
 # the device code of the solve kernels (a committed capture is valid while these are unchanged)
-KERNEL_SOURCES = ("pf_body.cuh", "pf_kernels.cu", "pf_device.cuh")
+KERNEL_SOURCES = ("pf_body.cuh", "pf_kernels.cu", "pf_device.cuh", "pf_si.cu")
+
+
+def headline_kernel(shape):
+    """The solve kernel a tuned launch shape runs, and the name of its committed ncu summary."""
+    if shape and shape.get("placement") == 5:
+        cl = "true" if shape.get("cluster", 1) > 1 else "false"
+        return (f"nr_solve_si_kernel<float, {shape['pack']}, {cl}>",
+                "nr_solve_si_c1_mixed.json")
+    return "nr_solve_kernel<float>", "nr_solve_c1_mixed.json"
 
 
 def profiled_traffic(kernel_json="nr_solve_c1_mixed.json"):
@@ -796,8 +805,9 @@ def gpu_leg(args, rank, world):
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": f64 / (ms_launch / 1e3) / 1e12, "peak": peak64,
                      "unit": "TFLOP/s", "frac": f64 / (ms_launch / 1e3) / 1e12 / peak64,
-                     "traffic": profiled_traffic() if args.workload == WORKLOAD else None,
-                     "kernel": "nr_solve_kernel<float>",
+                     "traffic": (profiled_traffic(headline_kernel(tuned.get("mixed"))[1])
+                                 if args.workload == WORKLOAD else None),
+                     "kernel": headline_kernel(tuned.get("mixed"))[0],
                      "note": ("FP64 pipe: achieved = algorithmic FP64 flops per launch / mean "
                               "launch time; peak = FP64 FMA rate measured in this run "
                               "(pf_measure_fma_peak, of measured); the FP32 work's share of its "

@@ -106,11 +106,12 @@ typedef struct {
     double ir_gate;    /* PF_MIXED: check and refine a Newton step only once ||F1||_inf <=
                           ir_gate (far from the solution the Newton model error dwarfs the
                           FP32 solve error); 0 = every step */
-    int pack;          /* PF_PLACE_INTERLEAVED: scenarios per pack (8, 16 or 32; 0 = auto or
-                          the autotuned choice); ignored by the other placements */
+    int pack;          /* PF_PLACE_INTERLEAVED: scenarios per pack (2, 4, 8, 16 or 32; 0 =
+                          auto or the autotuned choice); ignored by the other placements */
     int cluster;       /* PF_PLACE_INTERLEAVED: CTAs per pack, one thread-block cluster
-                          (1..16; 0 = auto or the autotuned choice); group_threads is then the
-                          threads per CTA (group_threads / pack a power of two >= 16) */
+                          (1..16, 1 = a single CTA with CTA barriers; 0 = auto or the autotuned
+                          choice); group_threads is then the threads per CTA (group_threads /
+                          pack a power of two >= 16) */
 } pf_solve_opts;
 
 typedef enum {
@@ -266,8 +267,13 @@ pf_err pf_solve(pf_handle* h, int batch,
  * before anything is launched: it must lie, for all the bytes the call touches, inside
  * one allocation that CUDA knows and that kernels on the handle's device address at the
  * same pointer value; otherwise (pageable memory, a range past the end of an allocation,
- * another device's memory) the call returns PF_EINVAL and does nothing.  Errors: those
- * of pf_solve.
+ * another device's memory) the call returns PF_EINVAL and does nothing.  With
+ * PF_PLACE_AUTO a per-scenario placement serves this call (the fastest per-scenario
+ * shape of the last pf_autotune, also when the tuning picked interleaved packs): those
+ * kernels read each scenario's host rows over its Newton iterations, while interleaved
+ * packs read them in one burst before the solve starts, which measured slower end to end.
+ * The workspace must then hold pf_workspace_size for PF_PLACE_GLOBAL (the largest
+ * per-scenario slot).  Errors: those of pf_solve.
  */
 pf_err pf_solve_host(pf_handle* h, int batch,
                      const double* Pd, const double* Qd, const double* Pg, const double* Vset,
@@ -369,9 +375,10 @@ pf_err pf_adjoint_qlim(pf_handle* h, int batch,
  * of the scenario data) for this handle, `batch` and opts->precision by timing
  * pf_solve on the given inputs (device, as pf_solve) for every candidate: 32..1024
  * threads per scenario, or 2, 4 or 8 one-warp scenarios per CTA, times every placement
- * that fits; and, on networks of 1000 buses or more without keep_factors, interleaved
- * packs of 8, 16 or 32 scenarios on clusters of 4, 8 or 16 CTAs of 512 or 1024 threads
- * whose workspace fits the one given (the best shape depends on the batch: a few scenarios of a large network
+ * that fits; and, without keep_factors, interleaved packs: 2 to 32 scenarios on one CTA
+ * of 256, 512 or 1024 threads, or 4 to 16 scenarios on clusters of 2 to 16 CTAs of 512 or
+ * 1024 threads, the shapes that occupy at least half of the SMs and whose workspace fits
+ * the one given (the best shape depends on the batch: a few scenarios of a large network
  * want the most threads each, thousands of small ones the most scenarios per SM).  The fastest one is kept in
  * the handle and used by later pf_solve calls with group_threads = 0 and placement =
  * PF_PLACE_AUTO at the same precision; *out (nullable) receives it.  The workspace

@@ -26,6 +26,9 @@ struct pf_handle {
     pf::DevPlan dp{};
     // autotuned launch configuration per precision (index 0 = FP64, 1 = mixed)
     pf_tune_result tuned[2] = {{0, 0, 0, 0.f}, {0, 0, 0, 0.f}};
+    // the fastest per-scenario configuration of the same tuning run: the choice for the
+    // calls the interleaved placement does not serve (kept factors, reactive limits)
+    pf_tune_result tuned_ps[2] = {{0, 0, 0, 0.f}, {0, 0, 0, 0.f}};
     // state of the last pf_solve (for pf_adjoint)
     int last_batch = -1;
     int last_ft = 0;
@@ -178,8 +181,6 @@ struct LaunchCfg {
 // below), and the largest cluster (at most 16 CTAs) that keeps every pack of the batch
 // resident at once.
 int auto_pack(int batch) { return batch >= 256 ? 16 : 8; }
-// The autotuner times interleaved packs from this network size up.
-constexpr int kSiMinBuses = 1000;
 int auto_cluster(const pf_handle* h, int batch, int S) {
     const int packs = (batch + S - 1) / S;
     int c = 16;
@@ -192,7 +193,10 @@ int auto_cluster(const pf_handle* h, int batch, int S) {
 // falls back to the heuristic placement and an explicit request is refused (-1).
 LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o, int batch = 0, bool si_ok = true) {
     const int ft = o->precision == PF_MIXED ? 4 : 8;
-    const pf_tune_result& t = h->tuned[o->precision == PF_MIXED ? 1 : 0];
+    const int pi = o->precision == PF_MIXED ? 1 : 0;
+    // where the interleaved placement may not serve, the tuned per-scenario shape stands in
+    const pf_tune_result& t =
+        (!si_ok && h->tuned[pi].placement == PF_PLACE_INTERLEAVED) ? h->tuned_ps[pi] : h->tuned[pi];
     const bool use_tuned = o->group_threads == 0 && o->instances_per_cta == 0 && t.group_threads;
     LaunchCfg c;
     c.threads = o->group_threads ? o->group_threads
@@ -228,7 +232,7 @@ LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o, int batch = 0, boo
 // Interleaved-pack shape check: threads / S a power of two of at least 16 lane groups (a
 // split sweep row's groups then never straddle two rounds), at most 1024 threads.
 bool si_shape_ok(int S, int cluster, int threads) {
-    if (S != 8 && S != 16 && S != 32) return false;
+    if (S != 2 && S != 4 && S != 8 && S != 16 && S != 32) return false;
     if (cluster < 1 || cluster > 16 || threads < 32 || threads > 1024 || threads % S) return false;
     const int ns = threads / S;
     return ns >= 16 && (ns & (ns - 1)) == 0;
@@ -278,7 +282,9 @@ bool opts_ok(const pf_solve_opts* o) {
     if (o->group_threads != 0 &&
         (o->group_threads < 32 || o->group_threads > 1024 || o->group_threads % 32)) return false;
     if (o->placement < PF_PLACE_AUTO || o->placement > PF_PLACE_INTERLEAVED) return false;
-    if (o->pack != 0 && o->pack != 8 && o->pack != 16 && o->pack != 32) return false;
+    if (o->pack != 0 && o->pack != 2 && o->pack != 4 && o->pack != 8 && o->pack != 16 &&
+        o->pack != 32)
+        return false;
     if (o->cluster < 0 || o->cluster > 16) return false;
     if (o->instances_per_cta < 0 || o->instances_per_cta > 8) return false;
     if (o->instances_per_cta > 1 && o->group_threads != 0 && o->group_threads != 32) return false;
@@ -387,12 +393,12 @@ pf_err solve_impl(pf_handle* h, int batch, const double* Pd, const double* Qd, c
                   const double* Vset, double tol, int max_iter, const pf_solve_opts* opts,
                   double* Vm, double* Va, double* Pg_out, double* Qg_out, int* iters, int* status,
                   double* final_mismatch, void* workspace, size_t workspace_bytes, void* stream,
-                  const QlimIn* q) {
+                  const QlimIn* q, bool si_allowed = true) {
     if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
         return PF_EINVAL;
     if (!(tol > 0.0) || max_iter < 0 || !opts_ok(opts)) return PF_EINVAL;
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    LaunchCfg cfg = resolve(h, opts, batch, !opts->keep_factors && !q);
+    LaunchCfg cfg = resolve(h, opts, batch, si_allowed && !opts->keep_factors && !q);
     if (cfg.placement < 0) return PF_ENOTSUP;
     if (cfg.placement == PF_PLACE_INTERLEAVED)
         return solve_si(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, cfg, Vm, Va, Pg_out,
@@ -793,10 +799,21 @@ pf_err pf_solve_host(pf_handle* h, int batch, const double* Pd, const double* Qd
     if (!h || batch < 1 || !Pd || !Qd || !Pg || !Vset || !Vm || !Va || !status || !workspace)
         return PF_EINVAL;
     if (!opts_ok(opts)) return PF_EINVAL;
+    // host buffers: the per-scenario forms read them over the Newton iterations; the
+    // interleaved packs read them in one burst before they start (measured slower end to
+    // end), so they serve this call only when asked for explicitly
     size_t ws_need = 0;
     {
-        const pf_err we = pf_workspace_size(h, batch, opts, &ws_need);
-        if (we != PF_OK) return we;
+        const int ft = opts->precision == PF_MIXED ? 4 : 8;
+        const LaunchCfg cfg = resolve(h, opts, batch,
+                                      opts->placement == PF_PLACE_INTERLEAVED && !opts->keep_factors);
+        if (cfg.placement < 0) return PF_ENOTSUP;
+        if (cfg.placement == PF_PLACE_INTERLEAVED) {
+            if (!si_shape_ok(cfg.S, cfg.cluster, cfg.threads)) return PF_EINVAL;
+            ws_need = si_workspace(h, ft, cfg, batch);
+        } else {
+            ws_need = make_layout(h, ft, opts->keep_factors, cfg.placement).slot_bytes * (size_t)batch;
+        }
     }
     const size_t row = sizeof(double) * (size_t)batch * (size_t)h->plan.n_bus;
     DeviceGuard guard(h->device);
@@ -811,7 +828,8 @@ pf_err pf_solve_host(pf_handle* h, int batch, const double* Pd, const double* Qd
         return PF_EINVAL;
     if (workspace_bytes < ws_need || !addressable(workspace, ws_need, h->device)) return PF_EINVAL;
     return solve_impl(h, batch, Pd, Qd, Pg, Vset, tol, max_iter, opts, Vm, Va, Pg_out, Qg_out,
-                      iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr);
+                      iters, status, final_mismatch, workspace, workspace_bytes, stream, nullptr,
+                      opts->placement == PF_PLACE_INTERLEAVED);
 }
 
 pf_err pf_bde_workspace_size(const pf_handle* h, int batch, size_t* bytes) {
@@ -936,14 +954,18 @@ pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, 
             if (err == PF_OK && (best.group_threads == 0 || ms_best < best.ms)) best = {th, pl, ipc, ms_best};
         }
     }
+    const pf_tune_result best_ps = best;
     // interleaved packs on thread-block clusters (forward solves without kept factors, on
     // networks large enough for it): scenarios per pack x CTAs per cluster x threads
     const int ft = opts->precision == PF_MIXED ? 4 : 8;
-    if (err == PF_OK && !opts->keep_factors && h->plan.n_bus >= kSiMinBuses) {
-        for (int S : {8, 16, 32}) {
-            if (S >= 2 * batch && S > 8) continue;  // packs mostly empty
-            for (int cl : {4, 8, 16}) {
-                for (int th : {512, 1024}) {
+    if (err == PF_OK && !opts->keep_factors) {
+        for (int S : {2, 4, 8, 16, 32}) {
+            if (S >= 2 * batch && S > 2) continue;  // packs mostly empty
+            for (int cl : {1, 2, 4, 8, 16}) {
+                if (cl > 1 && (S < 4 || S > 16)) continue;
+                if ((long long)((batch + S - 1) / S) * cl < h->num_sms / 2) continue;  // too few SMs
+                for (int th : {256, 512, 1024}) {
+                    if (cl > 1 && th < 512) continue;
                     const LaunchCfg c{th, PF_PLACE_INTERLEAVED, 1, S, cl};
                     if (!si_shape_ok(S, cl, th) || si_workspace(h, ft, c, batch) > workspace_bytes)
                         continue;
@@ -989,6 +1011,7 @@ pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, 
     h->last_batch = -1;  // the trial solves invalidate the adjoint state
     if (err != PF_OK) return err;
     h->tuned[opts->precision == PF_MIXED ? 1 : 0] = best;
+    h->tuned_ps[opts->precision == PF_MIXED ? 1 : 0] = best_ps;
     if (out) *out = best;
     return PF_OK;
 }

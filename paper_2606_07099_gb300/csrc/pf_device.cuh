@@ -140,7 +140,7 @@ struct AdjArgs {
 // thread-block cluster of `cluster` CTAs runs the pack.  Offsets are in bytes from the
 // pack's base.
 struct SiLayout {
-    int S;              // scenarios per pack (8, 16 or 32)
+    int S;              // scenarios per pack (2, 4, 8, 16 or 32)
     int cluster;        // CTAs per pack (one thread-block cluster)
     int threads;        // threads per CTA
     size_t pack_bytes;  // workspace bytes per pack

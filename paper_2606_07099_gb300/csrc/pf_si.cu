@@ -54,6 +54,13 @@ __device__ __forceinline__ void cluster_sync() {
         "barrier.cluster.arrive.release.aligned;\n\t"
         "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
+// The barrier between the phases of a pack: the cluster's, or the CTA's when one CTA runs
+// the pack (its global writes are then ordered for its own threads by __syncthreads).
+template <bool CL>
+__device__ __forceinline__ void pack_sync() {
+    if (CL) cluster_sync();
+    else __syncthreads();
+}
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -70,6 +77,20 @@ __device__ __forceinline__ unsigned cluster_index() {
     return r;
 }
 
+// Loads and stores of pack data: through L2 only (cache-global) when several CTAs share
+// the pack, plain (L1-cached) when one CTA runs it -- its own writes are then visible to
+// its own later loads after a CTA barrier.
+template <bool CL, typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+    if constexpr (CL) return __ldcg(p);
+    else return *p;
+}
+template <bool CL, typename T>
+__device__ __forceinline__ void stm(T* p, T v) {
+    if constexpr (CL) __stcg(p, v);
+    else *p = v;
+}
+
 // One pack's arrays (global memory).
 template <typename FT>
 struct Pack {
@@ -82,26 +103,26 @@ struct Pack {
 };
 
 // factor block e of lane s: float4 [e][S]; FP64 as two double2 rows [e][2][S]
-template <int S>
+template <int S, bool CL>
 __device__ __forceinline__ Blk<float> ldf(const float* fac, int e, int s) {
-    const float4 v = __ldcg(reinterpret_cast<const float4*>(fac) + ((size_t)e * S + s));
+    const float4 v = ldm<CL>(reinterpret_cast<const float4*>(fac) + ((size_t)e * S + s));
     return {v.x, v.y, v.z, v.w};
 }
-template <int S>
+template <int S, bool CL>
 __device__ __forceinline__ Blk<double> ldf(const double* fac, int e, int s) {
     const double2* p = reinterpret_cast<const double2*>(fac) + ((size_t)e * 2 * S + s);
-    const double2 u = __ldcg(p), w = __ldcg(p + S);
+    const double2 u = ldm<CL>(p), w = ldm<CL>(p + S);
     return {u.x, u.y, w.x, w.y};
 }
-template <int S>
+template <int S, bool CL>
 __device__ __forceinline__ void stf(float* fac, int e, int s, Blk<float> v) {
-    __stcg(reinterpret_cast<float4*>(fac) + ((size_t)e * S + s), make_float4(v.a, v.b, v.c, v.d));
+    stm<CL>(reinterpret_cast<float4*>(fac) + ((size_t)e * S + s), make_float4(v.a, v.b, v.c, v.d));
 }
-template <int S>
+template <int S, bool CL>
 __device__ __forceinline__ void stf(double* fac, int e, int s, Blk<double> v) {
     double2* p = reinterpret_cast<double2*>(fac) + ((size_t)e * 2 * S + s);
-    __stcg(p, make_double2(v.a, v.b));
-    __stcg(p + S, make_double2(v.c, v.d));
+    stm<CL>(p, make_double2(v.a, v.b));
+    stm<CL>(p + S, make_double2(v.c, v.d));
 }
 __device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
@@ -111,7 +132,7 @@ __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2
 // with a cluster barrier, so it also orders everything written before it.  The three
 // global slots rotate: slot r is read right after round r's barrier, and CTA 0 clears
 // slot r + 1 during round r, after the barrier that ended every read of its last use.
-template <int S>
+template <int S, bool CL>
 __device__ double cluster_max(unsigned long long k, unsigned long long* red, int& round,
                               unsigned long long* s_red, unsigned rank) {
 #pragma unroll
@@ -125,8 +146,8 @@ __device__ double cluster_max(unsigned long long k, unsigned long long* red, int
         atomicMax(slot + threadIdx.x, s_red[threadIdx.x]);
         if (rank == 0) atomicExch(red + ((round + 1) % 3) * 32 + threadIdx.x, 0ull);
     }
-    cluster_sync();
-    const unsigned long long r = __ldcg(slot + (threadIdx.x & (S - 1)));
+    pack_sync<CL>();
+    const unsigned long long r = __ldcg(slot + (threadIdx.x & (S - 1)));  // set by atomics: L2
     ++round;
     return key_to_norm(r);
 }
@@ -142,7 +163,7 @@ __device__ __forceinline__ unsigned lanes_where(bool pred) {
 // ---------------------------------------------------------------- per-bus phases
 // I = Y V, S = V conj(I), F1 = spec - S at the pivot positions; with FP32 copies for the
 // FP32 fill.  Returns the lane's max |F1| as an ordered key.
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __device__ unsigned long long si_mismatch(const DevPlan& P, const Pack<FT>& k, int gs, int TS,
                                           int s, bool go) {
     unsigned long long kmax = 0;
@@ -153,25 +174,25 @@ __device__ unsigned long long si_mismatch(const DevPlan& P, const Pack<FT>& k, i
         for (int q = __ldg(P.y_ptr + i); q < k1; ++q) {
             const int j = __ldg(P.y_idx + q);
             const double2 y = __ldg(P.y_gb + q);
-            const double2 v = __ldcg(k.V + ((size_t)j * S + s));
+            const double2 v = ldm<CL>(k.V + ((size_t)j * S + s));
             ir = fma(y.x, v.x, fma(-y.y, v.y, ir));
             ii = fma(y.x, v.y, fma(y.y, v.x, ii));
         }
         const size_t o = (size_t)i * S + s;
-        __stcg(k.I + o, make_double2(ir, ii));
+        stm<CL>(k.I + o, make_double2(ir, ii));
         if constexpr (sizeof(FT) == 4) {  // FP32 copies of V, u, Vm and u conj(I) for the FP32 fill
-            const double2 u = __ldcg(k.U + o), m = __ldcg(k.M + o);
+            const double2 u = ldm<CL>(k.U + o), m = ldm<CL>(k.M + o);
             const float c = float(u.x), sn = float(u.y), vm = float(m.x);
             const float fir = float(ir), fii = float(ii);
-            __stcg(k.FA + o, make_float4(vm * c, vm * sn, c, sn));
-            __stcg(k.FB + o, make_float4(vm, fmaf(c, fir, sn * fii), fmaf(sn, fir, -(c * fii)), 0.f));
+            stm<CL>(k.FA + o, make_float4(vm * c, vm * sn, c, sn));
+            stm<CL>(k.FB + o, make_float4(vm, fmaf(c, fir, sn * fii), fmaf(sn, fir, -(c * fii)), 0.f));
         }
         const int p = __ldg(P.bus2pos + i);
         if (p >= 0) {
-            const double2 v = __ldcg(k.V + o), sp = __ldcg(k.SP + o);
+            const double2 v = ldm<CL>(k.V + o), sp = ldm<CL>(k.SP + o);
             const double fP = fma(-v.x, ir, fma(-v.y, ii, sp.x));
             const double fQ = (__ldg(P.bus_type + i) == 0) ? fma(-v.y, ir, fma(v.x, ii, sp.y)) : 0.0;
-            __stcg(k.F + ((size_t)p * S + s), make_double2(fP, fQ));
+            stm<CL>(k.F + ((size_t)p * S + s), make_double2(fP, fQ));
             kmax = max(kmax, max(abs_key(fP), abs_key(fQ)));
         }
     }
@@ -180,7 +201,7 @@ __device__ unsigned long long si_mismatch(const DevPlan& P, const Pack<FT>& k, i
 
 // The Jacobian fill (Alg. 1 values, the element formulas of jac_block) into the factor,
 // and x = -F1 for the first solve.
-template <int S>
+template <int S, bool CL>
 __device__ void si_fill(const DevPlan& P, const Pack<float>& k, int gs, int TS, int s, bool go) {
     if (!go) return;
     for (int e = gs; e < P.nnzb; e += TS) {
@@ -189,19 +210,19 @@ __device__ void si_fill(const DevPlan& P, const Pack<float>& k, int gs, int TS, 
         Blk<float> m{0.f, 0.f, 0.f, 0.f};
         if (yi >= 0) {
             const float2 y = __ldg(P.y_gb32 + yi);
-            const float4 ai = __ldcg(k.FA + ((size_t)i * S + s)), bi = __ldcg(k.FB + ((size_t)i * S + s));
-            const float4 aj = __ldcg(k.FA + ((size_t)j * S + s)), bj = __ldcg(k.FB + ((size_t)j * S + s));
+            const float4 ai = ldm<CL>(k.FA + ((size_t)i * S + s)), bi = ldm<CL>(k.FB + ((size_t)i * S + s));
+            const float4 aj = ldm<CL>(k.FA + ((size_t)j * S + s)), bj = ldm<CL>(k.FB + ((size_t)j * S + s));
             m = jac_block<float>(p == q, y.x, y.y, ai.x, ai.y, aj.z, aj.w, bj.x, bi.x, bi.y, bi.z);
         }
-        stf<S>(k.fac, e, s, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
+        stf<S, CL>(k.fac, e, s, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
     }
     for (int p = gs; p < P.n; p += TS) {
-        const double2 f = __ldcg(k.F + ((size_t)p * S + s));
-        __stcg(k.X + ((size_t)p * S + s), make_float2(float(-f.x), float(-f.y)));
+        const double2 f = ldm<CL>(k.F + ((size_t)p * S + s));
+        stm<CL>(k.X + ((size_t)p * S + s), make_float2(float(-f.x), float(-f.y)));
     }
 }
 
-template <int S>
+template <int S, bool CL>
 __device__ void si_fill(const DevPlan& P, const Pack<double>& k, int gs, int TS, int s, bool go) {
     if (!go) return;
     for (int e = gs; e < P.nnzb; e += TS) {
@@ -211,23 +232,23 @@ __device__ void si_fill(const DevPlan& P, const Pack<double>& k, int gs, int TS,
         if (yi >= 0) {
             const double2 y = __ldg(P.y_gb + yi);
             const size_t oi = (size_t)i * S + s, oj = (size_t)j * S + s;
-            const double2 ui = __ldcg(k.U + oi), Ii = __ldcg(k.I + oi), vi = __ldcg(k.V + oi);
-            const double2 mi = __ldcg(k.M + oi), uj = __ldcg(k.U + oj), mj = __ldcg(k.M + oj);
+            const double2 ui = ldm<CL>(k.U + oi), Ii = ldm<CL>(k.I + oi), vi = ldm<CL>(k.V + oi);
+            const double2 mi = ldm<CL>(k.M + oi), uj = ldm<CL>(k.U + oj), mj = ldm<CL>(k.M + oj);
             m = jac_block<double>(p == q, y.x, y.y, vi.x, vi.y, uj.x, uj.y, mj.x, mi.x,
                                   ui.x * Ii.x + ui.y * Ii.y, ui.y * Ii.x - ui.x * Ii.y);
         }
-        stf<S>(k.fac, e, s, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
+        stf<S, CL>(k.fac, e, s, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
     }
     for (int p = gs; p < P.n; p += TS) {
-        const double2 f = __ldcg(k.F + ((size_t)p * S + s));
-        __stcg(k.X + ((size_t)p * S + s), make_double2(-f.x, -f.y));
+        const double2 f = ldm<CL>(k.F + ((size_t)p * S + s));
+        stm<CL>(k.X + ((size_t)p * S + s), make_double2(-f.x, -f.y));
     }
 }
 
 // ---------------------------------------------------------------- factorisation
 // Sum of the Schur contributions L(i,k) U(k,j) of one target over its pairs c0 .. c1,
 // kBatch pairs at a time, in pair order (as schur_gather does per scenario).
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __device__ __forceinline__ Blk<FT> si_schur(const DevPlan& P, const FT* fac, int c, int c1, int s) {
     constexpr int NB = kBatch<FT>;
     Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
@@ -239,8 +260,8 @@ __device__ __forceinline__ Blk<FT> si_schur(const DevPlan& P, const FT* fac, int
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             if (lu[q].x >= 0) {
-                xl[q] = ldf<S>(fac, lu[q].x, s);
-                yu[q] = ldf<S>(fac, lu[q].y, s);
+                xl[q] = ldf<S, CL>(fac, lu[q].x, s);
+                yu[q] = ldf<S, CL>(fac, lu[q].y, s);
             } else {
                 xl[q] = yu[q] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
             }
@@ -259,7 +280,7 @@ __device__ __forceinline__ Blk<FT> si_schur(const DevPlan& P, const FT* fac, int
 // One elimination level: the L-column scalings (phase A), a cluster barrier, then the
 // level's Schur targets and pivot inversions (phase B) as one item space, and a cluster
 // barrier.  A singular pivot raises the lane's flag in the pack's `sing` array.
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __device__ void si_lu_level(const DevPlan& P, const Pack<FT>& k, int l, int gs, int TS, int s,
                             bool go) {
     if (go) {
@@ -267,11 +288,11 @@ __device__ void si_lu_level(const DevPlan& P, const Pack<FT>& k, int l, int gs, 
         for (int c = __ldg(P.la_ptr + l) + gs; c < a1; c += TS) {
             const int2 ld = __ldg(P.la + c);
             int dummy = 0;
-            const Blk<FT> m = ldf<S>(k.fac, ld.x, s), d = ldf<S>(k.fac, ld.y, s);
-            stf<S>(k.fac, ld.x, s, mul(m, inv2(d, &dummy)));
+            const Blk<FT> m = ldf<S, CL>(k.fac, ld.x, s), d = ldf<S, CL>(k.fac, ld.y, s);
+            stf<S, CL>(k.fac, ld.x, s, mul(m, inv2(d, &dummy)));
         }
     }
-    cluster_sync();
+    pack_sync<CL>();
     if (go) {
         const int t0 = __ldg(P.sch_tptr + l), nT = __ldg(P.sch_tptr + l + 1) - t0;
         const int r0 = __ldg(P.lev_ptr + l), nI = nT + (__ldg(P.lev_ptr + l + 1) - r0);
@@ -281,22 +302,22 @@ __device__ void si_lu_level(const DevPlan& P, const Pack<FT>& k, int l, int gs, 
                 const int t = t0 + u;
                 const int tg = __ldg(P.sch_tgt + t);
                 const Blk<FT> acc =
-                    si_schur<FT, S>(P, k.fac, __ldg(P.sch_cptr + t), __ldg(P.sch_cptr + t + 1), s);
-                stf<S>(k.fac, tg, s, sub_blk(ldf<S>(k.fac, tg, s), acc));
+                    si_schur<FT, S, CL>(P, k.fac, __ldg(P.sch_cptr + t), __ldg(P.sch_cptr + t + 1), s);
+                stf<S, CL>(k.fac, tg, s, sub_blk(ldf<S, CL>(k.fac, tg, s), acc));
             } else {
                 const int dk = __ldg(P.lu_diag + r0 + (u - nT));
-                stf<S>(k.fac, dk, s, inv2(ldf<S>(k.fac, dk, s), &bad));
+                stf<S, CL>(k.fac, dk, s, inv2(ldf<S, CL>(k.fac, dk, s), &bad));
             }
         }
         if (bad) atomicOr(k.sing + s, 1u);
     }
-    cluster_sync();
+    pack_sync<CL>();
 }
 
 // ---------------------------------------------------------------- triangular sweeps
 // Gathered sum of one row over its entries e, e + stride, ... < e1 (kBatch at a time):
 // s0, s1 += M_e x_q(e).
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __device__ __forceinline__ void si_row_gather(const DevPlan& P, const Pack<FT>& k, int e, int e1,
                                               int stride, int s, FT& s0, FT& s1) {
     constexpr int NB = kBatch<FT>;
@@ -309,8 +330,8 @@ __device__ __forceinline__ void si_row_gather(const DevPlan& P, const Pack<FT>& 
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             if (q[b] >= 0) {
-                m[b] = ldf<S>(k.fac, e + b * stride, s);
-                y[b] = __ldcg(k.X + ((size_t)q[b] * S + s));
+                m[b] = ldf<S, CL>(k.fac, e + b * stride, s);
+                y[b] = ldm<CL>(k.X + ((size_t)q[b] * S + s));
             } else {
                 m[b] = Blk<FT>{FT(0), FT(0), FT(0), FT(0)};
                 y[b] = mk2(FT(0), FT(0));
@@ -326,17 +347,17 @@ __device__ __forceinline__ void si_row_gather(const DevPlan& P, const Pack<FT>& 
 
 // x_p <- x_p - s (lower sweep) or P_p^-1 (x_p - s) (upper sweep; the stored pivot is the
 // inverse).
-template <typename FT, int S, bool UPPER>
+template <typename FT, int S, bool UPPER, bool CL>
 __device__ __forceinline__ void si_row_finish(const Pack<FT>& k, int p, int dg, int s, FT s0,
                                               FT s1) {
     typename V2<FT>::T* xp = k.X + ((size_t)p * S + s);
-    const typename V2<FT>::T x = __ldcg(xp);
+    const typename V2<FT>::T x = ldm<CL>(xp);
     const FT x0 = x.x - s0, x1 = x.y - s1;
     if (UPPER) {
-        const Blk<FT> d = ldf<S>(k.fac, dg, s);
-        __stcg(xp, mk2(d.a * x0 + d.b * x1, d.c * x0 + d.d * x1));
+        const Blk<FT> d = ldf<S, CL>(k.fac, dg, s);
+        stm<CL>(xp, mk2(d.a * x0 + d.b * x1, d.c * x0 + d.d * x1));
     } else {
-        __stcg(xp, mk2(x0, x1));
+        stm<CL>(xp, mk2(x0, x1));
     }
 }
 
@@ -345,7 +366,7 @@ __device__ __forceinline__ void si_row_finish(const Pack<FT>& k, int p, int dg, 
 // min(G, kGMax) lane groups of one CTA (row r of the level belongs to CTA r mod C); the
 // groups' partial sums meet in shared memory and are added in group order.  Ends with a
 // cluster barrier.
-template <typename FT, int S, bool UPPER>
+template <typename FT, int S, bool UPPER, bool CL>
 __device__ void si_sweep_level(const DevPlan& P, const Pack<FT>& k, int l, int gs, int TS, int s,
                                int slot, int NS, int rank, int C, bool go,
                                typename V2<FT>::T* part) {
@@ -357,9 +378,9 @@ __device__ void si_sweep_level(const DevPlan& P, const Pack<FT>& k, int l, int g
             for (int r = gs; r < R; r += TS) {
                 const int p = r0 + r, dg = __ldg(P.lu_diag + p);
                 FT s0 = FT(0), s1 = FT(0);
-                si_row_gather<FT, S>(P, k, UPPER ? dg + 1 : __ldg(P.lu_ptr + p),
+                si_row_gather<FT, S, CL>(P, k, UPPER ? dg + 1 : __ldg(P.lu_ptr + p),
                                      UPPER ? __ldg(P.lu_ptr + p + 1) : dg, 1, s, s0, s1);
-                si_row_finish<FT, S, UPPER>(k, p, dg, s, s0, s1);
+                si_row_finish<FT, S, UPPER, CL>(k, p, dg, s, s0, s1);
             }
         }
     } else {
@@ -374,7 +395,7 @@ __device__ void si_sweep_level(const DevPlan& P, const Pack<FT>& k, int l, int g
             int dg = 0;
             if (act) {
                 dg = __ldg(P.lu_diag + p);
-                si_row_gather<FT, S>(P, k, (UPPER ? dg + 1 : __ldg(P.lu_ptr + p)) + g,
+                si_row_gather<FT, S, CL>(P, k, (UPPER ? dg + 1 : __ldg(P.lu_ptr + p)) + g,
                                      UPPER ? __ldg(P.lu_ptr + p + 1) : dg, G, s, s0, s1);
             }
             part[slot * S + s] = mk2(s0, s1);
@@ -386,26 +407,26 @@ __device__ void si_sweep_level(const DevPlan& P, const Pack<FT>& k, int l, int g
                     t0 += v.x;
                     t1 += v.y;
                 }
-                si_row_finish<FT, S, UPPER>(k, p, dg, s, t0, t1);
+                si_row_finish<FT, S, UPPER, CL>(k, p, dg, s, t0, t1);
             }
             __syncthreads();
         }
     }
-    cluster_sync();
+    pack_sync<CL>();
 }
 
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __device__ void si_solve(const DevPlan& P, const Pack<FT>& k, int gs, int TS, int s, int slot,
                          int NS, int rank, int C, bool go, typename V2<FT>::T* part) {
     for (int l = 0; l < P.n_levels; ++l)
-        si_sweep_level<FT, S, false>(P, k, l, gs, TS, s, slot, NS, rank, C, go, part);
+        si_sweep_level<FT, S, false, CL>(P, k, l, gs, TS, s, slot, NS, rank, C, go, part);
     for (int l = P.n_levels - 1; l >= 0; --l)
-        si_sweep_level<FT, S, true>(P, k, l, gs, TS, s, slot, NS, rank, C, go, part);
+        si_sweep_level<FT, S, true, CL>(P, k, l, gs, TS, s, slot, NS, rank, C, go, part);
 }
 
 // ---------------------------------------------------------------- refinement (mixed)
 // dz += x (dz = x on the first call), and dV = u dVm + j V dtheta for the residual.
-template <int S>
+template <int S, bool CL>
 __device__ void si_accumulate(const DevPlan& P, const Pack<float>& k, int gs, int TS, int s,
                               bool go, bool first) {
     if (!go) return;
@@ -414,26 +435,26 @@ __device__ void si_accumulate(const DevPlan& P, const Pack<float>& k, int gs, in
         double2 dv = make_double2(0.0, 0.0);
         if (p >= 0) {
             const size_t op = (size_t)p * S + s;
-            const float2 xv = __ldcg(k.X + op);
+            const float2 xv = ldm<CL>(k.X + op);
             double2 dz = make_double2(double(xv.x), double(xv.y));
             if (!first) {
-                const double2 d0 = __ldcg(k.DZ + op);
+                const double2 d0 = ldm<CL>(k.DZ + op);
                 dz.x += d0.x;
                 dz.y += d0.y;
             }
-            __stcg(k.DZ + op, dz);
+            stm<CL>(k.DZ + op, dz);
             const size_t o = (size_t)i * S + s;
             const double dth = dz.x, dvm = (__ldg(P.bus_type + i) == 0) ? dz.y : 0.0;
-            const double2 u = __ldcg(k.U + o), v = __ldcg(k.V + o);
+            const double2 u = ldm<CL>(k.U + o), v = ldm<CL>(k.V + o);
             dv = make_double2(u.x * dvm - v.y * dth, u.y * dvm + v.x * dth);
         }
-        __stcg(k.DV + ((size_t)i * S + s), dv);
+        stm<CL>(k.DV + ((size_t)i * S + s), dv);
     }
 }
 
 // r = -F1 - J1 dz (FP64, linearised through Ybus), rounded into x; returns the lane's
 // max |r| (of the rounded values) as an ordered key.
-template <int S>
+template <int S, bool CL>
 __device__ unsigned long long si_residual(const DevPlan& P, const Pack<float>& k, int gs, int TS,
                                           int s, bool go) {
     float lmax = 0.f;
@@ -446,26 +467,26 @@ __device__ unsigned long long si_residual(const DevPlan& P, const Pack<float>& k
         for (int q = __ldg(P.y_ptr + i); q < k1; ++q) {
             const int j = __ldg(P.y_idx + q);
             const double2 y = __ldg(P.y_gb + q);
-            const double2 d = __ldcg(k.DV + ((size_t)j * S + s));
+            const double2 d = ldm<CL>(k.DV + ((size_t)j * S + s));
             ir = fma(y.x, d.x, fma(-y.y, d.y, ir));
             ii = fma(y.x, d.y, fma(y.y, d.x, ii));
         }
         const size_t o = (size_t)i * S + s, op = (size_t)p * S + s;
-        const double2 v = __ldcg(k.V + o), I = __ldcg(k.I + o), dv = __ldcg(k.DV + o);
-        const double2 F = __ldcg(k.F + op);
+        const double2 v = ldm<CL>(k.V + o), I = ldm<CL>(k.I + o), dv = ldm<CL>(k.DV + o);
+        const double2 F = ldm<CL>(k.F + op);
         const double rP = fma(dv.x, I.x, fma(dv.y, I.y, fma(v.x, ir, fma(v.y, ii, -F.x))));
         const double rQ = (__ldg(P.bus_type + i) == 0)
                               ? fma(dv.y, I.x, fma(-dv.x, I.y, fma(v.y, ir, fma(-v.x, ii, -F.y))))
                               : 0.0;
         const float xr = float(rP), xq = float(rQ);
-        __stcg(k.X + op, make_float2(xr, xq));
+        stm<CL>(k.X + op, make_float2(xr, xq));
         lmax = fmaxf(lmax, fmaxf(absinf(xr), absinf(xq)));
     }
     return abs_key(double(lmax));
 }
 
 // ---------------------------------------------------------------- update
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __device__ void si_update(const DevPlan& P, const Pack<FT>& k, int gs, int TS, int s, bool go) {
     if (!go) return;
     for (int i = gs; i < P.n_bus; i += TS) {
@@ -473,31 +494,31 @@ __device__ void si_update(const DevPlan& P, const Pack<FT>& k, int gs, int TS, i
         if (p < 0) continue;
         double dth, dvm;
         if constexpr (sizeof(FT) == 4) {  // the refined step, accumulated in FP64
-            const double2 dz = __ldcg(k.DZ + ((size_t)p * S + s));
+            const double2 dz = ldm<CL>(k.DZ + ((size_t)p * S + s));
             dth = dz.x;
             dvm = dz.y;
         } else {
-            const double2 x = __ldcg(k.X + ((size_t)p * S + s));
+            const double2 x = ldm<CL>(k.X + ((size_t)p * S + s));
             dth = x.x;
             dvm = x.y;
         }
         const size_t o = (size_t)i * S + s;
-        const double2 m = __ldcg(k.M + o);
+        const double2 m = ldm<CL>(k.M + o);
         const double th = m.y + dth;
         const double vm = (__ldg(P.bus_type + i) == 0) ? m.x + dvm : m.x;
         double c, sn;
         if (abs_key(dth) <= 0x3fc0000000000000ULL) {  // |dth| <= 1/8: rotate u (false for NaN)
             double rc, rs;
             small_angle_phasor(dth, &rc, &rs);
-            const double2 u = __ldcg(k.U + o);
+            const double2 u = ldm<CL>(k.U + o);
             c = u.x * rc - u.y * rs;
             sn = u.y * rc + u.x * rs;
         } else {
             sincos(th, &sn, &c);
         }
-        __stcg(k.M + o, make_double2(vm, th));
-        __stcg(k.U + o, make_double2(c, sn));
-        __stcg(k.V + o, make_double2(vm * c, vm * sn));
+        stm<CL>(k.M + o, make_double2(vm, th));
+        stm<CL>(k.U + o, make_double2(c, sn));
+        stm<CL>(k.V + o, make_double2(vm * c, vm * sn));
     }
 }
 
@@ -524,7 +545,7 @@ __device__ __forceinline__ Pack<FT> carve_pack(const SiArgs& A, unsigned pack) {
 }
 
 // ---------------------------------------------------------------- the kernel
-template <typename FT, int S>
+template <typename FT, int S, bool CL>
 __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_red[32];
@@ -542,30 +563,35 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
     // reduction slots and singular flags start at zero
     if (rank == 0 && threadIdx.x < 3 * 32) atomicExch(k.red + threadIdx.x, 0ull);
     if (rank == 0 && threadIdx.x < 32) atomicExch(k.sing + threadIdx.x, 0u);
-    // flat start (Sec. IV-A) and the specified injections, transposed into the pack
-    for (int i = gs; i < P.n_bus; i += TS) {
+    // flat start (Sec. IV-A) and the specified injections, transposed into the pack: the
+    // pack's input rows are read in row order (consecutive threads, consecutive buses of
+    // one scenario), so that every read is coalesced -- also when the inputs are in host
+    // memory and each transaction crosses the chip-to-chip link
+    const int nflat = S * P.n_bus;
+    for (int f = (int)(rank * blockDim.x + threadIdx.x); f < nflat; f += (int)(C * blockDim.x)) {
+        const int sf = f / P.n_bus, i = f - sf * P.n_bus, bf = (int)pack * S + sf;
         const int t = __ldg(P.bus_type + i);
         double vm = 1.0, psp = 0.0, qsp = 0.0;
-        if (valid) {
-            const size_t r = (size_t)b * P.n_bus + i;
+        if (bf < A.batch) {
+            const size_t r = (size_t)bf * P.n_bus + i;
             if (t != 0) vm = A.Vset[r];
             psp = (t == 1 ? A.Pg[r] : 0.0) - A.Pd[r];
             qsp = -A.Qd[r];
         }
-        const size_t o = (size_t)i * S + s;
-        __stcg(k.M + o, make_double2(vm, 0.0));
-        __stcg(k.U + o, make_double2(1.0, 0.0));
-        __stcg(k.V + o, make_double2(vm, 0.0));
-        __stcg(k.SP + o, make_double2(psp, qsp));
+        const size_t o = (size_t)i * S + sf;
+        stm<CL>(k.M + o, make_double2(vm, 0.0));
+        stm<CL>(k.U + o, make_double2(1.0, 0.0));
+        stm<CL>(k.V + o, make_double2(vm, 0.0));
+        stm<CL>(k.SP + o, make_double2(psp, qsp));
     }
-    cluster_sync();
+    pack_sync<CL>();
 
     int status = valid ? -1 : 4;  // -1: still iterating; 4: no scenario in this lane
     int it = 0;
     double norm = 0.0;
     for (;;) {
-        const unsigned long long km = si_mismatch<FT, S>(P, k, gs, TS, s, status < 0);
-        const double nrm = cluster_max<S>(km, k.red, round, s_red, rank);
+        const unsigned long long km = si_mismatch<FT, S, CL>(P, k, gs, TS, s, status < 0);
+        const double nrm = cluster_max<S, CL>(km, k.red, round, s_red, rank);
         if (status < 0) {
             norm = nrm;
             if (!(norm <= 1e10)) status = 2;
@@ -574,125 +600,137 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
         }
         if (lanes_where<S>(status < 0) == 0u) break;
         const bool go = status < 0;
-        si_fill<S>(P, k, gs, TS, s, go);
-        cluster_sync();
-        for (int l = 0; l < P.n_levels; ++l) si_lu_level<FT, S>(P, k, l, gs, TS, s, go);
-        if (go && __ldcg(k.sing + s) != 0u) status = 3;  // read after the last level's barrier
+        si_fill<S, CL>(P, k, gs, TS, s, go);
+        pack_sync<CL>();
+        for (int l = 0; l < P.n_levels; ++l) si_lu_level<FT, S, CL>(P, k, l, gs, TS, s, go);
+        // read after the last level's barrier, through L2 (the flags are set by atomics)
+        if (go && __ldcg(k.sing + s) != 0u) status = 3;
         const bool g2 = status < 0;
         if (lanes_where<S>(g2) == 0u) break;
-        si_solve<FT, S>(P, k, gs, TS, s, slot, NS, (int)rank, (int)C, g2, part);
+        si_solve<FT, S, CL>(P, k, gs, TS, s, slot, NS, (int)rank, (int)C, g2, part);
         if constexpr (mixed) {
-            si_accumulate<S>(P, k, gs, TS, s, g2, true);
-            cluster_sync();
+            si_accumulate<S, CL>(P, k, gs, TS, s, g2, true);
+            pack_sync<CL>();
             const int sweeps = (A.ir_gate > 0.0 && norm > A.ir_gate) ? 0 : A.ir_steps;
             bool refine = g2 && sweeps > 0;
             for (int sw = 0; lanes_where<S>(refine) != 0u; ++sw) {
-                const unsigned long long kr = si_residual<S>(P, k, gs, TS, s, refine);
-                const double rmax = cluster_max<S>(kr, k.red, round, s_red, rank);
+                const unsigned long long kr = si_residual<S, CL>(P, k, gs, TS, s, refine);
+                const double rmax = cluster_max<S, CL>(kr, k.red, round, s_red, rank);
                 // forcing term min(ir_rtol, ||F1||): see the per-scenario form
                 if (refine && A.ir_rtol > 0.0 && rmax <= fmin(A.ir_rtol, norm) * norm) refine = false;
                 if (lanes_where<S>(refine) == 0u) break;
-                si_solve<FT, S>(P, k, gs, TS, s, slot, NS, (int)rank, (int)C, refine, part);
-                si_accumulate<S>(P, k, gs, TS, s, refine, false);
-                cluster_sync();
+                si_solve<FT, S, CL>(P, k, gs, TS, s, slot, NS, (int)rank, (int)C, refine, part);
+                si_accumulate<S, CL>(P, k, gs, TS, s, refine, false);
+                pack_sync<CL>();
                 if (sw + 1 >= sweeps) refine = false;
             }
         }
-        si_update<FT, S>(P, k, gs, TS, s, g2);
-        cluster_sync();
+        si_update<FT, S, CL>(P, k, gs, TS, s, g2);
+        pack_sync<CL>();
         if (g2) ++it;
     }
 
     // Step 2 (Eq. F2_completion) and outputs, from the state of each scenario's last
-    // mismatch evaluation
-    if (valid) {
-        for (int i = gs; i < P.n_bus; i += TS) {
-            const size_t o = (size_t)i * S + s, r = (size_t)b * P.n_bus + i;
-            const int t = __ldg(P.bus_type + i);
-            const double2 m = __ldcg(k.M + o), v = __ldcg(k.V + o), I = __ldcg(k.I + o);
-            A.Vm[r] = m.x;
-            A.Va[r] = m.y;
-            if (A.Pg_out) A.Pg_out[r] = (t == 1) ? A.Pg[r] : (t == 2 ? v.x * I.x + v.y * I.y + A.Pd[r] : 0.0);
-            if (A.Qg_out) A.Qg_out[r] = (t == 0) ? 0.0 : (v.y * I.x - v.x * I.y) + A.Qd[r];
-        }
-        if (rank == 0 && slot == 0) {
-            A.status[b] = status;
-            if (A.iters) A.iters[b] = it;
-            if (A.fmis) A.fmis[b] = norm;
-        }
+    // mismatch evaluation; written in row order, like the inputs were read
+    for (int f = (int)(rank * blockDim.x + threadIdx.x); f < nflat; f += (int)(C * blockDim.x)) {
+        const int sf = f / P.n_bus, i = f - sf * P.n_bus, bf = (int)pack * S + sf;
+        if (bf >= A.batch) continue;
+        const size_t o = (size_t)i * S + sf, r = (size_t)bf * P.n_bus + i;
+        const int t = __ldg(P.bus_type + i);
+        const double2 m = ldm<CL>(k.M + o), v = ldm<CL>(k.V + o), I = ldm<CL>(k.I + o);
+        A.Vm[r] = m.x;
+        A.Va[r] = m.y;
+        if (A.Pg_out) A.Pg_out[r] = (t == 1) ? A.Pg[r] : (t == 2 ? v.x * I.x + v.y * I.y + A.Pd[r] : 0.0);
+        if (A.Qg_out) A.Qg_out[r] = (t == 0) ? 0.0 : (v.y * I.x - v.x * I.y) + A.Qd[r];
+    }
+    if (valid && rank == 0 && slot == 0) {
+        A.status[b] = status;
+        if (A.iters) A.iters[b] = it;
+        if (A.fmis) A.fmis[b] = norm;
     }
 }
 
 }  // namespace si
 
 // ---------------------------------------------------------------- launch
-template <typename FT, int S>
-static cudaError_t prepare(const void** fn) {
-    auto kfn = si::nr_solve_si_kernel<FT, S>;
-    *fn = reinterpret_cast<const void*>(kfn);
+// One CTA per pack (cluster 1) runs the single-CTA instantiation: CTA barriers, no cluster
+// launch attribute.
+template <typename FT, int S, bool CL>
+static cudaError_t prepare() {
     static std::mutex mu;
     static std::map<int, bool> done;  // per device: the non-portable cluster size allowed
+    if (!CL) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(si::nr_solve_si_kernel<FT, S, CL>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-template <typename FT, int S>
-static cudaError_t launch_s(const DevPlan& P, const SiArgs& A, cudaStream_t st) {
-    const void* fn = nullptr;
-    cudaError_t e = prepare<FT, S>(&fn);
-    if (e != cudaSuccess) return e;
-    const int packs = (A.batch + S - 1) / S;
+template <typename FT, int S, bool CL>
+static cudaLaunchConfig_t si_config(int grid, int cluster, int threads, size_t smem,
+                                    cudaStream_t st, cudaLaunchAttribute* at) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(packs * A.L.cluster), 1, 1);
-    cfg.blockDim = dim3((unsigned)A.L.threads, 1, 1);
-    cfg.dynamicSmemBytes = A.L.smem_bytes;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)A.L.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, si::nr_solve_si_kernel<FT, S>, P, A);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-}
-
-template <typename FT>
-cudaError_t launch_solve_si(const DevPlan& P, const SiArgs& A, cudaStream_t s) {
-    switch (A.L.S) {
-        case 8: return launch_s<FT, 8>(P, A, s);
-        case 16: return launch_s<FT, 16>(P, A, s);
-        case 32: return launch_s<FT, 32>(P, A, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename FT, int S>
-static cudaError_t fits_s(int cluster, int threads, size_t smem, bool* fits) {
-    const void* fn = nullptr;
-    cudaError_t e = prepare<FT, S>(&fn);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cluster, 1, 1);
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute at[1];
+    cfg.stream = st;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = CL ? 1 : 0;
+    return cfg;
+}
+
+template <typename FT, int S, bool CL>
+static cudaError_t launch_s(const DevPlan& P, const SiArgs& A, cudaStream_t st) {
+    cudaError_t e = prepare<FT, S, CL>();
+    if (e != cudaSuccess) return e;
+    const int packs = (A.batch + S - 1) / S;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = si_config<FT, S, CL>(packs * A.L.cluster, A.L.cluster,
+                                                        A.L.threads, A.L.smem_bytes, st, at);
+    e = cudaLaunchKernelEx(&cfg, si::nr_solve_si_kernel<FT, S, CL>, P, A);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <typename FT, int S>
+static cudaError_t launch_c(const DevPlan& P, const SiArgs& A, cudaStream_t st) {
+    return A.L.cluster > 1 ? launch_s<FT, S, true>(P, A, st) : launch_s<FT, S, false>(P, A, st);
+}
+
+template <typename FT>
+cudaError_t launch_solve_si(const DevPlan& P, const SiArgs& A, cudaStream_t s) {
+    switch (A.L.S) {
+        case 2: return launch_c<FT, 2>(P, A, s);
+        case 4: return launch_c<FT, 4>(P, A, s);
+        case 8: return launch_c<FT, 8>(P, A, s);
+        case 16: return launch_c<FT, 16>(P, A, s);
+        case 32: return launch_c<FT, 32>(P, A, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename FT, int S, bool CL>
+static cudaError_t fits_s(int cluster, int threads, size_t smem, bool* fits) {
+    cudaError_t e = prepare<FT, S, CL>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = si_config<FT, S, CL>(cluster, cluster, threads, smem, 0, at);
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, si::nr_solve_si_kernel<FT, S>, &cfg);
+    if (CL) {
+        e = cudaOccupancyMaxActiveClusters(&n, si::nr_solve_si_kernel<FT, S, CL>, &cfg);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, si::nr_solve_si_kernel<FT, S, CL>,
+                                                          threads, smem);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();  // a refused shape is an answer, not an error
         *fits = false;
@@ -702,15 +740,44 @@ static cudaError_t fits_s(int cluster, int threads, size_t smem, bool* fits) {
     return cudaSuccess;
 }
 
+template <typename FT, int S>
+static cudaError_t fits_c(int cluster, int threads, size_t smem, bool* fits) {
+    return cluster > 1 ? fits_s<FT, S, true>(cluster, threads, smem, fits)
+                       : fits_s<FT, S, false>(cluster, threads, smem, fits);
+}
+
+// The answer is kept per (device, shape), so that only a shape's first solve queries the
+// occupancy API (later calls may be recorded into a CUDA graph).
 template <typename FT>
 cudaError_t si_shape_fits(int S, int cluster, int threads, size_t smem, bool* fits) {
     *fits = false;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, size_t>, bool> known;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(dev, S, cluster, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = known.find(key);
+        if (it != known.end()) {
+            *fits = it->second;
+            return cudaSuccess;
+        }
+    }
     switch (S) {
-        case 8: return fits_s<FT, 8>(cluster, threads, smem, fits);
-        case 16: return fits_s<FT, 16>(cluster, threads, smem, fits);
-        case 32: return fits_s<FT, 32>(cluster, threads, smem, fits);
+        case 2: e = fits_c<FT, 2>(cluster, threads, smem, fits); break;
+        case 4: e = fits_c<FT, 4>(cluster, threads, smem, fits); break;
+        case 8: e = fits_c<FT, 8>(cluster, threads, smem, fits); break;
+        case 16: e = fits_c<FT, 16>(cluster, threads, smem, fits); break;
+        case 32: e = fits_c<FT, 32>(cluster, threads, smem, fits); break;
         default: return cudaErrorInvalidValue;
     }
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(mu);
+        known[key] = *fits;
+    }
+    return e;
 }
 
 template cudaError_t launch_solve_si<float>(const DevPlan&, const SiArgs&, cudaStream_t);

@@ -241,7 +241,10 @@ class PowerFlow:
                 raise ValueError(f"{nm} must be page-locked (pin_memory()) or on the device")
         opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
                               instances_per_cta, ir_gate)
-        ws = self.workspace(batch, opts)
+        # a per-scenario placement serves host buffers unless interleaved packs are asked for
+        ws = self.workspace(batch, opts if placement == L.PF_PLACE_INTERLEAVED else
+                            self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors,
+                                           L.PF_PLACE_GLOBAL))
         if out is None:
             e = dict(dtype=torch.float64, pin_memory=True)
             out = SolveResult(
@@ -395,7 +398,7 @@ class PowerFlow:
         need = [self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors, L.PF_PLACE_GLOBAL)]
         if not keep_factors:
             need += [self.make_opts(precision, ir_steps, ir_rtol, 1024, False,
-                                    L.PF_PLACE_INTERLEAVED, 0, ir_gate, S, 16) for S in (8, 16, 32)]
+                                    L.PF_PLACE_INTERLEAVED, 0, ir_gate, S, 16) for S in (2, 4, 8, 16, 32)]
         ws = self.workspace(batch, max(need, key=lambda o: self.workspace_bytes(batch, o)))
         res = L.TuneResult()
         stream = torch.cuda.current_stream(Pd.device).cuda_stream

@@ -132,15 +132,24 @@ def test_autotune_keeps_results(PowerFlow):
     import torch
     g, sc = workload("c1", 512)
     pf = PowerFlow.from_grid(g)
-    ref = run_gpu(pf, sc, precision="mixed", group_threads=128, placement=1)
     best = pf.autotune(*to_dev(sc), precision="mixed")
     assert best["group_threads"] in (32, 64, 128, 256, 512, 1024)
-    assert best["placement"] in (1, 2, 3, 4) and best["ms"] > 0
+    assert best["placement"] in (1, 2, 3, 4, 5) and best["ms"] > 0
     assert best["instances_per_cta"] in (1, 2, 4, 8)
+    # the shape it picked, given explicitly
+    ref = run_gpu(pf, sc, precision="mixed", group_threads=best["group_threads"],
+                  placement=best["placement"], instances_per_cta=best["instances_per_cta"],
+                  pack=best["pack"], cluster=best["cluster"])
     out = run_gpu(pf, sc, precision="mixed")  # now uses the tuned configuration
     torch.cuda.synchronize()
     for k in ref:
         assert np.array_equal(ref[k], out[k]), k
+    # a solve with kept factors (which the interleaved placement does not produce) still
+    # runs, on the fastest per-scenario shape of the same tuning, and matches a fixed shape
+    keep = run_gpu(pf, sc, precision="mixed", keep_factors=True)
+    fixed = run_gpu(pf, sc, precision="mixed", group_threads=128, placement=1)
+    for k in fixed:
+        assert np.array_equal(keep[k], fixed[k]), k
 
 
 def test_solve_captured_in_cuda_graph(PowerFlow):
