@@ -204,7 +204,9 @@ __device__ unsigned long long si_mismatch(const DevPlan& P, const Pack<FT>& k, i
 template <int S, bool CL>
 __device__ void si_fill(const DevPlan& P, const Pack<float>& k, int gs, int TS, int s, bool go) {
     if (!go) return;
-    for (int e = gs; e < P.nnzb; e += TS) {
+    // two blocks per slot and round, both blocks' loads before either store (the stores to
+    // the factor could otherwise alias the next block's bus reads for the compiler)
+    auto block = [&](int e) {
         const int p = __ldg(P.lu_row + e), q = __ldg(P.lu_col + e), yi = __ldg(P.fill_y + e);
         const int i = __ldg(P.pos2bus + p), j = __ldg(P.pos2bus + q);
         Blk<float> m{0.f, 0.f, 0.f, 0.f};
@@ -214,7 +216,14 @@ __device__ void si_fill(const DevPlan& P, const Pack<float>& k, int gs, int TS, 
             const float4 aj = ldm<CL>(k.FA + ((size_t)j * S + s)), bj = ldm<CL>(k.FB + ((size_t)j * S + s));
             m = jac_block<float>(p == q, y.x, y.y, ai.x, ai.y, aj.z, aj.w, bj.x, bi.x, bi.y, bi.z);
         }
-        stf<S, CL>(k.fac, e, s, pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j)));
+        return pad_pv(m, p == q, __ldg(P.bus_type + i), __ldg(P.bus_type + j));
+    };
+    for (int e = gs; e < P.nnzb; e += 2 * TS) {
+        const int e2 = e + TS;
+        const bool two = e2 < P.nnzb;
+        const Blk<float> m1 = block(e), m2 = block(two ? e2 : e);
+        stf<S, CL>(k.fac, e, s, m1);
+        if (two) stf<S, CL>(k.fac, e2, s, m2);
     }
     for (int p = gs; p < P.n; p += TS) {
         const double2 f = ldm<CL>(k.F + ((size_t)p * S + s));
@@ -277,12 +286,95 @@ __device__ __forceinline__ Blk<FT> si_schur(const DevPlan& P, const FT* fac, int
     return acc;
 }
 
-// One elimination level: the L-column scalings (phase A), a cluster barrier, then the
-// level's Schur targets and pivot inversions (phase B) as one item space, and a cluster
-// barrier.  A singular pivot raises the lane's flag in the pack's `sing` array.
+// Two targets' sums interleaved (A over ca..ea, B over cb..eb), half a batch of each per
+// round so that both chains of loads are in flight at once; each target still sums its
+// pairs in order from zero, as si_schur does.
+template <typename FT, int S, bool CL>
+__device__ __forceinline__ void si_schur2(const DevPlan& P, const FT* fac, int ca, int ea, int cb,
+                                          int eb, int s, Blk<FT>& A, Blk<FT>& B) {
+    constexpr int NB = kBatch<FT> / 2 > 0 ? kBatch<FT> / 2 : 1;
+    const Blk<FT> z{FT(0), FT(0), FT(0), FT(0)};
+    A = z;
+    B = z;
+    for (; ca < ea || cb < eb; ca += NB, cb += NB) {
+        int2 la[NB], lb[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            la[q] = (ca + q < ea) ? __ldg(P.sch + ca + q) : make_int2(-1, -1);
+            lb[q] = (cb + q < eb) ? __ldg(P.sch + cb + q) : make_int2(-1, -1);
+        }
+        Blk<FT> xa[NB], ya[NB], xb[NB], yb[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            xa[q] = la[q].x >= 0 ? ldf<S, CL>(fac, la[q].x, s) : z;
+            ya[q] = la[q].x >= 0 ? ldf<S, CL>(fac, la[q].y, s) : z;
+            xb[q] = lb[q].x >= 0 ? ldf<S, CL>(fac, lb[q].x, s) : z;
+            yb[q] = lb[q].x >= 0 ? ldf<S, CL>(fac, lb[q].y, s) : z;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            A.a += xa[q].a * ya[q].a + xa[q].b * ya[q].c;
+            A.b += xa[q].a * ya[q].b + xa[q].b * ya[q].d;
+            A.c += xa[q].c * ya[q].a + xa[q].d * ya[q].c;
+            A.d += xa[q].c * ya[q].b + xa[q].d * ya[q].d;
+            B.a += xb[q].a * yb[q].a + xb[q].b * yb[q].c;
+            B.b += xb[q].a * yb[q].b + xb[q].b * yb[q].d;
+            B.c += xb[q].c * yb[q].a + xb[q].d * yb[q].c;
+            B.d += xb[q].c * yb[q].b + xb[q].d * yb[q].d;
+        }
+    }
+}
+
+// One elimination level: the L-column scalings (phase A), a pack barrier, then the
+// level's Schur targets and pivot inversions (phase B), and a pack barrier.  With the
+// FP32 factor each slot takes two items per round (their loads in flight together;
+// within a level the pivots read, the L blocks scaled and the targets written are
+// disjoint).  A singular pivot raises the lane's flag in the pack's `sing` array.
 template <typename FT, int S, bool CL>
 __device__ void si_lu_level(const DevPlan& P, const Pack<FT>& k, int l, int gs, int TS, int s,
                             bool go) {
+    if constexpr (sizeof(FT) == 4) {
+        if (go) {
+            const int a1 = __ldg(P.la_ptr + l + 1);
+            for (int c = __ldg(P.la_ptr + l) + gs; c < a1; c += 2 * TS) {
+                const bool two = c + TS < a1;
+                const int2 ld = __ldg(P.la + c), ld2 = two ? __ldg(P.la + c + TS) : ld;
+                int dummy = 0;
+                const Blk<FT> m1 = ldf<S, CL>(k.fac, ld.x, s), q1 = ldf<S, CL>(k.fac, ld.y, s);
+                const Blk<FT> m2 = ldf<S, CL>(k.fac, ld2.x, s), q2 = ldf<S, CL>(k.fac, ld2.y, s);
+                stf<S, CL>(k.fac, ld.x, s, mul(m1, inv2(q1, &dummy)));
+                if (two) stf<S, CL>(k.fac, ld2.x, s, mul(m2, inv2(q2, &dummy)));
+            }
+        }
+        pack_sync<CL>();
+        if (go) {
+            const int t0 = __ldg(P.sch_tptr + l), t1 = __ldg(P.sch_tptr + l + 1);
+            for (int t = t0 + gs; t < t1; t += 2 * TS) {
+                const int t2 = t + TS;
+                const bool two = t2 < t1;
+                Blk<FT> acc, acc2;
+                si_schur2<FT, S, CL>(P, k.fac, __ldg(P.sch_cptr + t), __ldg(P.sch_cptr + t + 1),
+                                     two ? __ldg(P.sch_cptr + t2) : 0,
+                                     two ? __ldg(P.sch_cptr + t2 + 1) : 0, s, acc, acc2);
+                const int tg = __ldg(P.sch_tgt + t), tg2 = two ? __ldg(P.sch_tgt + t2) : tg;
+                const Blk<FT> o1 = ldf<S, CL>(k.fac, tg, s), o2 = ldf<S, CL>(k.fac, tg2, s);
+                stf<S, CL>(k.fac, tg, s, sub_blk(o1, acc));
+                if (two) stf<S, CL>(k.fac, tg2, s, sub_blk(o2, acc2));
+            }
+            int bad = 0;
+            const int r1 = __ldg(P.lev_ptr + l + 1);
+            for (int p = __ldg(P.lev_ptr + l) + gs; p < r1; p += 2 * TS) {
+                const bool two = p + TS < r1;
+                const int dk = __ldg(P.lu_diag + p), dk2 = two ? __ldg(P.lu_diag + p + TS) : dk;
+                const Blk<FT> d1 = ldf<S, CL>(k.fac, dk, s), d2 = ldf<S, CL>(k.fac, dk2, s);
+                stf<S, CL>(k.fac, dk, s, inv2(d1, &bad));
+                if (two) stf<S, CL>(k.fac, dk2, s, inv2(d2, &bad));
+            }
+            if (bad) atomicOr(k.sing + s, 1u);
+        }
+        pack_sync<CL>();
+        return;
+    }
     if (go) {
         const int a1 = __ldg(P.la_ptr + l + 1);
         for (int c = __ldg(P.la_ptr + l) + gs; c < a1; c += TS) {
