@@ -283,14 +283,15 @@ def alg_counts(info: dict, n_bus: int, iters: np.ndarray, ir_steps: int, precisi
     return f64, f32, hbm
 
 
-def rank_scenarios(workload, g, rank, world):
-    """This rank's scenarios.  One GPU solves the workload's batch; with N ranks, rank r
-    solves the r-th of N equal batches drawn from one seeded stream, so every rank does
-    the same amount of distinct work (weak scaling, no collective on the data path)."""
+def rank_scenarios(workload, g, rank, world, batch=0):
+    """This rank's scenarios.  One GPU solves the workload's batch (or its first `batch`
+    scenarios); with N ranks, rank r solves the r-th of N equal batches drawn from one
+    seeded stream, so every rank does the same amount of distinct work (weak scaling, no
+    collective on the data path)."""
     from synthgrid import Scenarios, configs
     if world == 1:
-        return configs.scenarios(workload, g=g)
-    n = configs.CONFIGS[workload]["n_scen"]
+        return configs.scenarios(workload, batch or None, g=g)
+    n = batch or configs.CONFIGS[workload]["n_scen"]
     sc = configs.scenarios(workload, n * world, g)
     part = slice(rank * n, (rank + 1) * n)
     return Scenarios(Pd=sc.Pd[part].copy(), Qd=sc.Qd[part].copy(), Pg=sc.Pg[part].copy(),
@@ -321,7 +322,7 @@ def gpu_leg(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     g = configs.grid(args.workload)
-    sc = rank_scenarios(args.workload, g, rank, world)
+    sc = rank_scenarios(args.workload, g, rank, world, args.batch)
     N, nb = sc.n, g.n_bus
     pf = PowerFlow.from_grid(g)
     info = pf.info()
@@ -503,8 +504,9 @@ def gpu_leg(args, rank, world):
     if "sweep" in secs:  # solve time vs batch size on the large grids (the shape of Table II)
         for sname, sizes in (("c1", (256, 1024, 2048, 4096)), ("c2", (4, 16, 64, 256, 1024)),
                              ("c3", (4, 16, 64, 256)), ("c5", (4, 16, 64, 256))):
-            if sname == "c1":  # the headline network (its handle is tuned already)
-                gs_, scs_, pfs_ = g, sc, pf
+            if sname == "c1":  # the headline network, on a handle of its own (the sweep
+                # retunes the launch shape at every batch size)
+                gs_, scs_, pfs_ = g, sc, PowerFlow.from_grid(g)
             elif sname in large:
                 gs_, scs_, pfs_ = large[sname][0], large[sname][1], large[sname][2]
             else:
@@ -630,8 +632,7 @@ def gpu_leg(args, rank, world):
                     o_ = dict(opts, precision=prec_)
                     # launch shape for this batch size (a few scenarios of a large grid
                     # want more threads each than a full batch does); setup, not timed
-                    shape_ = (pfs_.autotune(*sub, **o_) if args.autotune and sname != "c1"
-                              else None)
+                    shape_ = pfs_.autotune(*sub, **o_) if args.autotune else None
                     r_ = pfs_.solve(*sub, **o_)
                     tn = timed(lambda: pfs_.solve(*sub, out=r_, **o_), 5, 3, f"sweep_{sname}_{n_}_{prec_}")
                     ms_ = statistics.median(tn)
@@ -767,9 +768,9 @@ def gpu_leg(args, rank, world):
                 for k in ("Vm", "Va", "Pg", "Qg", "iters", "status")}
     par_in = {}
     if world == 1:
-        par_in["c1"] = {"idx": list(range(N)), "mixed": arrays(res)}
+        par_in[args.workload] = {"idx": list(range(N)), "mixed": arrays(res)}
         if "fp64" in secs:
-            par_in["c1"]["fp64"] = arrays(res64)
+            par_in[args.workload]["fp64"] = arrays(res64)
         samples = {"c2": 32, "c3": 16, "c5": 8}
         for pname, (pfx, inx, rx) in (
                 [("c2", (pf2, in2, res2))] if "layer_c2" in secs else []) + [
@@ -879,6 +880,8 @@ def main():
     ap.add_argument("--sections", default="mixed,fp64,fwdbwd,layer_c2,e2e,multi_c4,c3,c5,qlim,jacobian,memory,bde,sweep,train",
                     help="timed sections to run (the first one, mixed, always runs)")
     ap.add_argument("--workload", default="c1", help="synthgrid workload (c1 is the bench line)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="scenarios per GPU for the headline section (0 = the workload's batch)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -948,7 +951,8 @@ def main():
                 line["parity"] = parity
             line["cpu_baseline"] = {"value": conv / dt, "unit": UNIT, "cores": pool.procs,
                                     "kind": "oracle", "single_core_value": conv1 / dt1,
-                                    "sample": f"first {n_c} of the 4096 scenarios ({dt:.1f} s "
+                                    "sample": f"first {n_c} of the {line['config']['batch_per_gpu']} "
+                                              f"scenarios ({dt:.1f} s "
                                               f"wall); single core: first {n1}",
                                     "cpu": cpu_model()}
         print(json.dumps(ordered(line)), flush=True)

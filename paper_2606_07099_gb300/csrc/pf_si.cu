@@ -1,5 +1,5 @@
 // pf_si.cu -- the Newton-Raphson solve on scenario-interleaved packs, one thread-block
-// cluster per pack (placement PF_PLACE_INTERLEAVED; sm_103a).
+// cluster (or one CTA) per pack (placement PF_PLACE_INTERLEAVED; sm_103a).
 //
 // The per-scenario form (pf_body.cuh) gives each scenario one CTA.  On large networks
 // (thousands of buses) that leaves every elimination-level step of the factorisation
@@ -14,7 +14,8 @@
 // (and the levels inside the factorisation and the sweeps) are separated by hardware
 // cluster barriers.  Data written by one CTA and read by another goes through L2 only
 // (ld.global.cg / st.global.cg): the barrier's release/acquire orders it, and no SM keeps
-// a stale L1 copy.
+// a stale L1 copy.  With C = 1 a pack is one CTA: CTA barriers and plain (L1-cached)
+// loads, the shape that suits small networks with many scenarios.
 //
 // The arithmetic is that of the per-scenario form: FP64 mismatch, update, residual and
 // convergence test; the factor and the sweeps in FT (float: the mixed form, refined by
