@@ -357,7 +357,15 @@ def gpu_leg(args, rank, world):
     # the largest workspace any section needs, allocated once (captured graphs keep its address)
     pf.workspace(N, pf.make_opts("fp64", keep_factors=True, placement=3))
     tuned = {}
-    if args.autotune:  # launch shape per precision, picked on these inputs (setup, not timed)
+    hopts = dict(opts)  # the headline solve's options
+    if args.shape:  # an explicit launch shape for the headline solve (no tuning for it)
+        pl, th, pk, cl = (int(v) for v in args.shape.split(","))
+        hopts.update(placement=pl, group_threads=th, pack=pk, cluster=cl)
+        tuned["mixed"] = {"group_threads": th, "placement": pl, "instances_per_cta": 1,
+                          "pack": pk, "cluster": cl, "fixed": True}
+        if args.autotune and "fp64" in secs:
+            tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
+    elif args.autotune:  # launch shape per precision, picked on these inputs (setup, not timed)
         tuned["mixed"] = pf.autotune(Pd, Qd, Pg, Vset, **opts)
         if "fp64" in secs:
             tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
@@ -373,8 +381,8 @@ def gpu_leg(args, rank, world):
             fn()
         return gr.replay
 
-    res = pf.solve(Pd, Qd, Pg, Vset, **opts)
-    mixed_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **opts))
+    res = pf.solve(Pd, Qd, Pg, Vset, **hopts)
+    mixed_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **hopts))
     if "fp64" in secs:
         res64 = pf.solve(Pd, Qd, Pg, Vset, precision="fp64")
         fp64_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64))
@@ -874,6 +882,9 @@ def main():
     ap.add_argument("--ir-gate", type=float, default=1e-2,
                     help="check/refine Newton steps only once ||F1||_inf <= this (0 = all)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--shape", default="",
+                    help="placement,threads,pack,cluster of the headline solve instead of the "
+                         "autotuned one (e.g. 3,32,0,0: per-scenario, 32 threads, global)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
