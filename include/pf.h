@@ -377,8 +377,8 @@ pf_err pf_adjoint_qlim(pf_handle* h, int batch,
  * threads per scenario, or 2, 4 or 8 one-warp scenarios per CTA, times every placement
  * that fits; and, without keep_factors, interleaved packs: 2 to 32 scenarios on one CTA
  * of 256, 512 or 1024 threads, or 4 to 16 scenarios on clusters of 2 to 16 CTAs of 512 or
- * 1024 threads, the shapes that occupy at least half of the SMs and whose workspace fits
- * the one given (the best shape depends on the batch: a few scenarios of a large network
+ * 1024 threads, the shapes that occupy at least half of the SMs (or use 16-CTA clusters)
+ * and whose workspace fits the one given (the best shape depends on the batch: a few scenarios of a large network
  * want the most threads each, thousands of small ones the most scenarios per SM).  The fastest one is kept in
  * the handle and used by later pf_solve calls with group_threads = 0 and placement =
  * PF_PLACE_AUTO at the same precision; *out (nullable) receives it.  The workspace

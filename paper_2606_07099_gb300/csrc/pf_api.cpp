@@ -963,7 +963,9 @@ pf_err pf_autotune(pf_handle* h, int batch, const double* Pd, const double* Qd, 
             if (S >= 2 * batch && S > 2) continue;  // packs mostly empty
             for (int cl : {1, 2, 4, 8, 16}) {
                 if (cl > 1 && (S < 4 || S > 16)) continue;
-                if ((long long)((batch + S - 1) / S) * cl < h->num_sms / 2) continue;  // too few SMs
+                // too few SMs for the batch, unless no larger cluster is left to try (a few
+                // scenarios of a large network: one pack on the largest cluster)
+                if ((long long)((batch + S - 1) / S) * cl < h->num_sms / 2 && cl < 16) continue;
                 for (int th : {256, 512, 1024}) {
                     if (cl > 1 && th < 512) continue;
                     const LaunchCfg c{th, PF_PLACE_INTERLEAVED, 1, S, cl};
