@@ -226,7 +226,7 @@ class PowerFlow:
     def solve_host(self, Pd, Qd, Pg, Vset, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2,
                    ir_rtol=1e-3, group_threads=0, keep_factors=False,
                    out: SolveResult | None = None, placement=0, instances_per_cta=0,
-                   ir_gate=0.0) -> SolveResult:
+                   ir_gate=0.0, pack=0, cluster=0) -> SolveResult:
         """pf_solve_host: the solve reading its inputs from, and writing its outputs to,
         page-locked host tensors (``pin_memory()``) in place; device tensors are accepted
         too.  The outputs (page-locked host tensors unless ``out`` is given) are complete
@@ -240,7 +240,7 @@ class PowerFlow:
             if not v.is_cuda and not v.is_pinned():
                 raise ValueError(f"{nm} must be page-locked (pin_memory()) or on the device")
         opts = self.make_opts(precision, ir_steps, ir_rtol, group_threads, keep_factors, placement,
-                              instances_per_cta, ir_gate)
+                              instances_per_cta, ir_gate, pack, cluster)
         # a per-scenario placement serves host buffers unless interleaved packs are asked for
         ws = self.workspace(batch, opts if placement == L.PF_PLACE_INTERLEAVED else
                             self.make_opts(precision, ir_steps, ir_rtol, 0, keep_factors,
