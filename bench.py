@@ -354,9 +354,12 @@ def gpu_leg(args, rank, world):
 
     opts = dict(precision="mixed", ir_steps=args.ir_steps, ir_rtol=args.ir_rtol, ir_gate=args.ir_gate)
     secs = set(args.sections.split(","))
+    tuned = {}
+    from paper_2606_07099_gb300.powerflow import autotune_schedule
+    # the headline network keeps the default plan schedule: the schedule tuner found no
+    # faster one for its mixed solve, and its choice can slow the host-buffer path
     # the largest workspace any section needs, allocated once (captured graphs keep its address)
     pf.workspace(N, pf.make_opts("fp64", keep_factors=True, placement=3))
-    tuned = {}
     hopts = dict(opts)  # the headline solve's options
     if args.shape:  # an explicit launch shape for the headline solve (no tuning for it)
         pl, th, pk, cl = (int(v) for v in args.shape.split(","))
@@ -415,19 +418,27 @@ def gpu_leg(args, rank, world):
 
     if "multi_c4" in secs:  # uneven batch: 30/300/2000-bus networks in one persistent launch
         from paper_2606_07099_gb300.powerflow import solve_multi
-        items4, slacks4 = [], []
+        grids4, inputs4, slacks4 = [], [], []
         for name in ("c4a", "c4b", "c4c"):
             g4 = configs.grid(name)
             sc4 = configs.scenarios(name, g=g4)
-            items4.append((PowerFlow.from_grid(g4),
-                           *[torch.as_tensor(np.ascontiguousarray(a), device=dev)
-                             for a in (sc4.Pd, sc4.Qd, sc4.Pg, sc4.Vset)]))
+            grids4.append(g4)
+            inputs4.append([torch.as_tensor(np.ascontiguousarray(a), device=dev)
+                            for a in (sc4.Pd, sc4.Qd, sc4.Pg, sc4.Vset)])
             slacks4.append(torch.as_tensor(g4.bus_type == 2, device=dev))
+        # each network's plan schedule and the single launch's shape (pf_autotune_multi:
+        # threads per CTA x per-network forms or all-global placement), on these inputs
+        # (setup, not timed)
+        from paper_2606_07099_gb300.powerflow import (autotune_multi_schedule,
+                                                      multi_workspace_bytes)
+        if args.autotune:
+            pfs4, rep4 = autotune_multi_schedule(grids4, inputs4, keep_factors=True, **opts)
+            tuned["multi_c4"] = {**rep4["shape"], "schedules": rep4["schedules"]}
+        else:
+            pfs4 = [PowerFlow.from_grid(g4) for g4 in grids4]
+            tuned["multi_c4"] = {"group_threads": 256, "placement": 0}
+        items4 = [(p4, *in4) for p4, in4 in zip(pfs4, inputs4)]
         n4 = sum(it[1].shape[0] for it in items4)
-        # launch shape of the single launch: pf_autotune_multi (threads per CTA x per-network
-        # forms or all-global placement), on these inputs (setup, not timed)
-        from paper_2606_07099_gb300.powerflow import autotune_multi, multi_workspace_bytes
-        tuned["multi_c4"] = autotune_multi(items4, keep_factors=True, **opts)
         shape4 = dict(group_threads=tuned["multi_c4"]["group_threads"],
                       placement=tuned["multi_c4"]["placement"])
         # preallocated results, gradients and workspace: the captured steps allocate nothing
@@ -457,13 +468,15 @@ def gpu_leg(args, rank, world):
             continue
         gl = configs.grid(lname)
         scl = configs.scenarios(lname, g=gl)
-        pfl = PowerFlow.from_grid(gl)
         inl = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in (scl.Pd, scl.Qd, scl.Pg, scl.Vset)]
+        if args.autotune:  # plan schedule and launch shape, picked on these inputs
+            pfl, rep = autotune_schedule(gl, *inl, **opts)
+            tuned[lname] = {**rep["shape"], "schedule": rep["schedule"]}
+        else:
+            pfl = PowerFlow.from_grid(gl)
         # sized for the FP64 form too (the parity block solves it once, after the timing;
         # captured graphs keep this buffer's address)
         pfl.workspace(scl.n, pfl.make_opts("fp64", placement=3))
-        if args.autotune:
-            tuned[lname] = pfl.autotune(*inl, **opts)
         resl = pfl.solve(*inl, **opts)
         # the tuple keeps the inputs alive: a captured graph holds only their addresses
         large[lname] = (gl, scl, pfl, resl,

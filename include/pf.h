@@ -172,6 +172,38 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices,
                  pf_handle** out);
 
 /*
+ * The schedule choices of a plan (Sec. III-B's one-time analysis leaves them free; none
+ * changes what is computed, only the elimination order, the level schedule and how the
+ * levels' work is split, hence rounding and speed):
+ *   order_slack: the fill-reducing minimum-degree ordering breaks ties, and near-ties up
+ *     to this degree slack, towards a shallower elimination tree (0 = ties only);
+ *   dense_max: the longest dense tail (trailing single-row levels whose block is full)
+ *     factored and swept densely in shared memory, in blocks, 0..32 (0 = none; values
+ *     above 32 act as 32); tails shorter than 3 blocks are not used;
+ *   split_len, split_rows: on levels of at most split_rows rows, a gathered row longer
+ *     than split_len blocks is split over a power-of-two group of lanes (about four
+ *     blocks each, at most 32 lanes), reduced in a fixed order.
+ * pf_plan_opts_default writes the defaults pf_create uses (1, 32, 8, 128).
+ */
+typedef struct {
+    int order_slack;
+    int dense_max;
+    int split_len;
+    int split_rows;
+} pf_plan_opts;
+
+void pf_plan_opts_default(pf_plan_opts* opts);
+
+/*
+ * pf_create_ex -- pf_create with explicit schedule choices (host, NULL = the defaults).
+ * Errors: as pf_create, and PF_EINVAL for order_slack outside 0..8, a negative dense_max
+ * or split_rows, or split_len < 1.
+ */
+pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices,
+                    const double* y_re, const double* y_im, const int* bus_type,
+                    const pf_plan_opts* plan_opts, pf_handle** out);
+
+/*
  * pf_analyze -- the host half of pf_create without any device work: validates the
  * network and runs the symbolic analysis, then reports the plan.  Inputs as in
  * pf_create (host).  If pos2bus / lu_ptr / lu_col / lev_ptr are non-NULL they

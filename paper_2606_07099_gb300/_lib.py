@@ -36,6 +36,11 @@ class SolveOpts(C.Structure):
                 ("cluster", C.c_int)]
 
 
+class PlanOpts(C.Structure):
+    _fields_ = [("order_slack", C.c_int), ("dense_max", C.c_int), ("split_len", C.c_int),
+                ("split_rows", C.c_int)]
+
+
 class TuneResult(C.Structure):
     _fields_ = [("group_threads", C.c_int), ("placement", C.c_int),
                 ("instances_per_cta", C.c_int), ("ms", C.c_float), ("pack", C.c_int),
@@ -57,6 +62,8 @@ class Job(C.Structure):
 SIGNATURES = {
     "pf_build_ybus": (_i, [_i, _i, _ip, _ip, _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _ip]),
     "pf_create": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(_p)]),
+    "pf_create_ex": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanOpts), C.POINTER(_p)]),
+    "pf_plan_opts_default": (None, [C.POINTER(PlanOpts)]),
     "pf_analyze": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanInfo), _ip, _ip, _ip, _ip,
                         _ip, _ip]),
     "pf_jacobian_pattern": (_i, [_p, _ip, _ip]),

@@ -615,13 +615,38 @@ pf_err pf_build_ybus(int n_bus, int n_branch, const int* f, const int* t, const 
     return PF_OK;
 }
 
+void pf_plan_opts_default(pf_plan_opts* o) {
+    if (!o) return;
+    const pf::PlanParams d;
+    o->order_slack = d.order_slack;
+    o->dense_max = d.dense_max;
+    o->split_len = d.split_len;
+    o->split_rows = d.split_rows;
+}
+
 pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
                  const double* y_im, const int* bus_type, pf_handle** out) {
+    return pf_create_ex(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, nullptr, out);
+}
+
+pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
+                    const double* y_im, const int* bus_type, const pf_plan_opts* plan_opts,
+                    pf_handle** out) {
     if (!out) return PF_EINVAL;
     *out = nullptr;
+    pf::PlanParams pp;
+    if (plan_opts) {
+        if (plan_opts->order_slack < 0 || plan_opts->order_slack > 8 || plan_opts->dense_max < 0 ||
+            plan_opts->split_len < 1 || plan_opts->split_rows < 0)
+            return PF_EINVAL;
+        pp.order_slack = plan_opts->order_slack;
+        pp.dense_max = plan_opts->dense_max;
+        pp.split_len = plan_opts->split_len;
+        pp.split_rows = plan_opts->split_rows;
+    }
     pf_handle* h = new (std::nothrow) pf_handle();
     if (!h) return PF_ENOMEM;
-    pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, h->plan);
+    pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, h->plan, pp);
     if (bs != pf::BUILD_OK) {
         delete h;
         return bs == pf::BUILD_ESINGULAR ? PF_ESINGULAR_PATTERN : PF_EINVAL;

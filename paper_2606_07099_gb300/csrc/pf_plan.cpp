@@ -97,7 +97,7 @@ void minimum_degree(const std::vector<std::vector<int>>& adj0, std::vector<int>&
 
 BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
                        const double* y_re, const double* y_im, const int* bus_type,
-                       Plan& P) {
+                       Plan& P, const PlanParams& pp) {
     if (n_bus < 1 || !y_indptr || !y_indices || !y_re || !y_im || !bus_type) return BUILD_EINVAL;
     if (y_indptr[0] != 0) return BUILD_EINVAL;
     for (int i = 0; i < n_bus; ++i)
@@ -200,7 +200,7 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
     }
     std::vector<int> order;
     std::vector<std::vector<int>> structs;
-    minimum_degree(adj, order, structs, kOrderSlack);
+    minimum_degree(adj, order, structs, pp.order_slack);
     std::vector<int> elim(n);  // node -> elimination index
     for (int k = 0; k < n; ++k) elim[order[k]] = k;
 
@@ -325,8 +325,8 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
     // a power-of-two group of lanes (about four blocks each) and reduced by shuffles.  The
     // choice depends on the plan only, so the summation order (and every result) is the
     // same for any number of threads per scenario.
-    auto lanes = [](int len, int rows) {
-        if (len <= 8 || rows > 128) return 1;
+    auto lanes = [&pp](int len, int rows) {
+        if (len <= pp.split_len || rows > pp.split_rows) return 1;
         int g = 1;
         while (g * 4 < len && g < 32) g <<= 1;
         return g;
@@ -354,7 +354,8 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
     // that block in shared memory and factors it densely instead of level by level.
     {
         int s = 0;
-        while (s < kDenseMax && s < n_levels &&
+        const int dmax = std::min(pp.dense_max, kDenseMax);
+        while (s < dmax && s < n_levels &&
                P.lev_ptr[n_levels - s] - P.lev_ptr[n_levels - s - 1] == 1) {
             const int c = s + 1, p0 = n - c;
             bool full = true;

@@ -71,10 +71,21 @@ struct Plan {
 
 enum BuildStatus { BUILD_OK = 0, BUILD_EINVAL = 1, BUILD_ESINGULAR = 2 };
 
+// The schedule choices of a plan (none changes what is computed, only the elimination
+// order, the levels and how their work is split): the ordering's degree slack, the
+// largest dense tail, and the rule that splits a long gather over lane groups (rows
+// longer than split_len blocks on levels of at most split_rows rows).
+struct PlanParams {
+    int order_slack = 1;
+    int dense_max = 32;
+    int split_len = 8;
+    int split_rows = 128;
+};
+
 // Validates the inputs, sorts/sums the CSR and builds the whole plan.
 BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
                        const double* y_re, const double* y_im, const int* bus_type,
-                       Plan& plan);
+                       Plan& plan, const PlanParams& params = PlanParams());
 
 // Minimum-degree elimination order of an undirected graph given by sorted
 // adjacency lists; also returns, for every node, its neighbours at the time it

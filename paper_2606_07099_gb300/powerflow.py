@@ -126,7 +126,9 @@ def _check_bus_tensor(x: torch.Tensor, name: str, n_bus: int, batch: int | None 
 class PowerFlow:
     """One network plan (pf_create) on the current CUDA device."""
 
-    def __init__(self, n_bus, y_indptr, y_indices, y_re, y_im, bus_type):
+    def __init__(self, n_bus, y_indptr, y_indices, y_re, y_im, bus_type, plan=None):
+        """``plan``: schedule choices (dict with any of order_slack, dense_max, split_len,
+        split_rows; pf_create_ex), or None for the defaults."""
         lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("libpf needs a CUDA device")
@@ -139,8 +141,13 @@ class PowerFlow:
                         np.ascontiguousarray(y_im, np.float64)]
         h = C.c_void_p()
         ip, ix, g, bv = self._arrays
-        L.check(lib.pf_create(self.n_bus, _iptr(ip), _iptr(ix), _dptr(g), _dptr(bv),
-                              _iptr(self.bus_type), C.byref(h)), "pf_create")
+        po = L.PlanOpts()
+        lib.pf_plan_opts_default(C.byref(po))
+        for k, v in (plan or {}).items():
+            setattr(po, k, int(v))
+        self.plan = {k: getattr(po, k) for k, _ in L.PlanOpts._fields_}
+        L.check(lib.pf_create_ex(self.n_bus, _iptr(ip), _iptr(ix), _dptr(g), _dptr(bv),
+                                 _iptr(self.bus_type), C.byref(po), C.byref(h)), "pf_create_ex")
         self._h = h
         self._lib = lib
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -152,15 +159,15 @@ class PowerFlow:
         self._last = None
 
     @classmethod
-    def from_branches(cls, n_bus, f, t, r, x, b, tap, bus_type):
+    def from_branches(cls, n_bus, f, t, r, x, b, tap, bus_type, plan=None):
         ip, ix, g, bv = build_ybus(n_bus, f, t, r, x, b, tap)
-        return cls(n_bus, ip, ix, g, bv, bus_type)
+        return cls(n_bus, ip, ix, g, bv, bus_type, plan)
 
     @classmethod
-    def from_grid(cls, grid):
+    def from_grid(cls, grid, plan=None):
         """From a ``synthgrid.Grid`` (branch list + bus types)."""
         return cls.from_branches(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.b, grid.tap,
-                                 grid.bus_type)
+                                 grid.bus_type, plan)
 
     def info(self) -> dict:
         info = L.PlanInfo()
@@ -659,3 +666,82 @@ def autotune_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, 
         pf._solve_id += 1
         pf._last = None
     return {"group_threads": res.group_threads, "placement": res.placement, "ms": res.ms}
+
+
+# Schedule candidates of the plan autotuner: the ordering's degree slack and the dense
+# tail's cap (split rules at their defaults).
+SCHEDULES = tuple({"order_slack": sl, "dense_max": dm} for sl in (0, 1, 2) for dm in (16, 32))
+
+
+def _time_ms(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def autotune_schedule(grid, Pd, Qd, Pg, Vset, schedules=SCHEDULES, **solve_kw):
+    """Pivot-level schedule autotuner: builds one plan per schedule choice (pf_create_ex),
+    times each with the launch shape pf_autotune picks for the default plan, then tunes the
+    launch shape of the fastest plan.  Returns (PowerFlow of the fastest plan, report).
+    Stream-synchronous; every trial solve computes the same power flow (the schedules
+    differ only in elimination order, level schedule and work split)."""
+    base = PowerFlow.from_grid(grid)
+    shape = base.autotune(Pd, Qd, Pg, Vset, **solve_kw)
+    fixed = dict(placement=shape["placement"], group_threads=shape["group_threads"],
+                 instances_per_cta=shape["instances_per_cta"], pack=shape["pack"],
+                 cluster=shape["cluster"])
+    trials = []
+    best = None
+    for sch in schedules:
+        pf = base if sch == {k: base.plan[k] for k in sch} else PowerFlow.from_grid(grid, sch)
+        ms = _time_ms(lambda: pf.solve(Pd, Qd, Pg, Vset, **fixed, **solve_kw))
+        trials.append({**sch, "ms": ms})
+        if best is None or ms < best[1]:
+            best = (pf, ms, sch)
+        elif pf is not base:
+            pf.close()
+    pf, _, sch = best
+    final = pf.autotune(Pd, Qd, Pg, Vset, **solve_kw) if pf is not base else shape
+    return pf, {"schedule": pf.plan, "shape": final, "trials": trials}
+
+
+def autotune_multi_schedule(grids, inputs, schedules=SCHEDULES, **solve_kw):
+    """The schedule of each network of a pf_solve_multi batch, chosen one network at a time
+    (the others fixed) by the launch's measured time, with the multi launch shape retuned
+    by pf_autotune_multi at the end.  ``inputs``: per network (Pd, Qd, Pg, Vset).  Returns
+    (list of PowerFlow, report)."""
+    pfs = [PowerFlow.from_grid(g) for g in grids]
+    items = lambda: [(p, *inp) for p, inp in zip(pfs, inputs)]
+    shape = autotune_multi(items(), **solve_kw)
+    kw = dict(group_threads=shape["group_threads"], placement=shape["placement"], **solve_kw)
+    trials = []
+    for k, g in enumerate(grids):
+        cur = pfs[k]
+        best_pf, best_ms = cur, _time_ms(lambda: solve_multi(items(), **kw))
+        for sch in schedules:
+            if sch == {key: cur.plan[key] for key in sch}:
+                continue
+            cand = PowerFlow.from_grid(g, sch)
+            pfs[k] = cand
+            ms = _time_ms(lambda: solve_multi(items(), **kw))
+            trials.append({"network": k, **sch, "ms": ms})
+            if ms < best_ms:
+                if best_pf is not cur:
+                    best_pf.close()
+                best_pf, best_ms = cand, ms
+            else:
+                cand.close()
+        pfs[k] = best_pf
+        if best_pf is not cur:
+            cur.close()
+    shape = autotune_multi(items(), **solve_kw)
+    return pfs, {"schedules": [p.plan for p in pfs], "shape": shape, "trials": trials}
