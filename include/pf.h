@@ -81,10 +81,12 @@ typedef struct {
     int n_levels;      /* depth of the elimination tree */
     long long schur_block_ops; /* 2x2 multiply-subtracts of one factorisation */
     long long plan_bytes;      /* the network's device plan (shared by every scenario) */
-    int dense_tail;            /* blocks in the dense tail: the last dense_tail elimination
-                                  levels hold one pivot each and their trailing block is
-                                  full, so the LU factors it densely in shared memory
-                                  (0: none) */
+    int top_pivots;            /* pivots of the top region: the trailing top_levels
+                                  elimination levels (few rows each), whose pivots the LU
+                                  and the sweeps take one at a time in shared memory
+                                  instead of level by level (0: none) */
+    int top_levels;            /* elimination levels in the top region */
+    int top_blocks;            /* 2x2 blocks the top region holds in shared memory */
 } pf_plan_info;
 
 /* Tunables of a solve; zero-initialise and set what you need. */
@@ -177,17 +179,24 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices,
  * levels' work is split, hence rounding and speed):
  *   order_slack: the fill-reducing minimum-degree ordering breaks ties, and near-ties up
  *     to this degree slack, towards a shallower elimination tree (0 = ties only);
- *   dense_max: the longest dense tail (trailing single-row levels whose block is full)
- *     factored and swept densely in shared memory, in blocks, 0..32 (0 = none; values
- *     above 32 act as 32); tails shorter than 3 blocks are not used;
+ *   top_rows, top_blocks: the top region is made of the trailing elimination levels
+ *     (from the top of the tree down) that hold at most top_rows rows each, as long as
+ *     the region's blocks (its rows' entries from its first row on) number at most
+ *     top_blocks (0..65534), its rows at most 128, and its FP64 shared-memory arena
+ *     (blocks, solve vector, index lists) at most 160 KB.  The LU and the triangular
+ *     sweeps take its pivots one at a time with the blocks in shared memory (16 bytes
+ *     per block in the mixed form, 32 in FP64, plus the lists), instead of one
+ *     barrier-separated step per level.  top_rows 0 = no region; regions under 3 rows
+ *     are not used;
  *   split_len, split_rows: on levels of at most split_rows rows, a gathered row longer
  *     than split_len blocks is split over a power-of-two group of lanes (about four
  *     blocks each, at most 32 lanes), reduced in a fixed order.
- * pf_plan_opts_default writes the defaults pf_create uses (1, 32, 8, 128).
+ * pf_plan_opts_default writes the defaults pf_create uses (1, 4, 2048, 8, 128).
  */
 typedef struct {
     int order_slack;
-    int dense_max;
+    int top_rows;
+    int top_blocks;
     int split_len;
     int split_rows;
 } pf_plan_opts;
@@ -196,8 +205,8 @@ void pf_plan_opts_default(pf_plan_opts* opts);
 
 /*
  * pf_create_ex -- pf_create with explicit schedule choices (host, NULL = the defaults).
- * Errors: as pf_create, and PF_EINVAL for order_slack outside 0..8, a negative dense_max
- * or split_rows, or split_len < 1.
+ * Errors: as pf_create, and PF_EINVAL for order_slack outside 0..8, a negative top_rows
+ * or split_rows, top_blocks outside 0..65534, or split_len < 1.
  */
 pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices,
                     const double* y_re, const double* y_im, const int* bus_type,

@@ -26,7 +26,7 @@ class PlanInfo(C.Structure):
                 ("n_unknowns", C.c_int), ("n_block", C.c_int), ("nnz_ybus", C.c_int),
                 ("nnz_j1", C.c_int), ("nnzb_lu", C.c_int), ("n_levels", C.c_int),
                 ("schur_block_ops", C.c_longlong), ("plan_bytes", C.c_longlong),
-                ("dense_tail", C.c_int)]
+                ("top_pivots", C.c_int), ("top_levels", C.c_int), ("top_blocks", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -37,8 +37,8 @@ class SolveOpts(C.Structure):
 
 
 class PlanOpts(C.Structure):
-    _fields_ = [("order_slack", C.c_int), ("dense_max", C.c_int), ("split_len", C.c_int),
-                ("split_rows", C.c_int)]
+    _fields_ = [("order_slack", C.c_int), ("top_rows", C.c_int), ("top_blocks", C.c_int),
+                ("split_len", C.c_int), ("split_rows", C.c_int)]
 
 
 class TuneResult(C.Structure):

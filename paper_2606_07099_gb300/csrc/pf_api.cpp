@@ -114,6 +114,13 @@ size_t smem_budget(const pf_handle* h) {
     return (size_t)h->smem_optin > kStaticSmemReserve ? (size_t)h->smem_optin - kStaticSmemReserve : 0;
 }
 
+static_assert(pf::kTopMaxRows == 32 * pf::kTopSlots, "region rows: one register slot per row");
+
+// Shared memory of the top region's arena (its blocks, solve vector and lists).
+size_t top_bytes(const pf::Plan& P, int ft_bytes) {
+    return pf::top_arena_bytes(P.top_blocks(), P.top_R, (int)P.top_ints.size(), ft_bytes);
+}
+
 // Default placement without tuning data: keep a scenario on chip only while at least
 // three of them fit on one SM (76 KB each); past that, more scenarios in flight from
 // the global workspace beat fewer scenarios in shared memory.
@@ -132,18 +139,18 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int place
     const pf::Plan& P = h->plan;
     pf::SlotLayout L{};
     L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
-    // the dense tail's staging area comes out of the budget first, then follows the
-    // placement's own arrays (a multiple of 16 bytes: warp arenas are laid end to end)
-    const size_t dense = pf::align_up((size_t)P.dense_s * P.dense_s * 4 * ft_bytes, 16);
+    // the top region's arena comes out of the budget first, then follows the placement's
+    // own arrays (a multiple of 16 bytes: warp arenas are laid end to end)
+    const size_t top = top_bytes(P, ft_bytes);
     const size_t full = smem_budget(h);
-    const size_t budget = full > dense ? full - dense : 0;
+    const size_t budget = full > top ? full - top : 0;
     L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes, budget,
                   placement, (size_t)ft_bytes * 2 * (size_t)P.n);
     L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes, budget,
                   placement);
     for (pf::KernelSmem* k : {&L.fwd, &L.adj}) {
-        k->smem_dense_off = pf::align_up(k->smem_bytes, 16);
-        k->smem_bytes = k->smem_dense_off + dense;
+        k->smem_top_off = pf::align_up(k->smem_bytes, 16);
+        k->smem_bytes = k->smem_top_off + top;
     }
     L.fac_global = (!L.fwd.fac_in_smem || keep) ? 1 : 0;
     size_t vec_global = 0;
@@ -306,7 +313,7 @@ namespace {
 // Every plan array packed into one buffer (one device allocation per network).
 struct PlanOffsets {
     size_t ygb, ytgb, ygb32, yptr, yidx, ytptr, ytidx, bt, p2b, b2p, lev, lup, lur, luc, lud,
-        lum, fy, lap, la, stp, stg, scp, sch, levg, j1pos, j1ptr, j1col;
+        lum, fy, lap, la, stp, stg, scp, sch, levg, j1pos, j1ptr, j1col, tmap, tsplit, tints, ttr;
 };
 
 void pack_plan(const pf::Plan& P, std::vector<unsigned char>& buf, PlanOffsets& o) {
@@ -335,6 +342,10 @@ void pack_plan(const pf::Plan& P, std::vector<unsigned char>& buf, PlanOffsets& 
     o.stp = push(buf, P.sch_tptr), o.stg = push(buf, P.sch_tgt), o.scp = push(buf, P.sch_cptr);
     o.sch = push(buf, sch), o.levg = push(buf, levg), o.j1pos = push(buf, j1pos);
     o.j1ptr = push(buf, P.j1_ptr), o.j1col = push(buf, P.j1_col);
+    std::vector<int2> ttr(P.top_tr_t.size());
+    for (size_t k = 0; k < ttr.size(); ++k) ttr[k] = make_int2(P.top_tr_t[k], P.top_tr_lu[k]);
+    o.tmap = push(buf, P.top_map), o.tsplit = push(buf, P.top_split);
+    o.tints = push(buf, P.top_ints), o.ttr = push(buf, ttr);
 }
 
 // Reactive-limit inputs of pf_solve_qlim (null for pf_solve).
@@ -619,7 +630,8 @@ void pf_plan_opts_default(pf_plan_opts* o) {
     if (!o) return;
     const pf::PlanParams d;
     o->order_slack = d.order_slack;
-    o->dense_max = d.dense_max;
+    o->top_rows = d.top_rows;
+    o->top_blocks = d.top_blocks;
     o->split_len = d.split_len;
     o->split_rows = d.split_rows;
 }
@@ -636,11 +648,13 @@ pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices, const 
     *out = nullptr;
     pf::PlanParams pp;
     if (plan_opts) {
-        if (plan_opts->order_slack < 0 || plan_opts->order_slack > 8 || plan_opts->dense_max < 0 ||
+        if (plan_opts->order_slack < 0 || plan_opts->order_slack > 8 || plan_opts->top_rows < 0 ||
+            plan_opts->top_blocks < 0 || plan_opts->top_blocks > pf::kTopMaxBlocks ||
             plan_opts->split_len < 1 || plan_opts->split_rows < 0)
             return PF_EINVAL;
         pp.order_slack = plan_opts->order_slack;
-        pp.dense_max = plan_opts->dense_max;
+        pp.top_rows = plan_opts->top_rows;
+        pp.top_blocks = plan_opts->top_blocks;
         pp.split_len = plan_opts->split_len;
         pp.split_rows = plan_opts->split_rows;
     }
@@ -683,9 +697,19 @@ pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices, const 
     d.n = P.n;
     d.nnzb = P.nnzb();
     d.n_levels = P.n_levels;
-    d.dense_s = P.dense_s;
-    d.dense_l0 = P.dense_l0;
-    d.dense_g = P.dense_g;
+    d.top_l0 = P.top_l0;
+    d.top_p0 = P.top_p0;
+    d.top_R = P.top_R;
+    d.top_nblk = P.top_blocks();
+    d.top_g = P.top_g;
+    d.top_nl = P.top_nl;
+    d.top_nfw = P.top_nfw;
+    d.top_nbw = P.top_nbw;
+    d.top_nints = (int)P.top_ints.size();
+    d.top_map = I(po.tmap);
+    d.top_split = I(po.tsplit);
+    d.top_ints = I(po.tints);
+    d.top_tr = reinterpret_cast<const int2*>(base + po.ttr);
     d.y_ptr = I(po.yptr);
     d.y_idx = I(po.yidx);
     d.y_gb = reinterpret_cast<const double2*>(base + po.ygb);
@@ -732,7 +756,9 @@ static void fill_info(const pf::Plan& P, size_t plan_bytes, pf_plan_info* info) 
     info->n_levels = P.n_levels;
     info->schur_block_ops = P.schur_ops;
     info->plan_bytes = (long long)plan_bytes;
-    info->dense_tail = P.dense_s;
+    info->top_pivots = P.top_R;
+    info->top_levels = P.n_levels - P.top_l0;
+    info->top_blocks = P.top_blocks();
 }
 
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info) {
@@ -1082,10 +1108,10 @@ JobForm multi_form(const pf_handle* h, const pf_solve_opts* opts) {
     const size_t vec = pf::carve(nullptr, P.n_bus, P.n, ft, false, nullptr);
     const size_t fac = pf::align_up((size_t)P.nnzb() * 4 * ft, 16);
     const size_t wpc = (size_t)multi_threads(opts) / 32;
-    const size_t dense = pf::align_up((size_t)P.dense_s * P.dense_s * 4 * ft, 16);
+    const size_t top = top_bytes(P, ft);
     if (wpc >= 2 && P.n_bus <= kWarpFormBuses)
-        return {1, (vec + fac + dense) * wpc <= budget ? PF_PLACE_ONCHIP : PF_PLACE_GLOBAL};
-    return {0, fac + (size_t)ft * 2 * P.n + dense <= budget ? PF_PLACE_FACTOR : PF_PLACE_GLOBAL};
+        return {1, (vec + fac + top) * wpc <= budget ? PF_PLACE_ONCHIP : PF_PLACE_GLOBAL};
+    return {0, fac + (size_t)ft * 2 * P.n + top <= budget ? PF_PLACE_FACTOR : PF_PLACE_GLOBAL};
 }
 
 pf::SlotLayout multi_layout(const pf_handle* h, const pf_solve_opts* opts) {

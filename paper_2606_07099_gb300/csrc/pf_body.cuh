@@ -421,46 +421,143 @@ __device__ __forceinline__ Blk<T> sub_blk(Blk<T> m, Blk<T> s) {
     return {m.a - s.a, m.b - s.b, m.c - s.c, m.d - s.d};
 }
 
-// The plan's dense tail: the last s levels hold one row each and rows p0 = n - s .. n - 1
-// are full from column p0 on (block (a, b) of the tail sits at lu_diag[p0 + a] - a + b).
-// It is staged in shared memory (D, s x s blocks, row-major) and factored densely with the
-// level schedule's own steps in its order -- L column scaling by the pivot's inverse,
-// Schur updates, the pivot replaced by its inverse -- so that its s steps cost
-// shared-memory round trips instead of the schedule's index chains through global memory.
-template <typename FT, bool W>
-__device__ void dense_tail_lu(const DevPlan& P, FT* fac, FT* D, int* bad) {
-    const int s = P.dense_s, p0 = P.n - s;
-    for (int t = GTID; t < s * s; t += GSZ) {
-        const int a = t / s, b = t - a * s;
-        stb(D, t, ldb(fac, __ldg(P.lu_diag + p0 + a) - a + b));
+// The plan's top region: its trailing elimination levels hold a few rows each, so a level
+// step there is mostly the latency of its chain of index and operand loads and of its
+// barrier.  Its blocks are staged in shared memory (T, in the plan's local numbering) and
+// its pivots are taken one at a time, in pivot order, with the level schedule's own
+// steps -- L column scaling by the pivot's inverse, Schur updates, the pivot replaced by
+// its inverse -- by at most kTopThreads threads.  Every target block receives one update
+// per pivot, in pivot order, so the result does not depend on the number of threads.
+template <typename FT>
+struct TopArena {
+    FT* T;   // the region's blocks
+    FT* ts;  // the region rows' part of the solve vector
+    int* I;  // the plan's staged lists: piv | lc_ptr | lc | tr_ptr | fw_ptr | fw | bw_ptr | bw
+};
+
+// The region's arena at byte offset `off` of the kernel's dynamic shared memory (every
+// extern __shared__ array starts at that one base), addressed from the shared-memory
+// symbol itself so that its loads and stores are shared-memory instructions.
+template <typename FT>
+__device__ __forceinline__ TopArena<FT> top_arena(const DevPlan& P, size_t off) {
+    extern __shared__ __align__(16) unsigned char pf_dyn_smem[];
+    unsigned char* a = pf_dyn_smem + off;
+    return {reinterpret_cast<FT*>(a),
+            reinterpret_cast<FT*>(a + top_ts_off(P.top_nblk, (int)sizeof(FT))),
+            reinterpret_cast<int*>(a + top_ints_off(P.top_nblk, P.top_R, (int)sizeof(FT)))};
+}
+
+constexpr size_t kNoTop = ~size_t(0);  // no region arena (level sweeps over every level)
+constexpr int kTopThreads = 1024;  // threads of a CTA that factor the region
+constexpr int kTopPrefetch = 2;    // Schur triples per thread loaded one pivot ahead
+
+// Barrier of the region's factoring threads: the group's warp, or named barrier 1 over the
+// first nt threads of the CTA (the others wait at the group barrier that follows).
+template <bool W>
+__device__ __forceinline__ void top_bar(int nt) {
+    if (W)
+        __syncwarp();
+    else
+        asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+}
+
+// The region's pivots on one scenario's arena A, by threads t = 0 .. nt - 1 (each calls it,
+// `bar` is their barrier).  One barrier per pivot: each Schur triple of pivot k scales its
+// L block on the fly, L(i,k) = A(i,k) P_k^-1 (the same product the stored L block gets),
+// and the stores of column k's L blocks and of the pivot inverse are deferred to pivot
+// k + 1's round, when no thread reads those blocks any more (pivot k + 1 reads column
+// k + 1 and row k + 1 only, and its targets lie beyond both).  bk is set if a pivot was
+// singular.
+template <typename FT, typename Bar>
+__device__ __forceinline__ void top_factor(const DevPlan& P, const TopArena<FT>& A, int t, int nt,
+                                           Bar bar, int& bk) {
+    const int R = P.top_R;
+    FT* T = A.T;
+    const int* piv = A.I;
+    const int* lcp = piv + R;
+    const int* lc = lcp + R + 1;
+    const int* trp = lc + P.top_nl;
+    constexpr int PF = kTopPrefetch;
+    const int2 idle = make_int2(-1, 0);
+    int2 nx[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+        const int c = trp[0] + t + j * nt;
+        nx[j] = c < trp[1] ? __ldg(P.top_tr + c) : idle;
     }
-    gsync<W>();
-    for (int k = 0; k < s; ++k) {
-        const int m = s - 1 - k;
-        for (int i = GTID; i < m; i += GSZ) {  // L(k+1+i, k) <- A(k+1+i, k) A(k, k)^-1
-            const int r = (k + 1 + i) * s + k;
-            int dummy = 0;
-            stb(D, r, mul(ldb(D, r), inv2(ldb(D, k * s + k), &dummy)));
+    Blk<FT> dprev{FT(0), FT(0), FT(0), FT(0)};
+    for (int k = 0; k < R; ++k) {
+        int2 cur[PF];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) cur[j] = nx[j];
+        if (k + 1 < R) {  // the next pivot's first triples: plan data, loaded ahead
+            const int d0 = trp[k + 1], d1 = trp[k + 2];
+#pragma unroll
+            for (int j = 0; j < PF; ++j) {
+                const int c = d0 + t + j * nt;
+                nx[j] = c < d1 ? __ldg(P.top_tr + c) : idle;
+            }
         }
-        gsync<W>();
-        for (int t = GTID; t < m * m; t += GSZ) {  // A(i, j) -= L(i, k) U(k, j), i, j > k
-            const int i = k + 1 + t / m, j = k + 1 + t % m;
-            const Blk<FT> x = ldb(D, i * s + k), y = ldb(D, k * s + j);
+        const Blk<FT> d = inv2(ldb(T, piv[k]), &bk);
+        if (k > 0) {  // deferred: column k - 1's L blocks and its pivot inverse
+            for (int c = lcp[k - 1] + t; c < lcp[k]; c += nt) {
+                const int li = lc[c] & 0xffff;
+                stb(T, li, mul(ldb(T, li), dprev));
+            }
+            if (t == 0) stb(T, piv[k - 1], dprev);
+        }
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            if (cur[j].x >= 0) {
+                const unsigned lu = (unsigned)cur[j].y;
+                const Blk<FT> x = mul(ldb(T, (int)(lu & 0xffffu)), d);
+                const Blk<FT> y = ldb(T, (int)(lu >> 16));
+                Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+                acc.a += x.a * y.a + x.b * y.c;
+                acc.b += x.a * y.b + x.b * y.d;
+                acc.c += x.c * y.a + x.d * y.c;
+                acc.d += x.c * y.b + x.d * y.d;
+                stb(T, cur[j].x, sub_blk(ldb(T, cur[j].x), acc));
+            }
+        }
+        for (int c = trp[k] + t + PF * nt; c < trp[k + 1]; c += nt) {
+            const int2 tr = __ldg(P.top_tr + c);
+            const unsigned lu = (unsigned)tr.y;
+            const Blk<FT> x = mul(ldb(T, (int)(lu & 0xffffu)), d), y = ldb(T, (int)(lu >> 16));
             Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
             acc.a += x.a * y.a + x.b * y.c;
             acc.b += x.a * y.b + x.b * y.d;
             acc.c += x.c * y.a + x.d * y.c;
             acc.d += x.c * y.b + x.d * y.d;
-            stb(D, i * s + j, sub_blk(ldb(D, i * s + j), acc));
+            stb(T, tr.x, sub_blk(ldb(T, tr.x), acc));
         }
-        if (GTID == 0) stb(D, k * s + k, inv2(ldb(D, k * s + k), bad));  // no target touches it
-        gsync<W>();
+        dprev = d;
+        bar();
     }
-    for (int t = GTID; t < s * s; t += GSZ) {
-        const int a = t / s, b = t - a * s;
-        stb(fac, __ldg(P.lu_diag + p0 + a) - a + b, ldb(D, t));
+    if (t == 0) stb(T, piv[R - 1], dprev);  // the last pivot has no L blocks below it
+}
+
+// Factors the region in the arena at `arena` (shared memory) after the levels below it;
+// with `wb` the factored blocks are also written back into fac (for sweeps or an adjoint
+// that read the factor there).  Sets *bad if a pivot was singular.
+template <typename FT, bool W>
+__device__ void top_lu(const DevPlan& P, FT* fac, size_t arena, int* bad, bool wb) {
+    const int nb = P.top_nblk;
+    const TopArena<FT> A = top_arena<FT>(P, arena);
+    for (int k = GTID; k < P.top_nints; k += GSZ) A.I[k] = __ldg(P.top_ints + k);
+    for (int r = GTID; r < nb; r += GSZ) stb(A.T, r, ldb(fac, __ldg(P.top_map + r)));
+    gsync<W>();
+    const int nt = W ? 32 : min(GSZ, kTopThreads);
+    if (GTID < nt) {
+        int bk = 0;
+        top_factor<FT>(P, A, GTID, nt, [nt] { top_bar<W>(nt); }, bk);
+        if (GTID == 0) *bad |= bk;
     }
     gsync<W>();
+    if (wb) {
+        for (int r = GTID; r < nb; r += GSZ) stb(fac, __ldg(P.top_map + r), ldb(A.T, r));
+        gsync<W>();
+    }
 }
 
 // Right-looking, one elimination-tree level at a time.  Phase A scales the L columns of
@@ -468,13 +565,14 @@ __device__ void dense_tail_lu(const DevPlan& P, FT* fac, FT* D, int* bad) {
 // block (no two threads write the same block) and replaces the level's pivot blocks by
 // their inverses.  (A variant with one barrier per level, recomputing L(i,k) inside each
 // Schur update, measured slower: the extra 2x2 inverse per update costs more than the
-// barrier it saves.)  The plan's dense tail, if any, is factored by dense_tail_lu in
-// `dense` (shared memory).  Returns nonzero if a pivot was singular.
+// barrier it saves.)  The plan's top region, if any, is factored by top_lu in `top`
+// (shared memory; written back into fac with `wb`).  Returns nonzero if a pivot was
+// singular.
 template <typename FT, bool W>
-__device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad, FT* dense) {
+__device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad, size_t top, bool wb) {
     int bad = 0;
     if (!W && threadIdx.x == 0) *s_bad = 0;
-    const int n_sparse = P.dense_s ? P.dense_l0 : P.n_levels;
+    const int n_sparse = P.top_R ? P.top_l0 : P.n_levels;
     for (int l = 0; l < n_sparse; ++l) {
         // FP32 factor: two items per thread and round, so that two chains of loads are in
         // flight (within a level the pivots read, the L blocks scaled and the Schur
@@ -554,7 +652,7 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad, FT* dense) {
         }
         gsync<W>();
     }
-    if (P.dense_s) dense_tail_lu<FT, W>(P, fac, dense, &bad);
+    if (P.top_R) top_lu<FT, W>(P, fac, top, &bad, wb);
     if (W) return __any_sync(0xffffffffu, bad);
     if (bad) *s_bad = 1;
     gsync<W>();
@@ -660,20 +758,107 @@ __device__ __forceinline__ void sweep_level(const DevPlan& P, const FT* fac, FT*
     }
 }
 
-// The forward sweep over the plan's dense tail (rows p0 = n - s .. n - 1; D: the factored
-// tail left in shared memory by phase_lu): first every tail row's part left of the tail
-// (those x are final: one gather over all tail rows, dense_g lanes per row), then the
-// unit-lower dense substitution, one shared-memory step per tail row.
+// x_q of one register slot (q uniform over the warp).
+template <typename FT>
+__device__ __forceinline__ FT top_slot(const FT (&v)[kTopSlots], int q) {
+    FT r = v[0];
+#pragma unroll
+    for (int j = 1; j < kTopSlots; ++j) r = q == j ? v[j] : r;
+    return r;
+}
+
+// v0[q], v1[q] -= M (x0, x1) for this lane's slot q (q < 0: no entry), without branches
+// (the other slots subtract zero, which leaves every value unchanged).
+template <typename FT>
+__device__ __forceinline__ void top_upd(FT (&v0)[kTopSlots], FT (&v1)[kTopSlots], int q,
+                                        const Blk<FT>& m, FT x0, FT x1) {
+    const FT d0 = m.a * x0 + m.b * x1, d1 = m.c * x0 + m.d * x1;
+#pragma unroll
+    for (int j = 0; j < kTopSlots; ++j) {
+        v0[j] -= q == j ? d0 : FT(0);
+        v1[j] -= q == j ? d1 : FT(0);
+    }
+}
+
+// The region's forward and backward sweeps by one warp, on the region rows' part of the
+// solve vector held in registers: lane l owns rows l, l + 32, ... (slot q = row / 32).
+// The plan lists the sweeps as rounds of one entry per lane.  A forward round of column
+// k: x_k (final) is broadcast by its owner lane and every lane updates its row i > k with
+// L(i,k) x_k.  A backward round of column k: its first round forms x_k <- P_k^-1 x_k (the
+// owner keeps it in the row's slot), every round updates rows i < k with U(i,k) x_k.
+// Each row receives its updates in column order.  No round branches: an empty entry
+// (-1) reads block 0 into no slot, and the rounds' loads depend on the plan only, so
+// several rounds' loads are in flight together.  Reads ts (the rows after their part
+// left of the region), writes the region's solution to x[2 p0 ..].
+template <typename FT>
+__device__ __forceinline__ void top_sweeps(const DevPlan& P, const TopArena<FT>& A, int lane,
+                                           const FT* ts, FT* x) {
+    const int R = P.top_R;
+    const int* piv = A.I;
+    const int* fwk = piv + R + (R + 1) + P.top_nl + (R + 1);
+    const int* fw = fwk + P.top_nfw;
+    const int* bwk = fw + 32 * P.top_nfw;
+    const int* bw = bwk + P.top_nbw;
+    const FT* T = A.T;
+    FT v0[kTopSlots], v1[kTopSlots];
+#pragma unroll
+    for (int j = 0; j < kTopSlots; ++j) {
+        const int i = j * 32 + lane;
+        v0[j] = i < R ? ts[2 * i] : FT(0);
+        v1[j] = i < R ? ts[2 * i + 1] : FT(0);
+    }
+#pragma unroll 4
+    for (int u = 0; u < P.top_nfw; ++u) {
+        const int k = fwk[u], e = fw[u * 32 + lane];
+        const Blk<FT> m = ldb(T, max(e, 0) & 0xffff);
+        const FT x0 = __shfl_sync(0xffffffffu, top_slot(v0, k >> 5), k & 31);
+        const FT x1 = __shfl_sync(0xffffffffu, top_slot(v1, k >> 5), k & 31);
+        top_upd(v0, v1, e >= 0 ? e >> 16 : -1, m, x0, x1);
+    }
+#pragma unroll 4
+    for (int u = 0; u < P.top_nbw; ++u) {
+        const int kf = bwk[u], k = kf >> 1, e = bw[u * 32 + lane];
+        const Blk<FT> m = ldb(T, max(e, 0) & 0xffff);
+        const Blk<FT> d = ldb(T, piv[k]);
+        const FT y0 = __shfl_sync(0xffffffffu, top_slot(v0, k >> 5), k & 31);
+        const FT y1 = __shfl_sync(0xffffffffu, top_slot(v1, k >> 5), k & 31);
+        const bool first = (kf & 1) != 0;
+        const FT x0 = first ? d.a * y0 + d.b * y1 : y0;
+        const FT x1 = first ? d.c * y0 + d.d * y1 : y1;
+        const bool own = first && (k & 31) == lane;  // the owner keeps x_k in the row's slot
+#pragma unroll
+        for (int j = 0; j < kTopSlots; ++j) {
+            v0[j] = own && (k >> 5) == j ? x0 : v0[j];
+            v1[j] = own && (k >> 5) == j ? x1 : v1[j];
+        }
+        top_upd(v0, v1, e >= 0 ? e >> 16 : -1, m, x0, x1);
+    }
+#pragma unroll
+    for (int j = 0; j < kTopSlots; ++j) {
+        const int i = j * 32 + lane;
+        if (i < R) {
+            x[2 * (P.top_p0 + i)] = v0[j];
+            x[2 * (P.top_p0 + i) + 1] = v1[j];
+        }
+    }
+}
+
+// The sweeps over the top region (after the levels below it have been swept forward, so
+// the x of every row left of the region is final): first every region row's part left of
+// the region (one gather over all region rows, top_g lanes per row) into the region's copy
+// of x in shared memory, then the region's columns one at a time by one warp (top_sweeps),
+// which writes the region's x back.
 template <typename FT, bool W>
-__device__ void dense_tail_lower(const DevPlan& P, const FT* fac, const FT* D, FT* x) {
-    const int s = P.dense_s, p0 = P.n - s, G = P.dense_g;
+__device__ void top_solve(const DevPlan& P, const FT* fac, FT* x, size_t arena) {
+    const int p0 = P.top_p0, G = P.top_g;
+    const TopArena<FT> A = top_arena<FT>(P, arena);
     if (G == 1) {
         for (int p = p0 + GTID; p < P.n; p += GSZ) {
             FT s0 = FT(0), s1 = FT(0);
-            row_gather<FT, false>(P, fac, x, __ldg(P.lu_ptr + p), __ldg(P.lu_diag + p) - (p - p0),
-                                  1, s0, s1);
-            x[2 * p] -= s0;
-            x[2 * p + 1] -= s1;
+            row_gather<FT, false>(P, fac, x, __ldg(P.lu_ptr + p), __ldg(P.top_split + p - p0), 1,
+                                  s0, s1);
+            A.ts[2 * (p - p0)] = x[2 * p] - s0;
+            A.ts[2 * (p - p0) + 1] = x[2 * p + 1] - s1;
         }
     } else {  // G lanes per row; every lane runs the same rounds (the shuffles need whole warps)
         const int sub = GTID & (G - 1), nrg = GSZ / G;
@@ -683,69 +868,34 @@ __device__ void dense_tail_lower(const DevPlan& P, const FT* fac, const FT* D, F
             FT s0 = FT(0), s1 = FT(0);
             if (act)
                 row_gather<FT, false>(P, fac, x, __ldg(P.lu_ptr + p) + sub,
-                                      __ldg(P.lu_diag + p) - (p - p0), G, s0, s1);
+                                      __ldg(P.top_split + p - p0), G, s0, s1);
             for (int o = G >> 1; o; o >>= 1) {
                 s0 += __shfl_xor_sync(0xffffffffu, s0, o);
                 s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             }
             if (act && sub == 0) {
-                x[2 * p] -= s0;
-                x[2 * p + 1] -= s1;
+                A.ts[2 * (p - p0)] = x[2 * p] - s0;
+                A.ts[2 * (p - p0) + 1] = x[2 * p + 1] - s1;
             }
         }
     }
     gsync<W>();
-    for (int k = 0; k < s; ++k) {  // x_i -= L(i, k) x_k for the tail rows i > k
-        const FT x0 = x[2 * (p0 + k)], x1 = x[2 * (p0 + k) + 1];
-        for (int i = k + 1 + GTID; i < s; i += GSZ) {
-            const Blk<FT> m = ldb(D, i * s + k);
-            x[2 * (p0 + i)] -= m.a * x0 + m.b * x1;
-            x[2 * (p0 + i) + 1] -= m.c * x0 + m.d * x1;
-        }
-        gsync<W>();
-    }
-}
-
-// The backward sweep over the dense tail (its U entries all lie inside the tail):
-// x_k <- P_k^-1 x_k (the stored pivot is the inverse; every thread forms it), then
-// x_i -= U(i, k) x_k for the tail rows i < k.  x_k itself is stored after the step's
-// barrier, once every thread has read it; no later tail step reads it.
-template <typename FT, bool W>
-__device__ void dense_tail_upper(const DevPlan& P, const FT* D, FT* x) {
-    const int s = P.dense_s, p0 = P.n - s;
-    for (int k = s - 1; k >= 0; --k) {
-        const Blk<FT> d = ldb(D, k * s + k);
-        const FT y0 = x[2 * (p0 + k)], y1 = x[2 * (p0 + k) + 1];
-        const FT x0 = d.a * y0 + d.b * y1, x1 = d.c * y0 + d.d * y1;
-        for (int i = GTID; i < k; i += GSZ) {
-            const Blk<FT> m = ldb(D, i * s + k);
-            x[2 * (p0 + i)] -= m.a * x0 + m.b * x1;
-            x[2 * (p0 + i) + 1] -= m.c * x0 + m.d * x1;
-        }
-        gsync<W>();
-        if (GTID == 0) {
-            x[2 * (p0 + k)] = x0;
-            x[2 * (p0 + k) + 1] = x1;
-        }
-    }
+    if (GTID < 32) top_sweeps<FT>(P, A, GTID, A.ts, x);
     gsync<W>();
 }
 
 // x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
-// then U x = y by descending levels.  With `dense` (the dense tail as phase_lu left it in
-// shared memory) the tail's levels are swept densely there.
+// then U x = y by descending levels.  With `top` (the top region as phase_lu left it in
+// shared memory) the region's levels are swept there, one column at a time.
 template <typename FT, bool W>
-__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x, const FT* dense = nullptr) {
-    const bool dt = dense != nullptr && P.dense_s > 0;
-    const int nl = dt ? P.dense_l0 : P.n_levels;
+__device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x, size_t top = kNoTop) {
+    const bool dt = top != kNoTop && P.top_R > 0;
+    const int nl = dt ? P.top_l0 : P.n_levels;
     for (int l = 0; l < nl; ++l) {
         sweep_level<FT, false, false, W>(P, fac, x, l);
         gsync<W>();
     }
-    if (dt) {
-        dense_tail_lower<FT, W>(P, fac, dense, x);
-        dense_tail_upper<FT, W>(P, dense, x);
-    }
+    if (dt) top_solve<FT, W>(P, fac, x, top);
     for (int l = nl - 1; l >= 0; --l) {
         sweep_level<FT, true, false, W>(P, fac, x, l);
         gsync<W>();
@@ -901,9 +1051,10 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         if (it_round >= A.max_iter) { status = 1; break; }
         phase_fill<W, QL>(P, a, fac);
         gsync<W>();
-        // the dense tail, factored by phase_lu, stays in shared memory for this step's sweeps
-        FT* const tail = reinterpret_cast<FT*>(smem + K.smem_dense_off);
-        if (phase_lu<FT, W>(P, fac, &s_bad, tail)) {
+        // the top region, factored by phase_lu, stays in shared memory for this step's
+        // sweeps (and goes back into fac too when the factor is kept for the adjoint)
+        const size_t top = (W ? (size_t)(threadIdx.x >> 5) * K.smem_bytes : 0) + K.smem_top_off;
+        if (phase_lu<FT, W>(P, fac, &s_bad, top, A.keep_factors != 0)) {
             status = 3;
             factored = false;
             break;
@@ -912,7 +1063,7 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
         // first solve with the FT factor
         for (int k = GTID; k < 2 * P.n; k += GSZ) x[k] = FT(-a.F[k]);
         gsync<W>();
-        phase_solve<FT, W>(P, fac, x, tail);
+        phase_solve<FT, W>(P, fac, x, top);
         if (mixed) {
             for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] = double(x[k]);
             gsync<W>();
@@ -922,7 +1073,7 @@ __device__ __forceinline__ void solve_body(const DevPlan& P, const SolveArgs& A,
                 // forcing term min(ir_rtol, ||F1||): loose far from the solution, quadratic
                 // near it, so the inexact Newton steps keep the quadratic convergence
                 if (A.ir_rtol > 0.0 && rmax <= fmin(A.ir_rtol, norm) * norm) break;
-                phase_solve<FT, W>(P, fac, x, tail);
+                phase_solve<FT, W>(P, fac, x, top);
                 for (int k = GTID; k < 2 * P.n; k += GSZ) a.dz[k] += double(x[k]);
                 gsync<W>();
             }
@@ -1137,8 +1288,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             }
             phase_fill<false, QL>(P, a, fac);
             gsync<false>();
-            if (phase_lu<FT, false>(P, fac, &s_bad,
-                                    reinterpret_cast<FT*>(smem + K.smem_dense_off))) {
+            if (phase_lu<FT, false>(P, fac, &s_bad, K.smem_top_off, true)) {
                 astat = 3;
                 break;
             }

@@ -9,8 +9,14 @@ namespace pf {
 // Read-only plan arrays on the device (see pf_plan.h for their meaning).
 struct DevPlan {
     int n_bus, n, nnzb, n_levels;
-    int dense_s, dense_l0;  // dense tail: its size in blocks and first level (0: none)
-    int dense_g;            // lanes per tail row for its part left of the tail
+    // top region (the trailing levels top_l0.. whose pivots are taken one at a time in
+    // shared memory; top_R = 0: none): first level and row, rows, blocks, lanes per row of
+    // its part left of the region, and the lengths of its staged lists
+    int top_l0, top_p0, top_R, top_nblk, top_g, top_nl, top_nfw, top_nbw, top_nints;
+    const int* top_map;    // [top_nblk] fac position of each region block
+    const int* top_split;  // [top_R] first entry of each region row inside the region
+    const int* top_ints;   // piv | lc_ptr | lc | tr_ptr | fw_ptr | fw | bw_ptr | bw (see Plan)
+    const int2* top_tr;    // Schur triples: (target, L block | U block << 16)
     const int* y_ptr;
     const int* y_idx;
     const double2* y_gb;  // (G, B) of every Ybus entry
@@ -50,7 +56,7 @@ struct KernelSmem {
     int x_in_smem;        // the solve vector in shared memory although the vectors are not
     size_t smem_x_off;    // its offset inside the dynamic shared memory
     size_t vec_bytes;     // size of this kernel's vector arena
-    size_t smem_dense_off;  // the dense tail's staging area (dense_s^2 blocks), if any
+    size_t smem_top_off;  // the top region's arena (top_arena_bytes), if any
 };
 
 // Per-scenario workspace slot (global memory), offsets in bytes from the slot base.
@@ -194,6 +200,22 @@ struct Arrays {
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Region rows per lane of the warp that sweeps the top region (its rows' x in registers).
+constexpr int kTopSlots = 4;
+
+// The top region's shared-memory arena: its blocks and one scratch block (ft bytes per
+// value; idle lanes read and write the scratch block instead of branching), then its
+// solve vector (2 values per row), then its staged index lists (nints ints).
+__host__ __device__ inline size_t top_ts_off(int nblk, int ft) {
+    return align_up((size_t)(nblk + 1) * 4 * ft, 16);
+}
+__host__ __device__ inline size_t top_ints_off(int nblk, int R, int ft) {
+    return top_ts_off(nblk, ft) + align_up((size_t)2 * R * ft, 16);
+}
+__host__ __device__ inline size_t top_arena_bytes(int nblk, int R, int nints, int ft) {
+    return R ? top_ints_off(nblk, R, ft) + align_up((size_t)4 * nints, 16) : 0;
+}
 
 // Arena layout shared by host (sizing) and device (carving).  In the forward layout the
 // refinement's dV (FP64, two per bus) shares its bytes with the first four FP32 fill

@@ -95,6 +95,115 @@ void minimum_degree(const std::vector<std::vector<int>>& adj0, std::vector<int>&
     }
 }
 
+// The top region from level l0 on (none if l0 == n_levels): local block numbering, the
+// LU lists and the sweep rounds (see Plan).  `lanes` is the plan's gather split rule.
+template <typename Lanes>
+static BuildStatus build_top(Plan& P, int l0, Lanes lanes) {
+    const int n = P.n, p0 = P.lev_ptr[l0], R = n - p0;
+    P.top_l0 = l0;
+    P.top_p0 = p0;
+    P.top_R = R;
+    P.top_map.clear();
+    P.top_split.assign(R, 0);
+    P.top_ints.clear();
+    P.top_tr_t.clear();
+    P.top_tr_lu.clear();
+    P.top_nl = P.top_nfw = P.top_nbw = 0;
+    P.top_g = 1;
+    if (R == 0) return BUILD_OK;
+    std::vector<int> base(R + 1, 0);
+    int mT = 0;  // longest part of a region row left of the region
+    for (int p = p0; p < n; ++p) {
+        const auto b = P.lu_col.begin() + P.lu_ptr[p], e = P.lu_col.begin() + P.lu_ptr[p + 1];
+        const int f = (int)(std::lower_bound(b, e, p0) - P.lu_col.begin());
+        P.top_split[p - p0] = f;
+        base[p - p0 + 1] = base[p - p0] + (P.lu_ptr[p + 1] - f);
+        mT = std::max(mT, f - P.lu_ptr[p]);
+    }
+    P.top_g = lanes(mT, R);
+    P.top_map.resize(base[R]);
+    for (int p = p0; p < n; ++p)
+        for (int e = P.top_split[p - p0]; e < P.lu_ptr[p + 1]; ++e)
+            P.top_map[base[p - p0] + e - P.top_split[p - p0]] = e;
+    auto loc = [&](int p, int e) { return base[p - p0] + e - P.top_split[p - p0]; };
+    // the region's L columns (rows below the pivot) and U columns (rows above), rows
+    // ascending, as (local row, local block)
+    std::vector<std::vector<std::pair<int, int>>> lcol(R), ucol(R);
+    for (int i = p0; i < n; ++i) {
+        for (int e = P.top_split[i - p0]; e < P.lu_diag[i]; ++e)
+            lcol[P.lu_col[e] - p0].push_back({i - p0, loc(i, e)});
+        for (int e = P.lu_diag[i] + 1; e < P.lu_ptr[i + 1]; ++e)
+            ucol[P.lu_col[e] - p0].push_back({i - p0, loc(i, e)});
+    }
+    std::vector<int>& I = P.top_ints;
+    for (int k = p0; k < n; ++k) I.push_back(loc(k, P.lu_diag[k]));  // piv
+    I.push_back(0);                                                   // lc_ptr
+    for (int k = 0; k < R; ++k) I.push_back(I.back() + (int)lcol[k].size());
+    for (int k = 0; k < R; ++k)                                       // lc
+        for (const auto& e : lcol[k]) I.push_back(e.second);
+    P.top_nl = I[2 * R];
+    // Schur triples: for pivot k, every L block (i, k) of the region times every U block
+    // (k, j) updates block (i, j), which the filled pattern holds
+    I.push_back(0);  // tr_ptr
+    for (int k = p0; k < n; ++k) {
+        for (const auto& le : lcol[k - p0]) {
+            const int i = p0 + le.first;
+            for (int e = P.lu_diag[k] + 1; e < P.lu_ptr[k + 1]; ++e) {
+                const int j = P.lu_col[e];
+                const auto b = P.lu_col.begin() + P.lu_ptr[i], en = P.lu_col.begin() + P.lu_ptr[i + 1];
+                const auto it = std::lower_bound(b, en, j);
+                if (it == en || *it != j) return BUILD_EINVAL;  // clique property violated: bug
+                P.top_tr_t.push_back(loc(i, (int)(it - P.lu_col.begin())));
+                P.top_tr_lu.push_back(le.second | (loc(k, e) << 16));
+            }
+        }
+        I.push_back((int)P.top_tr_t.size());
+    }
+    // sweep rounds: a column's entries go to the lane that owns their row (row i: lane
+    // i % 32, register slot i / 32), one entry per lane and round, (slot << 16 | block)
+    // or -1.  Per round its column: k for the forward rounds (columns without entries have
+    // none), k << 1 | first for the backward rounds (every column has at least one: its
+    // first round also applies the pivot inverse)
+    auto rounds = [&](const std::vector<std::vector<std::pair<int, int>>>& cols, bool every,
+                      int& total) {
+        std::vector<int> rk, re;
+        for (int k = 0; k < R; ++k) {
+            std::vector<std::vector<int>> lane(32);
+            for (const auto& e : cols[k]) lane[e.first % 32].push_back(((e.first / 32) << 16) | e.second);
+            size_t nr = 0;
+            for (const auto& l : lane) nr = std::max(nr, l.size());
+            if (every) nr = std::max<size_t>(nr, 1);
+            for (size_t r = 0; r < nr; ++r) {
+                rk.push_back(every ? (k << 1) | (r == 0 ? 1 : 0) : k);
+                for (int l = 0; l < 32; ++l) re.push_back(r < lane[l].size() ? lane[l][r] : -1);
+            }
+        }
+        total = (int)rk.size();
+        I.insert(I.end(), rk.begin(), rk.end());
+        I.insert(I.end(), re.begin(), re.end());
+    };
+    rounds(lcol, false, P.top_nfw);
+    // the backward sweep takes the columns in descending order
+    std::vector<std::vector<std::pair<int, int>>> ucol_desc(ucol.rbegin(), ucol.rend());
+    {
+        const size_t at = I.size();
+        rounds(ucol_desc, true, P.top_nbw);
+        // column indices of the reversed list back to the region's own
+        for (int u = 0; u < P.top_nbw; ++u) {
+            const int v = I[at + u];
+            I[at + u] = ((R - 1 - (v >> 1)) << 1) | (v & 1);
+        }
+    }
+    return BUILD_OK;
+}
+
+// Bytes of the region's shared-memory arena in FP64 (blocks, solve vector, lists).
+static long long top_arena_fp64(const Plan& P) {
+    auto a16 = [](long long v) { return (v + 15) / 16 * 16; };
+    return a16((long long)(P.top_blocks() + 1) * 32) + a16((long long)P.top_R * 16) +
+           a16((long long)P.top_ints.size() * 4);
+}
+
 BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
                        const double* y_re, const double* y_im, const int* bus_type,
                        Plan& P, const PlanParams& pp) {
@@ -349,29 +458,32 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         P.lev_gS[l] = lanes(mS, targets);
     }
 
-    // dense tail: the most trailing levels (at most kDenseMax) that hold one row each and
-    // whose rows are full from the tail's first position on.  The factorisation stages
-    // that block in shared memory and factors it densely instead of level by level.
+    // top region: the trailing levels of at most top_rows rows each, taken from the top of
+    // the tree down while the region's blocks (its rows' entries from its first row on)
+    // stay within top_blocks, its rows within kTopMaxRows and its FP64 arena within
+    // kTopMaxBytes.  Its pivots are factored and swept one at a time.
     {
-        int s = 0;
-        const int dmax = std::min(pp.dense_max, kDenseMax);
-        while (s < dmax && s < n_levels &&
-               P.lev_ptr[n_levels - s] - P.lev_ptr[n_levels - s - 1] == 1) {
-            const int c = s + 1, p0 = n - c;
-            bool full = true;
-            for (int p = p0; p < n && full; ++p) {
-                const auto b = P.lu_col.begin() + P.lu_ptr[p], e = P.lu_col.begin() + P.lu_ptr[p + 1];
-                full = (e - std::lower_bound(b, e, p0)) == c;
-            }
-            if (!full) break;
-            s = c;
+        auto first_in = [&P](int p, int p0) {  // first entry of row p at column >= p0
+            const auto b = P.lu_col.begin() + P.lu_ptr[p], e = P.lu_col.begin() + P.lu_ptr[p + 1];
+            return (int)(std::lower_bound(b, e, p0) - P.lu_col.begin());
+        };
+        auto blocks_from = [&](int p0) {
+            long long c = 0;
+            for (int p = p0; p < n; ++p) c += P.lu_ptr[p + 1] - first_in(p, p0);
+            return c;
+        };
+        const long long cap = std::min(pp.top_blocks, kTopMaxBlocks);
+        int l0 = n_levels;
+        while (pp.top_rows > 0 && l0 > 0 &&
+               P.lev_ptr[l0] - P.lev_ptr[l0 - 1] <= pp.top_rows &&
+               n - P.lev_ptr[l0 - 1] <= kTopMaxRows && blocks_from(P.lev_ptr[l0 - 1]) <= cap)
+            --l0;
+        for (;; ++l0) {  // shrink from the bottom of the region until its arena fits
+            if (n - P.lev_ptr[l0] < kTopMin) l0 = n_levels;
+            if (build_top(P, l0, [&](int len, int rows) { return lanes(len, rows); }) != BUILD_OK)
+                return BUILD_EINVAL;
+            if (P.top_R == 0 || top_arena_fp64(P) <= kTopMaxBytes) break;
         }
-        P.dense_s = s >= kDenseMin ? s : 0;
-        P.dense_l0 = n_levels - P.dense_s;
-        int mT = 0;  // longest part of a tail row left of the tail
-        for (int p = n - P.dense_s; p < n; ++p)
-            mT = std::max(mT, P.lu_diag[p] - (p - (n - P.dense_s)) - P.lu_ptr[p]);
-        P.dense_g = P.dense_s ? lanes(mT, P.dense_s) : 1;
     }
 
     // scalar nonzeros of J1 (rows dP_{B\R}, dQ_D; columns theta_{B\R}, Vm_D)

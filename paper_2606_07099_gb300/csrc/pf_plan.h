@@ -38,11 +38,28 @@ struct Plan {
     // lanes per gathered row (a power of two <= 32) for each level: forward (L part),
     // backward (U part) and Schur-target gathers
     std::vector<int> lev_gL, lev_gU, lev_gS;
-    // dense tail: the last dense_s levels (from dense_l0 on) hold one row each and the
-    // trailing dense_s x dense_s block of the filled pattern is full (0 = none)
-    int dense_s = 0, dense_l0 = 0;
-    // lanes per tail row for the gather of its part left of the tail (forward sweeps)
-    int dense_g = 1;
+    // top region: the trailing levels top_l0 .. n_levels - 1 (rows top_p0 .. n - 1, top_R
+    // of them; top_R = 0: none).  The factorisation and the sweeps take its pivots one at a
+    // time in shared memory instead of level by level (few rows per level there, so a
+    // level step is mostly latency).  Its blocks are the region rows' entries from column
+    // top_p0 on, numbered row by row (local index r <-> fac position top_map[r]); every
+    // list below holds local indices, which fit in 16 bits.
+    int top_l0 = 0, top_p0 = 0, top_R = 0;
+    int top_g = 1;                       // lanes per region row for its part left of the region
+    std::vector<int> top_map;            // [blocks] fac position of each region block
+    std::vector<int> top_split;          // [top_R] first entry of each region row inside it
+    // staged into shared memory as one array: piv[R] (pivot blocks), lc_ptr[R + 1] and
+    // lc[nl] (per pivot k, the L blocks (i, k), i > k), tr_ptr[R + 1] (per pivot, its range
+    // of Schur triples), then the sweep rounds: fwk[nfw] and fw[32 nfw] (ascending columns
+    // k, their L blocks (i, k), i > k), bwk[nbw] and bw[32 nbw] (descending columns, their
+    // U blocks (i, k), i < k).  A round holds one entry per lane: the lane that owns row i
+    // (i % 32) gets (i / 32) << 16 | block, the others -1; fwk holds the round's column,
+    // bwk its column << 1 | (1 for the column's first round)
+    std::vector<int> top_ints;
+    int top_nl = 0, top_nfw = 0, top_nbw = 0;
+    // Schur triples of the region pivots: (target, L block | U block << 16), per pivot
+    std::vector<int> top_tr_t, top_tr_lu;
+    int top_blocks() const { return (int)top_map.size(); }
 
     // block CSR of the filled L+U pattern in position order
     std::vector<int> lu_ptr, lu_col, lu_row, lu_diag, lu_mirror;
@@ -73,11 +90,13 @@ enum BuildStatus { BUILD_OK = 0, BUILD_EINVAL = 1, BUILD_ESINGULAR = 2 };
 
 // The schedule choices of a plan (none changes what is computed, only the elimination
 // order, the levels and how their work is split): the ordering's degree slack, the
-// largest dense tail, and the rule that splits a long gather over lane groups (rows
-// longer than split_len blocks on levels of at most split_rows rows).
+// top region (trailing levels of at most top_rows rows each, while the region holds at
+// most top_blocks blocks; top_rows 0 = none), and the rule that splits a long gather over
+// lane groups (rows longer than split_len blocks on levels of at most split_rows rows).
 struct PlanParams {
     int order_slack = 1;
-    int dense_max = 32;
+    int top_rows = 4;
+    int top_blocks = 2048;
     int split_len = 8;
     int split_rows = 128;
 };
@@ -100,9 +119,15 @@ void minimum_degree(const std::vector<std::vector<int>>& adj,
 // minimum degree on the 118- to 2000-bus grids for 1-3 % more fill.
 constexpr int kOrderSlack = 1;
 
-// Largest dense tail the factorisation stages in shared memory (32 x 32 blocks: 16 KB in
-// FP32, 32 KB in FP64 per scenario), and the smallest worth it.
-constexpr int kDenseMax = 32;
-constexpr int kDenseMin = 3;
+// Smallest top region worth its pivot-by-pivot schedule (rows), and the largest number of
+// blocks a region may hold (its local indices are 16-bit).
+constexpr int kTopMin = 3;
+constexpr int kTopMaxBlocks = 65534;  // local indices (and the scratch block) in 16 bits
+// Largest region in rows: each lane of the sweeping warp holds its rows' x in registers,
+// 4 per lane (kTopSlots of the device code).
+constexpr int kTopMaxRows = 128;
+// Largest shared-memory arena of a region in FP64 (blocks of 32 bytes, the solve vector
+// and the lists), so that it fits a CTA with room to spare for the rest of the kernel.
+constexpr long long kTopMaxBytes = 160 * 1024;
 
 }  // namespace pf

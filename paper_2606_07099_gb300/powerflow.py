@@ -127,8 +127,8 @@ class PowerFlow:
     """One network plan (pf_create) on the current CUDA device."""
 
     def __init__(self, n_bus, y_indptr, y_indices, y_re, y_im, bus_type, plan=None):
-        """``plan``: schedule choices (dict with any of order_slack, dense_max, split_len,
-        split_rows; pf_create_ex), or None for the defaults."""
+        """``plan``: schedule choices (dict with any of order_slack, top_rows, top_blocks,
+        split_len, split_rows; pf_create_ex), or None for the defaults."""
         lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("libpf needs a CUDA device")
@@ -668,9 +668,10 @@ def autotune_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, 
     return {"group_threads": res.group_threads, "placement": res.placement, "ms": res.ms}
 
 
-# Schedule candidates of the plan autotuner: the ordering's degree slack and the dense
-# tail's cap (split rules at their defaults).
-SCHEDULES = tuple({"order_slack": sl, "dense_max": dm} for sl in (0, 1, 2) for dm in (16, 32))
+# Schedule candidates of the plan autotuner: the ordering's degree slack and the top
+# region's row and block caps (split rules at their defaults).
+SCHEDULES = tuple({"order_slack": sl, "top_rows": tr, "top_blocks": tb}
+                  for sl in (0, 1) for tr, tb in ((4, 2048), (4, 4096), (0, 0)))
 
 
 def _time_ms(fn, reps=3):

@@ -213,26 +213,30 @@ def test_jacobian_template_is_the_oracle_pattern(pfm, name):
 
 
 @pytest.mark.parametrize("name", ["c0", "c1", "c2", "c4b", "c4c"])
-def test_dense_tail_is_the_largest_full_single_row_tail(pfm, name):
-    """The plan's dense tail (factored densely in shared memory): its levels hold one
-    pivot each, its rows are full from the tail's first position on, it is as long as
-    those two rules and the 32-block cap allow, and shorter than 3 it is not used."""
+def test_top_region_is_the_largest_allowed(pfm, name):
+    """The plan's top region (pivots factored and swept one at a time in shared memory):
+    its levels are the trailing ones, each of at most 4 rows (the default row cap), its
+    blocks -- its rows' entries from its first row on -- number at most 2048 (the
+    default block cap), its rows at most 128, it reaches down as far as those rules
+    allow (the shared-memory byte cap does not bind on these grids), and under 3 rows it
+    is not used."""
     g = configs.raw_grid(name)
     ip, ix, gg, bb = _ybus(pfm, g)
     info, pos2bus, lu_ptr, lu_col, lev_ptr = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)
-    n, L, s = info["n_block"], info["n_levels"], info["dense_tail"]
+    n, L = info["n_block"], info["n_levels"]
     sizes = np.diff(lev_ptr)
 
-    def ok(c):
-        if c > L or np.any(sizes[L - c:] != 1):
-            return False
-        p0 = n - c
-        return all(np.count_nonzero(lu_col[lu_ptr[p]:lu_ptr[p + 1]] >= p0) == c
+    def blocks(p0):
+        return sum(int(np.count_nonzero(lu_col[lu_ptr[p]:lu_ptr[p + 1]] >= p0))
                    for p in range(p0, n))
 
-    longest = 0
-    while longest < 32 and ok(longest + 1):
-        longest += 1
-    assert s == (longest if longest >= 3 else 0)
-    if s:
-        assert ok(s)
+    l0 = L
+    while (l0 > 0 and sizes[l0 - 1] <= 4 and n - lev_ptr[l0 - 1] <= 128
+           and blocks(lev_ptr[l0 - 1]) <= 2048):
+        l0 -= 1
+    rows = n - lev_ptr[l0]
+    if rows < 3:
+        l0, rows = L, 0
+    assert info["top_pivots"] == rows
+    assert info["top_levels"] == L - l0
+    assert info["top_blocks"] == (blocks(lev_ptr[l0]) if rows else 0)

@@ -1,4 +1,4 @@
-"""Plan schedule choices (pf_create_ex: ordering slack, dense-tail cap, gather split rule)
+"""Plan schedule choices (pf_create_ex: ordering slack, top-region caps, gather split rule)
 and the schedule autotuners (GPU).  A schedule changes the elimination order, the level
 schedule and how the levels' work is split -- never what is computed -- so every
 schedule must reach the oracle's solution with the oracle's flags and iterations."""
@@ -10,9 +10,10 @@ from gpu_common import (check_every_solution, compare, ensure_built, mismatch_ch
 
 pytestmark = pytest.mark.gpu
 KEYS = ("Vm", "Va", "Pg", "Qg", "iters", "status", "final_mismatch")
-SCHEDULES = ({"order_slack": 0, "dense_max": 0}, {"order_slack": 2, "dense_max": 16},
-             {"order_slack": 1, "dense_max": 32, "split_len": 1000000},
-             {"order_slack": 0, "dense_max": 32, "split_len": 4, "split_rows": 1000000})
+SCHEDULES = ({"order_slack": 0, "top_rows": 0}, {"order_slack": 2, "top_rows": 1, "top_blocks": 64},
+             {"order_slack": 1, "top_rows": 8, "top_blocks": 8192, "split_len": 1000000},
+             {"order_slack": 0, "top_rows": 1000, "top_blocks": 65534, "split_len": 4,
+              "split_rows": 1000000})
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +46,8 @@ def test_every_schedule_reaches_the_oracle_solution(pm, name, n):
 def test_bad_schedule_is_refused(pm):
     from paper_2606_07099_gb300._lib import PFError
     g, _ = workload("c0")
-    for bad in ({"order_slack": -1}, {"order_slack": 9}, {"dense_max": -1}, {"split_len": 0},
+    for bad in ({"order_slack": -1}, {"order_slack": 9}, {"top_rows": -1}, {"top_blocks": -1},
+                {"top_blocks": 65535}, {"split_len": 0},
                 {"split_rows": -1}):
         with pytest.raises(PFError):
             pm.PowerFlow.from_grid(g, bad)
