@@ -188,15 +188,18 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices,
  *     per block in the mixed form, 32 in FP64, plus the lists), instead of one
  *     barrier-separated step per level.  top_rows 0 = no region; regions under 3 rows
  *     are not used;
+ *   top_min_pivots: networks with fewer pivot blocks get no region (their level steps
+ *     are cheap, and a region's shared memory would cost scenarios in flight);
  *   split_len, split_rows: on levels of at most split_rows rows, a gathered row longer
  *     than split_len blocks is split over a power-of-two group of lanes (about four
  *     blocks each, at most 32 lanes), reduced in a fixed order.
- * pf_plan_opts_default writes the defaults pf_create uses (1, 4, 2048, 8, 128).
+ * pf_plan_opts_default writes the defaults pf_create uses (1, 4, 2048, 1024, 8, 128).
  */
 typedef struct {
     int order_slack;
     int top_rows;
     int top_blocks;
+    int top_min_pivots;
     int split_len;
     int split_rows;
 } pf_plan_opts;
@@ -205,8 +208,8 @@ void pf_plan_opts_default(pf_plan_opts* opts);
 
 /*
  * pf_create_ex -- pf_create with explicit schedule choices (host, NULL = the defaults).
- * Errors: as pf_create, and PF_EINVAL for order_slack outside 0..8, a negative top_rows
- * or split_rows, top_blocks outside 0..65534, or split_len < 1.
+ * Errors: as pf_create, and PF_EINVAL for order_slack outside 0..8, a negative top_rows,
+ * top_min_pivots or split_rows, top_blocks outside 0..65534, or split_len < 1.
  */
 pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices,
                     const double* y_re, const double* y_im, const int* bus_type,

@@ -38,7 +38,7 @@ class SolveOpts(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("order_slack", C.c_int), ("top_rows", C.c_int), ("top_blocks", C.c_int),
-                ("split_len", C.c_int), ("split_rows", C.c_int)]
+                ("top_min_pivots", C.c_int), ("split_len", C.c_int), ("split_rows", C.c_int)]
 
 
 class TuneResult(C.Structure):

@@ -632,6 +632,7 @@ void pf_plan_opts_default(pf_plan_opts* o) {
     o->order_slack = d.order_slack;
     o->top_rows = d.top_rows;
     o->top_blocks = d.top_blocks;
+    o->top_min_pivots = d.top_min_pivots;
     o->split_len = d.split_len;
     o->split_rows = d.split_rows;
 }
@@ -650,11 +651,13 @@ pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices, const 
     if (plan_opts) {
         if (plan_opts->order_slack < 0 || plan_opts->order_slack > 8 || plan_opts->top_rows < 0 ||
             plan_opts->top_blocks < 0 || plan_opts->top_blocks > pf::kTopMaxBlocks ||
+            plan_opts->top_min_pivots < 0 ||
             plan_opts->split_len < 1 || plan_opts->split_rows < 0)
             return PF_EINVAL;
         pp.order_slack = plan_opts->order_slack;
         pp.top_rows = plan_opts->top_rows;
         pp.top_blocks = plan_opts->top_blocks;
+        pp.top_min_pivots = plan_opts->top_min_pivots;
         pp.split_len = plan_opts->split_len;
         pp.split_rows = plan_opts->split_rows;
     }

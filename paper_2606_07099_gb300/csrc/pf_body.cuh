@@ -462,12 +462,17 @@ __device__ __forceinline__ void top_bar(int nt) {
 }
 
 // The region's pivots on one scenario's arena A, by threads t = 0 .. nt - 1 (each calls it,
-// `bar` is their barrier).  One barrier per pivot: each Schur triple of pivot k scales its
-// L block on the fly, L(i,k) = A(i,k) P_k^-1 (the same product the stored L block gets),
-// and the stores of column k's L blocks and of the pivot inverse are deferred to pivot
-// k + 1's round, when no thread reads those blocks any more (pivot k + 1 reads column
-// k + 1 and row k + 1 only, and its targets lie beyond both).  bk is set if a pivot was
-// singular.
+// `bar` is their barrier); bk is set if a pivot was singular.
+//
+// FP32: one barrier per pivot.  Each Schur triple of pivot k scales its L block on the fly,
+// L(i,k) = A(i,k) P_k^-1 (the same product the stored L block gets), and the stores of
+// column k's L blocks and of the pivot inverse are deferred to pivot k + 1's round, when
+// no thread reads those blocks any more (pivot k + 1 reads column k + 1 and row k + 1
+// only, and its targets lie beyond both); every thread forms the pivot inverse.
+// FP64: two barriers per pivot, as in the level schedule (L column scaling, then the
+// Schur triples): a 2x2 inverse, and the scaling repeated in every triple, would cost
+// each FP64 warp instruction the scarce FP64 pipe, so only the threads that scale an L
+// block (and thread 0) form the inverse.
 template <typename FT, typename Bar>
 __device__ __forceinline__ void top_factor(const DevPlan& P, const TopArena<FT>& A, int t, int nt,
                                            Bar bar, int& bk) {
@@ -486,6 +491,56 @@ __device__ __forceinline__ void top_factor(const DevPlan& P, const TopArena<FT>&
         nx[j] = c < trp[1] ? __ldg(P.top_tr + c) : idle;
     }
     Blk<FT> dprev{FT(0), FT(0), FT(0), FT(0)};
+    if constexpr (sizeof(FT) == 8) {
+        for (int k = 0; k < R; ++k) {
+            int2 cur[PF];
+#pragma unroll
+            for (int j = 0; j < PF; ++j) cur[j] = nx[j];
+            if (k + 1 < R) {
+                const int d0 = trp[k + 1], d1 = trp[k + 2];
+#pragma unroll
+                for (int j = 0; j < PF; ++j) {
+                    const int c = d0 + t + j * nt;
+                    nx[j] = c < d1 ? __ldg(P.top_tr + c) : idle;
+                }
+            }
+            const int l0 = lcp[k], l1 = lcp[k + 1];
+            Blk<FT> d = dprev;
+            if (t == 0 || l0 + t < l1) d = inv2(ldb(T, piv[k]), &bk);
+            for (int c = l0 + t; c < l1; c += nt) {  // L(i, k) <- A(i, k) A(k, k)^-1
+                const int li = lc[c] & 0xffff;
+                stb(T, li, mul(ldb(T, li), d));
+            }
+            bar();
+            if (t == 0) stb(T, piv[k], d);  // no triple of this pivot reads the pivot block
+#pragma unroll
+            for (int j = 0; j < PF; ++j) {
+                if (cur[j].x >= 0) {
+                    const unsigned lu = (unsigned)cur[j].y;
+                    const Blk<FT> x = ldb(T, (int)(lu & 0xffffu)), y = ldb(T, (int)(lu >> 16));
+                    Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+                    acc.a += x.a * y.a + x.b * y.c;
+                    acc.b += x.a * y.b + x.b * y.d;
+                    acc.c += x.c * y.a + x.d * y.c;
+                    acc.d += x.c * y.b + x.d * y.d;
+                    stb(T, cur[j].x, sub_blk(ldb(T, cur[j].x), acc));
+                }
+            }
+            for (int c = trp[k] + t + PF * nt; c < trp[k + 1]; c += nt) {
+                const int2 tr = __ldg(P.top_tr + c);
+                const unsigned lu = (unsigned)tr.y;
+                const Blk<FT> x = ldb(T, (int)(lu & 0xffffu)), y = ldb(T, (int)(lu >> 16));
+                Blk<FT> acc{FT(0), FT(0), FT(0), FT(0)};
+                acc.a += x.a * y.a + x.b * y.c;
+                acc.b += x.a * y.b + x.b * y.d;
+                acc.c += x.c * y.a + x.d * y.c;
+                acc.d += x.c * y.b + x.d * y.d;
+                stb(T, tr.x, sub_blk(ldb(T, tr.x), acc));
+            }
+            bar();
+        }
+        return;
+    }
     for (int k = 0; k < R; ++k) {
         int2 cur[PF];
 #pragma unroll

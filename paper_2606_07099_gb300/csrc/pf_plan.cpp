@@ -474,7 +474,7 @@ BuildStatus build_plan(int n_bus, const int* y_indptr, const int* y_indices,
         };
         const long long cap = std::min(pp.top_blocks, kTopMaxBlocks);
         int l0 = n_levels;
-        while (pp.top_rows > 0 && l0 > 0 &&
+        while (pp.top_rows > 0 && n >= pp.top_min_pivots && l0 > 0 &&
                P.lev_ptr[l0] - P.lev_ptr[l0 - 1] <= pp.top_rows &&
                n - P.lev_ptr[l0 - 1] <= kTopMaxRows && blocks_from(P.lev_ptr[l0 - 1]) <= cap)
             --l0;

@@ -91,12 +91,14 @@ enum BuildStatus { BUILD_OK = 0, BUILD_EINVAL = 1, BUILD_ESINGULAR = 2 };
 // The schedule choices of a plan (none changes what is computed, only the elimination
 // order, the levels and how their work is split): the ordering's degree slack, the
 // top region (trailing levels of at most top_rows rows each, while the region holds at
-// most top_blocks blocks; top_rows 0 = none), and the rule that splits a long gather over
+// most top_blocks blocks; top_rows 0, or fewer than top_min_pivots pivots in the network:
+// none), and the rule that splits a long gather over
 // lane groups (rows longer than split_len blocks on levels of at most split_rows rows).
 struct PlanParams {
     int order_slack = 1;
     int top_rows = 4;
     int top_blocks = 2048;
+    int top_min_pivots = 1024;  // smaller networks get no region
     int split_len = 8;
     int split_rows = 128;
 };

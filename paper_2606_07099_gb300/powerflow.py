@@ -128,7 +128,7 @@ class PowerFlow:
 
     def __init__(self, n_bus, y_indptr, y_indices, y_re, y_im, bus_type, plan=None):
         """``plan``: schedule choices (dict with any of order_slack, top_rows, top_blocks,
-        split_len, split_rows; pf_create_ex), or None for the defaults."""
+        top_min_pivots, split_len, split_rows; pf_create_ex), or None for the defaults."""
         lib = L.load()
         if not torch.cuda.is_available():
             raise RuntimeError("libpf needs a CUDA device")

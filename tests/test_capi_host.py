@@ -218,8 +218,8 @@ def test_top_region_is_the_largest_allowed(pfm, name):
     its levels are the trailing ones, each of at most 4 rows (the default row cap), its
     blocks -- its rows' entries from its first row on -- number at most 2048 (the
     default block cap), its rows at most 128, it reaches down as far as those rules
-    allow (the shared-memory byte cap does not bind on these grids), and under 3 rows it
-    is not used."""
+    allow (the shared-memory byte cap does not bind on these grids), under 3 rows it is
+    not used, and networks of fewer than 1024 pivots get none (the default)."""
     g = configs.raw_grid(name)
     ip, ix, gg, bb = _ybus(pfm, g)
     info, pos2bus, lu_ptr, lu_col, lev_ptr = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)
@@ -231,7 +231,7 @@ def test_top_region_is_the_largest_allowed(pfm, name):
                    for p in range(p0, n))
 
     l0 = L
-    while (l0 > 0 and sizes[l0 - 1] <= 4 and n - lev_ptr[l0 - 1] <= 128
+    while (n >= 1024 and l0 > 0 and sizes[l0 - 1] <= 4 and n - lev_ptr[l0 - 1] <= 128
            and blocks(lev_ptr[l0 - 1]) <= 2048):
         l0 -= 1
     rows = n - lev_ptr[l0]

@@ -10,10 +10,12 @@ from gpu_common import (check_every_solution, compare, ensure_built, mismatch_ch
 
 pytestmark = pytest.mark.gpu
 KEYS = ("Vm", "Va", "Pg", "Qg", "iters", "status", "final_mismatch")
-SCHEDULES = ({"order_slack": 0, "top_rows": 0}, {"order_slack": 2, "top_rows": 1, "top_blocks": 64},
-             {"order_slack": 1, "top_rows": 8, "top_blocks": 8192, "split_len": 1000000},
-             {"order_slack": 0, "top_rows": 1000, "top_blocks": 65534, "split_len": 4,
-              "split_rows": 1000000})
+SCHEDULES = ({"order_slack": 0, "top_rows": 0},
+             {"order_slack": 2, "top_rows": 1, "top_blocks": 64, "top_min_pivots": 0},
+             {"order_slack": 1, "top_rows": 8, "top_blocks": 8192, "top_min_pivots": 0,
+              "split_len": 1000000},
+             {"order_slack": 0, "top_rows": 1000, "top_blocks": 65534, "top_min_pivots": 0,
+              "split_len": 4, "split_rows": 1000000})
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +49,7 @@ def test_bad_schedule_is_refused(pm):
     from paper_2606_07099_gb300._lib import PFError
     g, _ = workload("c0")
     for bad in ({"order_slack": -1}, {"order_slack": 9}, {"top_rows": -1}, {"top_blocks": -1},
-                {"top_blocks": 65535}, {"split_len": 0},
+                {"top_blocks": 65535}, {"top_min_pivots": -1}, {"split_len": 0},
                 {"split_rows": -1}):
         with pytest.raises(PFError):
             pm.PowerFlow.from_grid(g, bad)
