@@ -195,6 +195,8 @@ int auto_cluster(const pf_handle* h, int batch, int S) {
     return c;
 }
 
+pf::SiLayout si_layout(const pf_handle* h, int ft, const LaunchCfg& c);
+
 // The launch configuration of a solve.  `si_ok`: the interleaved placement may serve this
 // call (a forward solve without kept factors); where it may not, an automatic choice
 // falls back to the heuristic placement and an explicit request is refused (-1).
@@ -232,6 +234,9 @@ LaunchCfg resolve(const pf_handle* h, const pf_solve_opts* o, int batch = 0, boo
                                : (tuned_si && t.cluster ? t.cluster : auto_cluster(h, batch, c.S));
         c.threads = o->group_threads ? o->group_threads
                                      : (tuned_si && t.group_threads ? t.group_threads : 1024);
+        // an automatic cluster size grows until the pack's top regions fit its CTAs
+        if (!o->cluster && !(tuned_si && t.cluster))
+            while (c.cluster < 16 && si_layout(h, ft, c).smem_bytes > smem_budget(h)) c.cluster *= 2;
     }
     return c;
 }
@@ -274,6 +279,21 @@ pf::SiLayout si_layout(const pf_handle* h, int ft, const LaunchCfg& c) {
     L.off_ctl = take(3 * 32 * sizeof(unsigned long long) + 32 * sizeof(unsigned int));
     L.pack_bytes = o;
     L.smem_bytes = (size_t)c.threads * 2 * ft;  // one FT2 partial sum per thread
+    L.top_slots = 0;
+    L.top_stride = 0;
+    L.smem_top_off = pf::align_up(L.smem_bytes, 16);
+    if (P.top_R > 0) {
+        // as many scenarios' regions as fit (a power of two), at most this CTA's share
+        const size_t lists = pf::align_up((size_t)4 * P.top_ints.size(), 16);
+        const size_t budget = smem_budget(h);
+        L.top_stride = pf::top_ints_off(P.top_blocks(), P.top_R, ft);
+        const int share = (c.S + c.cluster - 1) / c.cluster;
+        int slots = 1;
+        while (slots < share && L.smem_top_off + (size_t)(2 * slots) * L.top_stride + lists <= budget)
+            slots *= 2;
+        L.top_slots = slots;
+        L.smem_bytes = L.smem_top_off + (size_t)L.top_slots * L.top_stride + lists;
+    }
     return L;
 }
 

@@ -844,10 +844,10 @@ __device__ __forceinline__ void top_upd(FT (&v0)[kTopSlots], FT (&v1)[kTopSlots]
 // Each row receives its updates in column order.  No round branches: an empty entry
 // (-1) reads block 0 into no slot, and the rounds' loads depend on the plan only, so
 // several rounds' loads are in flight together.  Reads ts (the rows after their part
-// left of the region), writes the region's solution to x[2 p0 ..].
-template <typename FT>
+// left of the region), hands row i's solution to out(i, x0, x1).
+template <typename FT, typename Out>
 __device__ __forceinline__ void top_sweeps(const DevPlan& P, const TopArena<FT>& A, int lane,
-                                           const FT* ts, FT* x) {
+                                           const FT* ts, Out out) {
     const int R = P.top_R;
     const int* piv = A.I;
     const int* fwk = piv + R + (R + 1) + P.top_nl + (R + 1);
@@ -891,10 +891,7 @@ __device__ __forceinline__ void top_sweeps(const DevPlan& P, const TopArena<FT>&
 #pragma unroll
     for (int j = 0; j < kTopSlots; ++j) {
         const int i = j * 32 + lane;
-        if (i < R) {
-            x[2 * (P.top_p0 + i)] = v0[j];
-            x[2 * (P.top_p0 + i) + 1] = v1[j];
-        }
+        if (i < R) out(i, v0[j], v1[j]);
     }
 }
 
@@ -935,7 +932,11 @@ __device__ void top_solve(const DevPlan& P, const FT* fac, FT* x, size_t arena) 
         }
     }
     gsync<W>();
-    if (GTID < 32) top_sweeps<FT>(P, A, GTID, A.ts, x);
+    if (GTID < 32)
+        top_sweeps<FT>(P, A, GTID, A.ts, [x, p0](int i, FT x0, FT x1) {
+            x[2 * (p0 + i)] = x0;
+            x[2 * (p0 + i) + 1] = x1;
+        });
     gsync<W>();
 }
 

@@ -157,7 +157,14 @@ struct SiLayout {
     size_t off_F, off_DZ;   // double2 [n][S]: F1 and the accumulated Newton step
     size_t off_X;       // FT2 [n][S]: the triangular-solve vector
     size_t off_ctl;     // reduction buffers (3 x 32 u64) and singular flags (32 u32)
-    size_t smem_bytes;  // dynamic shared memory per CTA (lane-group reductions)
+    size_t smem_bytes;  // dynamic shared memory per CTA (lane-group reductions, top region)
+    // the top region of the pack's scenarios: scenario s on CTA s mod cluster, in the
+    // CTA's arena at smem_top_off of the dynamic shared memory: top_slots slots of
+    // top_stride bytes (blocks and solve vector), then the plan's lists once.  A CTA with
+    // more scenarios than slots takes them top_slots at a time, keeping the factored
+    // regions in the pack's factor between the factorisation and the sweeps
+    size_t smem_top_off, top_stride;
+    int top_slots;
 };
 
 struct SiArgs {

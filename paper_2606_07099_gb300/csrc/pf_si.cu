@@ -508,12 +508,133 @@ __device__ void si_sweep_level(const DevPlan& P, const Pack<FT>& k, int l, int g
     pack_sync<CL>();
 }
 
+// ---------------------------------------------------------------- top region
+// The plan's top region (see top_factor / top_sweeps): scenario s of the pack is factored
+// and swept by CTA s mod C, in slot s / C of that CTA's arena, with the per-scenario
+// form's steps and order.  The levels below the region go as before, over the cluster.
+template <typename FT>
+__device__ __forceinline__ TopArena<FT> si_top_arena(const DevPlan& P, const SiLayout& L, int j) {
+    extern __shared__ __align__(16) unsigned char pf_dyn_smem[];
+    unsigned char* a = pf_dyn_smem + L.smem_top_off + (size_t)j * L.top_stride;
+    return {reinterpret_cast<FT*>(a),
+            reinterpret_cast<FT*>(a + top_ts_off(P.top_nblk, (int)sizeof(FT))),
+            reinterpret_cast<int*>(pf_dyn_smem + L.smem_top_off + (size_t)L.top_slots * L.top_stride)};
+}
+
+// Scenarios of the pack on this CTA: slot j holds scenario rank + j C.
+__device__ __forceinline__ int si_top_nsc(int S, unsigned rank, unsigned C) {
+    return (int)rank < S ? (S - 1 - (int)rank) / (int)C + 1 : 0;
+}
+
+// The region's factorisation for this CTA's scenarios (after the levels below it and
+// their pack barrier); the caller ends it with a pack barrier.  `go` is the thread's own
+// lane's flag; a slot's scenario is read from its lane.  With more scenarios than slots
+// they go top_slots at a time, each chunk's factored regions written back into the pack's
+// factor for the sweeps.
 template <typename FT, int S, bool CL>
-__device__ void si_solve(const DevPlan& P, const Pack<FT>& k, int gs, int TS, int s, int slot,
-                         int NS, int rank, int C, bool go, typename V2<FT>::T* part) {
-    for (int l = 0; l < P.n_levels; ++l)
+__device__ void si_top_lu(const DevPlan& P, const SiLayout& L, const Pack<FT>& k, unsigned rank,
+                          unsigned C, bool go) {
+    const int nsc = si_top_nsc(S, rank, C);
+    if (nsc == 0) return;  // uniform over the CTA
+    const int nb = P.top_nblk;
+    const bool resident = nsc <= L.top_slots;
+    int* I = si_top_arena<FT>(P, L, 0).I;
+    for (int q = (int)threadIdx.x; q < P.top_nints; q += (int)blockDim.x) I[q] = __ldg(P.top_ints + q);
+    for (int c0 = 0; c0 < nsc; c0 += L.top_slots) {
+        const int m = min(L.top_slots, nsc - c0);  // a power of two that divides blockDim
+        for (int u = (int)threadIdx.x; u < m * nb; u += (int)blockDim.x) {
+            const int j = u / nb, r = u - j * nb;
+            stb(si_top_arena<FT>(P, L, j).T, r,
+                ldf<S, CL>(k.fac, __ldg(P.top_map + r), (int)rank + (c0 + j) * (int)C));
+        }
+        __syncthreads();
+        const int j = (int)threadIdx.x & (m - 1), sj = (int)rank + (c0 + j) * (int)C;
+        const bool gj = __shfl_sync(0xffffffffu, go, sj & 31);
+        int bk = 0;
+        top_factor<FT>(P, si_top_arena<FT>(P, L, j), (int)threadIdx.x / m, (int)blockDim.x / m,
+                       [] { __syncthreads(); }, bk);
+        if (gj && bk && (int)threadIdx.x < m) atomicOr(k.sing + sj, 1u);
+        __syncthreads();
+        if (!resident) {
+            for (int u = (int)threadIdx.x; u < m * nb; u += (int)blockDim.x) {
+                const int jj = u / nb, r = u - jj * nb;
+                stf<S, CL>(k.fac, __ldg(P.top_map + r), (int)rank + (c0 + jj) * (int)C,
+                           ldb(si_top_arena<FT>(P, L, jj).T, r));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The region's sweeps for this CTA's scenarios (after the forward levels below it and
+// their pack barrier): each region row's part left of the region, gathered from the
+// pack's factor and solve vector (top_g lanes per row), then one warp per scenario sweeps
+// the region and writes its x back into the pack's solve vector.  The caller ends it with
+// a pack barrier.  Scenarios whose regions are not resident are staged again from the
+// pack's factor, top_slots at a time.
+template <typename FT, int S, bool CL>
+__device__ void si_top_solve(const DevPlan& P, const SiLayout& L, const Pack<FT>& k, unsigned rank,
+                             unsigned C, bool go) {
+    const int nsc = si_top_nsc(S, rank, C);
+    if (nsc == 0) return;
+    const int R = P.top_R, p0 = P.top_p0, G = P.top_g, nb = P.top_nblk;
+    const bool resident = nsc <= L.top_slots;
+    for (int c0 = 0; c0 < nsc; c0 += L.top_slots) {
+        const int m = min(L.top_slots, nsc - c0);
+        if (!resident)
+            for (int u = (int)threadIdx.x; u < m * nb; u += (int)blockDim.x) {
+                const int j = u / nb, r = u - j * nb;
+                stb(si_top_arena<FT>(P, L, j).T, r,
+                    ldf<S, CL>(k.fac, __ldg(P.top_map + r), (int)rank + (c0 + j) * (int)C));
+            }
+        const int items = R * m * G;
+        for (int ub = 0; ub < items; ub += (int)blockDim.x) {  // every lane runs the same rounds
+            const int u = ub + (int)threadIdx.x;
+            const bool act = u < items;
+            const int g = u % G, rj = u / G, j = rj % m, r = rj / m;
+            const int sj = (int)rank + (c0 + j) * (int)C;
+            FT s0 = FT(0), s1 = FT(0);
+            if (act)
+                si_row_gather<FT, S, CL>(P, k, __ldg(P.lu_ptr + p0 + r) + g, __ldg(P.top_split + r),
+                                         G, sj, s0, s1);
+            for (int o = G >> 1; o; o >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            }
+            if (act && g == 0) {
+                const typename V2<FT>::T xv = ldm<CL>(k.X + ((size_t)(p0 + r) * S + sj));
+                FT* ts = si_top_arena<FT>(P, L, j).ts;
+                ts[2 * r] = xv.x - s0;
+                ts[2 * r + 1] = xv.y - s1;
+            }
+        }
+        __syncthreads();
+        const int nw = (int)blockDim.x >> 5, w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+        for (int j = w; j < m; j += nw) {
+            const int sj = (int)rank + (c0 + j) * (int)C;
+            const bool gj = __shfl_sync(0xffffffffu, go, sj & 31);
+            if (!gj) continue;  // uniform over the warp
+            const TopArena<FT> A = si_top_arena<FT>(P, L, j);
+            top_sweeps<FT>(P, A, lane, A.ts, [&k, p0, sj](int i, FT x0, FT x1) {
+                stm<CL>(k.X + ((size_t)(p0 + i) * S + sj), mk2(x0, x1));
+            });
+        }
+        __syncthreads();
+    }
+}
+
+template <typename FT, int S, bool CL>
+__device__ void si_solve(const DevPlan& P, const SiLayout& L, const Pack<FT>& k, int gs, int TS,
+                         int s, int slot, int NS, int rank, int C, bool go,
+                         typename V2<FT>::T* part) {
+    const int nl = P.top_R ? P.top_l0 : P.n_levels;
+    for (int l = 0; l < nl; ++l)
         si_sweep_level<FT, S, false, CL>(P, k, l, gs, TS, s, slot, NS, rank, C, go, part);
-    for (int l = P.n_levels - 1; l >= 0; --l)
+    if (P.top_R) {
+        si_top_solve<FT, S, CL>(P, L, k, (unsigned)rank, (unsigned)C, go);
+        pack_sync<CL>();
+    }
+    for (int l = nl - 1; l >= 0; --l)
         si_sweep_level<FT, S, true, CL>(P, k, l, gs, TS, s, slot, NS, rank, C, go, part);
 }
 
@@ -695,12 +816,17 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
         const bool go = status < 0;
         si_fill<S, CL>(P, k, gs, TS, s, go);
         pack_sync<CL>();
-        for (int l = 0; l < P.n_levels; ++l) si_lu_level<FT, S, CL>(P, k, l, gs, TS, s, go);
+        const int nl = P.top_R ? P.top_l0 : P.n_levels;
+        for (int l = 0; l < nl; ++l) si_lu_level<FT, S, CL>(P, k, l, gs, TS, s, go);
+        if (P.top_R) {
+            si_top_lu<FT, S, CL>(P, A.L, k, rank, C, go);
+            pack_sync<CL>();
+        }
         // read after the last level's barrier, through L2 (the flags are set by atomics)
         if (go && __ldcg(k.sing + s) != 0u) status = 3;
         const bool g2 = status < 0;
         if (lanes_where<S>(g2) == 0u) break;
-        si_solve<FT, S, CL>(P, k, gs, TS, s, slot, NS, (int)rank, (int)C, g2, part);
+        si_solve<FT, S, CL>(P, A.L, k, gs, TS, s, slot, NS, (int)rank, (int)C, g2, part);
         if constexpr (mixed) {
             si_accumulate<S, CL>(P, k, gs, TS, s, g2, true);
             pack_sync<CL>();
@@ -712,7 +838,7 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
                 // forcing term min(ir_rtol, ||F1||): see the per-scenario form
                 if (refine && A.ir_rtol > 0.0 && rmax <= fmin(A.ir_rtol, norm) * norm) refine = false;
                 if (lanes_where<S>(refine) == 0u) break;
-                si_solve<FT, S, CL>(P, k, gs, TS, s, slot, NS, (int)rank, (int)C, refine, part);
+                si_solve<FT, S, CL>(P, A.L, k, gs, TS, s, slot, NS, (int)rank, (int)C, refine, part);
                 si_accumulate<S, CL>(P, k, gs, TS, s, refine, false);
                 pack_sync<CL>();
                 if (sw + 1 >= sweeps) refine = false;
@@ -785,6 +911,9 @@ template <typename FT, int S, bool CL>
 static cudaError_t launch_s(const DevPlan& P, const SiArgs& A, cudaStream_t st) {
     cudaError_t e = prepare<FT, S, CL>();
     if (e != cudaSuccess) return e;
+    e = ensure_smem_limit(reinterpret_cast<const void*>(si::nr_solve_si_kernel<FT, S, CL>),
+                          A.L.smem_bytes);
+    if (e != cudaSuccess) return e;
     const int packs = (A.batch + S - 1) / S;
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = si_config<FT, S, CL>(packs * A.L.cluster, A.L.cluster,
@@ -815,6 +944,12 @@ template <typename FT, int S, bool CL>
 static cudaError_t fits_s(int cluster, int threads, size_t smem, bool* fits) {
     cudaError_t e = prepare<FT, S, CL>();
     if (e != cudaSuccess) return e;
+    if (ensure_smem_limit(reinterpret_cast<const void*>(si::nr_solve_si_kernel<FT, S, CL>), smem) !=
+        cudaSuccess) {
+        cudaGetLastError();  // more shared memory than a CTA may have: the shape does not fit
+        *fits = false;
+        return cudaSuccess;
+    }
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = si_config<FT, S, CL>(cluster, cluster, threads, smem, 0, at);
     int n = 0;
