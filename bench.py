@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "c1"
 WORKLOAD_DESC = ("synthetic 118-bus meshed grid (186 branches, 9 transformers, 1 slack, 53 PV, "
                  "64 PQ), 4096 load scenarios x U(0.7, 1.3), flat start, tol 1e-8 pu, max 20 iterations")
+# Plan schedules the headline's tuner compares: the default plan, and top regions of
+# levels of at most 2 or 4 rows whatever the network's size.
+HEADLINE_SCHEDULES = ({}, {"top_rows": 2, "top_min_pivots": 0}, {"top_rows": 4, "top_min_pivots": 0})
 METRIC = "PF solves/s at <=1e-8 pu mismatch (mixed precision form)"
 
 UNIT = "solves/s"
@@ -356,10 +359,9 @@ def gpu_leg(args, rank, world):
     secs = set(args.sections.split(","))
     tuned = {}
     from paper_2606_07099_gb300.powerflow import autotune_schedule
-    # the headline network keeps the default plan schedule: the schedule tuner found no
-    # faster one for its mixed solve, and its choice can slow the host-buffer path
     # the largest workspace any section needs, allocated once (captured graphs keep its address)
     pf.workspace(N, pf.make_opts("fp64", keep_factors=True, placement=3))
+    pfh = pf  # the headline solve's network plan (the default one unless tuned)
     hopts = dict(opts)  # the headline solve's options
     if args.shape:  # an explicit launch shape for the headline solve (no tuning for it)
         pl, th, pk, cl = (int(v) for v in args.shape.split(","))
@@ -368,10 +370,19 @@ def gpu_leg(args, rank, world):
                           "pack": pk, "cluster": cl, "fixed": True}
         if args.autotune and "fp64" in secs:
             tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
-    elif args.autotune:  # launch shape per precision, picked on these inputs (setup, not timed)
-        tuned["mixed"] = pf.autotune(Pd, Qd, Pg, Vset, **opts)
+    elif args.autotune:  # plan schedule and launch shape, picked on these inputs (setup)
+        # the headline's mixed solve: the default plan against top regions on this network
+        # (a small network gets none by default); the other sections keep the default plan
+        pfh, rep = autotune_schedule(g, Pd, Qd, Pg, Vset, schedules=HEADLINE_SCHEDULES, **opts)
+        tuned["mixed"] = {**rep["shape"], "schedule": rep["schedule"], "trials": rep["trials"]}
+        if pfh is not pf:
+            pfh.workspace(N, pfh.make_opts("mixed", keep_factors=False, placement=3))
+        # the default plan's own shapes (the per-scenario ones serve kept factors, reactive
+        # limits and the host-buffer solve)
+        tuned["mixed_default_plan"] = pf.autotune(Pd, Qd, Pg, Vset, **opts)
         if "fp64" in secs:
             tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
+    info = pfh.info()
 
     def graphed(fn):
         """Record one step into a CUDA graph (the whole Newton loop is one kernel)."""
@@ -384,8 +395,8 @@ def gpu_leg(args, rank, world):
             fn()
         return gr.replay
 
-    res = pf.solve(Pd, Qd, Pg, Vset, **hopts)
-    mixed_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, out=res, **hopts))
+    res = pfh.solve(Pd, Qd, Pg, Vset, **hopts)
+    mixed_fn = graphed(lambda: pfh.solve(Pd, Qd, Pg, Vset, out=res, **hopts))
     if "fp64" in secs:
         res64 = pf.solve(Pd, Qd, Pg, Vset, precision="fp64")
         fp64_fn = graphed(lambda: pf.solve(Pd, Qd, Pg, Vset, precision="fp64", out=res64))
@@ -614,7 +625,7 @@ def gpu_leg(args, rank, world):
     rese = SolveResult(Vm=out_host[0], Va=out_host[1], Pg=None, Qg=None, iters=None,
                        status=st_host, final_mismatch=None)
 
-    def e2e():
+    def e2e():  # the default plan (a top region slows this network's per-scenario kernels)
         pf.solve_host(*host_views, out=rese, **opts)
 
     none = [float("nan")]
