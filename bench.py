@@ -34,8 +34,9 @@ WORKLOAD = "c1"
 WORKLOAD_DESC = ("synthetic 118-bus meshed grid (186 branches, 9 transformers, 1 slack, 53 PV, "
                  "64 PQ), 4096 load scenarios x U(0.7, 1.3), flat start, tol 1e-8 pu, max 20 iterations")
 # Plan schedules the headline's tuner compares: the default plan, and top regions of
-# levels of at most 2 or 4 rows whatever the network's size.
-HEADLINE_SCHEDULES = ({}, {"top_rows": 2, "top_min_pivots": 0}, {"top_rows": 4, "top_min_pivots": 0})
+# levels of at most 2, 3 or 4 rows whatever the network's size.
+HEADLINE_SCHEDULES = ({}, {"top_rows": 2, "top_min_pivots": 0}, {"top_rows": 3, "top_min_pivots": 0},
+                      {"top_rows": 4, "top_min_pivots": 0})
 METRIC = "PF solves/s at <=1e-8 pu mismatch (mixed precision form)"
 
 UNIT = "solves/s"

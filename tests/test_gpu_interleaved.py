@@ -179,3 +179,39 @@ def test_autotune_may_pick_interleaved_and_keeps_results(PowerFlow):
     torch.cuda.synchronize()
     for k in KEYS:
         assert np.array_equal(ref[k], out[k]), k
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # the oracle's V/|V| at a zero voltage
+@pytest.mark.parametrize("name,plan", [("c2", None), ("c1", {"top_min_pivots": 0})])
+def test_singular_pivot_in_the_top_region(PowerFlow, name, plan):
+    """A zero-voltage PV bus whose pivot lies in the plan's top region (factored pivot by
+    pivot in shared memory) and one whose pivot lies below it: SINGULAR before the first
+    Newton step in both, in the per-scenario kernel and in the interleaved packs (a
+    region per CTA, and several regions on one CTA), the other scenarios as the oracle."""
+    from paper_2606_07099_gb300.powerflow import analyze
+    g, sc = workload(name, 16)
+    pf = PowerFlow.from_grid(g, plan)
+    R = pf.info()["top_pivots"]
+    assert R > 0
+    ip, ix, gg, bb = pf._arrays[:4]
+    pos2bus = analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)[1]
+    n = len(pos2bus)
+    top = [b for b in pos2bus[n - R:] if g.bus_type[b] == PV]
+    below = [b for b in pos2bus[:n - R] if g.bus_type[b] == PV]
+    assert top and below
+    bad = Scenarios(Pd=sc.Pd.copy(), Qd=sc.Qd.copy(), Pg=sc.Pg.copy(), Vset=sc.Vset.copy())
+    bad.Vset[2, top[0]] = 0.0
+    bad.Vset[5, below[0]] = 0.0
+    bad.Vset[13, top[-1]] = 0.0
+    hit = [2, 5, 13]
+    orc = run_oracle(g, bad, range(16))
+    assert all(orc[s]["status"] == O.SINGULAR and orc[s]["iters"] == 0 for s in hit)
+    for prec in ("fp64", "mixed"):
+        runs = [run_gpu(pf, bad, precision=prec, placement=3, group_threads=256),
+                si(pf, bad, S=4, C=4, threads=512, precision=prec),
+                si(pf, bad, S=8, C=1, threads=256, precision=prec)]
+        for gpu in runs:
+            assert np.all(gpu["status"][hit] == O.SINGULAR), (prec, gpu["status"])
+            assert np.all(gpu["iters"][hit] == 0)
+            worst = compare(gpu, orc, iter_slack=0 if prec == "fp64" else 1)
+            assert worst["irregular"] == 0
