@@ -116,9 +116,14 @@ size_t smem_budget(const pf_handle* h) {
 
 static_assert(pf::kTopMaxRows == 32 * pf::kTopSlots, "region rows: one register slot per row");
 
-// Shared memory of the top region's arena (its blocks, solve vector and lists).
-size_t top_bytes(const pf::Plan& P, int ft_bytes) {
-    return pf::top_arena_bytes(P.top_blocks(), P.top_R, (int)P.top_ints.size(), ft_bytes);
+// Shared memory an SM may give the adjoint's top-region arenas (see pf_adjoint).
+constexpr size_t kTopAdjSmemPerSm = 128 * 1024;
+
+// Shared memory of the top region's arena (its blocks, solve vector and lists: the
+// forward solve's, or with `adj` the adjoint's, which also holds the transposed rounds).
+size_t top_bytes(const pf::Plan& P, int ft_bytes, bool adj = false) {
+    return pf::top_arena_bytes(P.top_blocks(), P.top_R,
+                               adj ? (int)P.top_ints.size() : P.top_nints_fwd, ft_bytes);
 }
 
 // Default placement without tuning data: keep a scenario on chip only while at least
@@ -141,17 +146,16 @@ pf::SlotLayout make_layout(const pf_handle* h, int ft_bytes, int keep, int place
     L.fac_bytes = pf::align_up((size_t)P.nnzb() * 4 * ft_bytes, 16);
     // the top region's arena comes out of the budget first, then follows the placement's
     // own arrays (a multiple of 16 bytes: warp arenas are laid end to end)
-    const size_t top = top_bytes(P, ft_bytes);
+    const size_t top = top_bytes(P, ft_bytes), top_adj = top_bytes(P, ft_bytes, true);
     const size_t full = smem_budget(h);
-    const size_t budget = full > top ? full - top : 0;
-    L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes, budget,
-                  placement, (size_t)ft_bytes * 2 * (size_t)P.n);
-    L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes, budget,
-                  placement);
-    for (pf::KernelSmem* k : {&L.fwd, &L.adj}) {
-        k->smem_top_off = pf::align_up(k->smem_bytes, 16);
-        k->smem_bytes = k->smem_top_off + top;
-    }
+    L.fwd = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, false, nullptr), L.fac_bytes,
+                  full > top ? full - top : 0, placement, (size_t)ft_bytes * 2 * (size_t)P.n);
+    L.adj = place(pf::carve(nullptr, P.n_bus, P.n, ft_bytes, true, nullptr), L.fac_bytes,
+                  full > top_adj ? full - top_adj : 0, placement);
+    L.fwd.smem_top_off = pf::align_up(L.fwd.smem_bytes, 16);
+    L.fwd.smem_bytes = L.fwd.smem_top_off + top;
+    L.adj.smem_top_off = pf::align_up(L.adj.smem_bytes, 16);
+    L.adj.smem_bytes = L.adj.smem_top_off + top_adj;
     L.fac_global = (!L.fwd.fac_in_smem || keep) ? 1 : 0;
     size_t vec_global = 0;
     if (!L.fwd.vec_in_smem) vec_global = std::max(vec_global, L.fwd.vec_bytes);
@@ -284,7 +288,7 @@ pf::SiLayout si_layout(const pf_handle* h, int ft, const LaunchCfg& c) {
     L.smem_top_off = pf::align_up(L.smem_bytes, 16);
     if (P.top_R > 0) {
         // as many scenarios' regions as fit (a power of two), at most this CTA's share
-        const size_t lists = pf::align_up((size_t)4 * P.top_ints.size(), 16);
+        const size_t lists = pf::align_up((size_t)4 * P.top_nints_fwd, 16);
         const size_t budget = smem_budget(h);
         L.top_stride = pf::top_ints_off(P.top_blocks(), P.top_R, ft);
         const int share = (c.S + c.cluster - 1) / c.cluster;
@@ -568,6 +572,19 @@ pf_err adjoint_impl(pf_handle* h, int batch, const double* dVm, const double* dV
     A.adj_status = adj_status;
     A.ws = static_cast<char*>(workspace);
     A.L = L;
+    // The adjoint takes the top region in shared memory (its transposed sweeps, and a
+    // refactorisation) unless the region's arena, over the CTAs one SM holds at this CTA
+    // size (64 registers a thread), would take more than kTopAdjSmemPerSm of the SM's
+    // L1/shared memory: the adjoint's other phases read the scenario's vectors through
+    // L1.  Without it the kernel walks the region's levels like the others and needs no
+    // arena.
+    {
+        const pf::Plan& P = h->plan;
+        const int ft = h->last_ft;
+        const size_t per_sm = (size_t)std::max(1, 1024 / std::max(32, h->last_threads));
+        A.top_t = (P.top_R > 0 && top_bytes(P, ft, true) * per_sm <= kTopAdjSmemPerSm) ? 1 : 0;
+        if (!A.top_t) A.L.adj.smem_bytes = A.L.adj.smem_top_off;
+    }
     A.Qmax = Qmax;
     A.dQmin = dQmin;
     A.dQmax = dQmax;
@@ -729,6 +746,9 @@ pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices, const 
     d.top_nfw = P.top_nfw;
     d.top_nbw = P.top_nbw;
     d.top_nints = (int)P.top_ints.size();
+    d.top_nft = P.top_nft;
+    d.top_nbt = P.top_nbt;
+    d.top_nints_fwd = P.top_nints_fwd;
     d.top_map = I(po.tmap);
     d.top_split = I(po.tsplit);
     d.top_ints = I(po.tints);

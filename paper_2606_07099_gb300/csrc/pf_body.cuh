@@ -599,7 +599,7 @@ template <typename FT, bool W>
 __device__ void top_lu(const DevPlan& P, FT* fac, size_t arena, int* bad, bool wb) {
     const int nb = P.top_nblk;
     const TopArena<FT> A = top_arena<FT>(P, arena);
-    for (int k = GTID; k < P.top_nints; k += GSZ) A.I[k] = __ldg(P.top_ints + k);
+    for (int k = GTID; k < P.top_nints_fwd; k += GSZ) A.I[k] = __ldg(P.top_ints + k);
     for (int r = GTID; r < nb; r += GSZ) stb(A.T, r, ldb(fac, __ldg(P.top_map + r)));
     gsync<W>();
     const int nt = W ? 32 : min(GSZ, kTopThreads);
@@ -621,13 +621,14 @@ __device__ void top_lu(const DevPlan& P, FT* fac, size_t arena, int* bad, bool w
 // their inverses.  (A variant with one barrier per level, recomputing L(i,k) inside each
 // Schur update, measured slower: the extra 2x2 inverse per update costs more than the
 // barrier it saves.)  The plan's top region, if any, is factored by top_lu in `top`
-// (shared memory; written back into fac with `wb`).  Returns nonzero if a pivot was
-// singular.
+// (shared memory; written back into fac with `wb`), or with top == kNoTop by the level
+// schedule like the rest.  Returns nonzero if a pivot was singular.
 template <typename FT, bool W>
 __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad, size_t top, bool wb) {
     int bad = 0;
     if (!W && threadIdx.x == 0) *s_bad = 0;
-    const int n_sparse = P.top_R ? P.top_l0 : P.n_levels;
+    const bool rg = P.top_R > 0 && top != kNoTop;  // kNoTop: every level by the schedule
+    const int n_sparse = rg ? P.top_l0 : P.n_levels;
     for (int l = 0; l < n_sparse; ++l) {
         // FP32 factor: two items per thread and round, so that two chains of loads are in
         // flight (within a level the pivots read, the L blocks scaled and the Schur
@@ -707,7 +708,7 @@ __device__ int phase_lu(const DevPlan& P, FT* fac, int* s_bad, size_t top, bool 
         }
         gsync<W>();
     }
-    if (P.top_R) top_lu<FT, W>(P, fac, top, &bad, wb);
+    if (rg) top_lu<FT, W>(P, fac, top, &bad, wb);
     if (W) return __any_sync(0xffffffffu, bad);
     if (bad) *s_bad = 1;
     gsync<W>();
@@ -940,6 +941,105 @@ __device__ void top_solve(const DevPlan& P, const FT* fac, FT* x, size_t arena) 
     gsync<W>();
 }
 
+// The region's transposed sweeps, (L U)^T x = b (the adjoint's solve), by one warp with
+// the region rows' x in registers as in top_sweeps.  U^T forward, ascending columns j:
+// the column's first round forms x_j <- P_j^-T x_j (the owner keeps it), every round
+// updates rows k > j with U(j,k)^T x_j.  L^T backward, descending columns i: rows k < i
+// with L(i,k)^T x_i.  Reads ts, hands row i's solution to out(i, x0, x1).
+template <typename FT, typename Out>
+__device__ __forceinline__ void top_sweeps_t(const DevPlan& P, const TopArena<FT>& A, int lane,
+                                             const FT* ts, Out out) {
+    const int R = P.top_R;
+    const int* piv = A.I;
+    const int* ftk = A.I + P.top_nints_fwd;
+    const int* ft = ftk + P.top_nft;
+    const int* btk = ft + 32 * P.top_nft;
+    const int* bt = btk + P.top_nbt;
+    const FT* T = A.T;
+    FT v0[kTopSlots], v1[kTopSlots];
+#pragma unroll
+    for (int j = 0; j < kTopSlots; ++j) {
+        const int i = j * 32 + lane;
+        v0[j] = i < R ? ts[2 * i] : FT(0);
+        v1[j] = i < R ? ts[2 * i + 1] : FT(0);
+    }
+#pragma unroll 4
+    for (int u = 0; u < P.top_nft; ++u) {
+        const int kf = ftk[u], k = kf >> 1, e = ft[u * 32 + lane];
+        const Blk<FT> m = ldb(T, max(e, 0) & 0xffff);
+        const Blk<FT> d = ldb(T, piv[k]);
+        const FT y0 = __shfl_sync(0xffffffffu, top_slot(v0, k >> 5), k & 31);
+        const FT y1 = __shfl_sync(0xffffffffu, top_slot(v1, k >> 5), k & 31);
+        const bool first = (kf & 1) != 0;
+        const FT x0 = first ? d.a * y0 + d.c * y1 : y0;
+        const FT x1 = first ? d.b * y0 + d.d * y1 : y1;
+        const bool own = first && (k & 31) == lane;
+#pragma unroll
+        for (int j = 0; j < kTopSlots; ++j) {
+            v0[j] = own && (k >> 5) == j ? x0 : v0[j];
+            v1[j] = own && (k >> 5) == j ? x1 : v1[j];
+        }
+        top_upd(v0, v1, e >= 0 ? e >> 16 : -1, Blk<FT>{m.a, m.c, m.b, m.d}, x0, x1);
+    }
+#pragma unroll 4
+    for (int u = 0; u < P.top_nbt; ++u) {
+        const int k = btk[u], e = bt[u * 32 + lane];
+        const Blk<FT> m = ldb(T, max(e, 0) & 0xffff);
+        const FT x0 = __shfl_sync(0xffffffffu, top_slot(v0, k >> 5), k & 31);
+        const FT x1 = __shfl_sync(0xffffffffu, top_slot(v1, k >> 5), k & 31);
+        top_upd(v0, v1, e >= 0 ? e >> 16 : -1, Blk<FT>{m.a, m.c, m.b, m.d}, x0, x1);
+    }
+#pragma unroll
+    for (int j = 0; j < kTopSlots; ++j) {
+        const int i = j * 32 + lane;
+        if (i < R) out(i, v0[j], v1[j]);
+    }
+}
+
+// The transposed sweeps over the top region (after the U^T levels below it): each region
+// row's part left of the region (the mirrors of its L part, transposed; top_g lanes per
+// row) into the region's copy of x, then top_sweeps_t by one warp.  The region's blocks
+// and all its lists must be staged (top_stage).
+template <typename FT, bool W>
+__device__ void top_solve_t(const DevPlan& P, const FT* fac, FT* x, size_t arena) {
+    const int p0 = P.top_p0, G = P.top_g;
+    const TopArena<FT> A = top_arena<FT>(P, arena);
+    const int sub = GTID & (G - 1), nrg = GSZ / G;
+    for (int pb = p0; pb < P.n; pb += nrg) {  // every lane runs the same rounds
+        const int p = pb + GTID / G;
+        const bool act = p < P.n;
+        FT s0 = FT(0), s1 = FT(0);
+        if (act)
+            row_gather<FT, true>(P, fac, x, __ldg(P.lu_ptr + p) + sub, __ldg(P.top_split + p - p0),
+                                 G, s0, s1);
+        for (int o = G >> 1; o; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (act && sub == 0) {
+            A.ts[2 * (p - p0)] = x[2 * p] - s0;
+            A.ts[2 * (p - p0) + 1] = x[2 * p + 1] - s1;
+        }
+    }
+    gsync<W>();
+    if (GTID < 32)
+        top_sweeps_t<FT>(P, A, GTID, A.ts, [x, p0](int i, FT x0, FT x1) {
+            x[2 * (p0 + i)] = x0;
+            x[2 * (p0 + i) + 1] = x1;
+        });
+    gsync<W>();
+}
+
+// Stages the region's factored blocks (from fac) and all its lists, for the transposed
+// sweeps.
+template <typename FT, bool W>
+__device__ void top_stage(const DevPlan& P, const FT* fac, size_t arena) {
+    const TopArena<FT> A = top_arena<FT>(P, arena);
+    for (int k = GTID; k < P.top_nints; k += GSZ) A.I[k] = __ldg(P.top_ints + k);
+    for (int r = GTID; r < P.top_nblk; r += GSZ) stb(A.T, r, ldb(fac, __ldg(P.top_map + r)));
+    gsync<W>();
+}
+
 // x <- (LU)^{-1} x in place (x holds 2 values per pivot): L y = x by ascending levels,
 // then U x = y by descending levels.  With `top` (the top region as phase_lu left it in
 // shared memory) the region's levels are swept there, one column at a time.
@@ -960,13 +1060,17 @@ __device__ void phase_solve(const DevPlan& P, const FT* fac, FT* x, size_t top =
 
 // x <- (LU)^{-T} x: U^T y = x by ascending levels (row p of U^T = mirrored L-part
 // positions of row p), then L^T x = y by descending levels (mirrored U-part positions).
+// With `top` (the region staged there by top_stage) the region's levels are swept there.
 template <typename FT, bool W>
-__device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x) {
-    for (int l = 0; l < P.n_levels; ++l) {
+__device__ void phase_solve_t(const DevPlan& P, const FT* fac, FT* x, size_t top = kNoTop) {
+    const bool dt = top != kNoTop && P.top_R > 0;
+    const int nl = dt ? P.top_l0 : P.n_levels;
+    for (int l = 0; l < nl; ++l) {
         sweep_level<FT, false, true, W>(P, fac, x, l);
         gsync<W>();
     }
-    for (int l = P.n_levels - 1; l >= 0; --l) {
+    if (dt) top_solve_t<FT, W>(P, fac, x, top);
+    for (int l = nl - 1; l >= 0; --l) {
         sweep_level<FT, true, true, W>(P, fac, x, l);
         gsync<W>();
     }
@@ -1344,16 +1448,18 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             }
             phase_fill<false, QL>(P, a, fac);
             gsync<false>();
-            if (phase_lu<FT, false>(P, fac, &s_bad, K.smem_top_off, true)) {
+            if (phase_lu<FT, false>(P, fac, &s_bad, A.top_t ? K.smem_top_off : kNoTop, true)) {
                 astat = 3;
                 break;
             }
             have = true;
             refactored = true;
         }
+        const size_t tt = (P.top_R && A.top_t) ? K.smem_top_off : kNoTop;
+        if (tt != kNoTop) top_stage<FT, false>(P, fac, tt);  // the factored region
         for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.F[k]);
         gsync<false>();
-        phase_solve_t<FT, false>(P, fac, x);
+        phase_solve_t<FT, false>(P, fac, x, tt);
         for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] = double(x[k]);
         gsync<false>();
         bool conv = false;
@@ -1381,7 +1487,7 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(DevPlan P, AdjArgs A) {
             if (s >= A.ir_max || !(rmax <= 1e300)) break;
             for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) x[k] = FT(a.r[k]);
             gsync<false>();
-            phase_solve_t<FT, false>(P, fac, x);
+            phase_solve_t<FT, false>(P, fac, x, tt);
             for (int k = threadIdx.x; k < 2 * P.n; k += blockDim.x) a.dz[k] += double(x[k]);
             gsync<false>();
         }

@@ -13,9 +13,10 @@ struct DevPlan {
     // shared memory; top_R = 0: none): first level and row, rows, blocks, lanes per row of
     // its part left of the region, and the lengths of its staged lists
     int top_l0, top_p0, top_R, top_nblk, top_g, top_nl, top_nfw, top_nbw, top_nints;
+    int top_nft, top_nbt, top_nints_fwd;  // transposed rounds; the forward solve's list length
     const int* top_map;    // [top_nblk] fac position of each region block
     const int* top_split;  // [top_R] first entry of each region row inside the region
-    const int* top_ints;   // piv | lc_ptr | lc | tr_ptr | fw_ptr | fw | bw_ptr | bw (see Plan)
+    const int* top_ints;   // piv | lc_ptr | lc | tr_ptr | fwk | fw | bwk | bw | ftk | ft | btk | bt
     const int2* top_tr;    // Schur triples: (target, L block | U block << 16)
     const int* y_ptr;
     const int* y_idx;
@@ -119,6 +120,7 @@ struct MultiArgs {
 
 struct AdjArgs {
     int batch;
+    int top_t;  // sweep the plan's top region in shared memory (else walk its levels)
     int ir_max;
     double ir_rtol;
     const double* dVm;

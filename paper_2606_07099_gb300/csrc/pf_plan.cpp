@@ -108,7 +108,8 @@ static BuildStatus build_top(Plan& P, int l0, Lanes lanes) {
     P.top_ints.clear();
     P.top_tr_t.clear();
     P.top_tr_lu.clear();
-    P.top_nl = P.top_nfw = P.top_nbw = 0;
+    P.top_nl = P.top_nfw = P.top_nbw = P.top_nft = P.top_nbt = 0;
+    P.top_nints_fwd = 0;
     P.top_g = 1;
     if (R == 0) return BUILD_OK;
     std::vector<int> base(R + 1, 0);
@@ -193,6 +194,24 @@ static BuildStatus build_top(Plan& P, int l0, Lanes lanes) {
             const int v = I[at + u];
             I[at + u] = ((R - 1 - (v >> 1)) << 1) | (v & 1);
         }
+    }
+    P.top_nints_fwd = (int)I.size();
+    // the transposed sweeps of (L U)^T x = b (the adjoint): U^T forward, ascending columns j
+    // with U's row j, (k, U(j, k)) for k > j, the first round of each column applying the
+    // transposed pivot inverse; then L^T backward, descending columns i with L's row i,
+    // (k, L(i, k)) for k < i
+    std::vector<std::vector<std::pair<int, int>>> urow(R), lrow_desc(R);
+    for (int j = p0; j < n; ++j) {
+        for (int e = P.lu_diag[j] + 1; e < P.lu_ptr[j + 1]; ++e)
+            urow[j - p0].push_back({P.lu_col[e] - p0, loc(j, e)});
+        for (int e = P.top_split[j - p0]; e < P.lu_diag[j]; ++e)
+            lrow_desc[n - 1 - j].push_back({P.lu_col[e] - p0, loc(j, e)});
+    }
+    rounds(urow, true, P.top_nft);
+    {
+        const size_t at = I.size();
+        rounds(lrow_desc, false, P.top_nbt);
+        for (int u = 0; u < P.top_nbt; ++u) I[at + u] = R - 1 - I[at + u];
     }
     return BUILD_OK;
 }

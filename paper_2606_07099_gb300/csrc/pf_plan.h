@@ -54,9 +54,13 @@ struct Plan {
     // k, their L blocks (i, k), i > k), bwk[nbw] and bw[32 nbw] (descending columns, their
     // U blocks (i, k), i < k).  A round holds one entry per lane: the lane that owns row i
     // (i % 32) gets (i / 32) << 16 | block, the others -1; fwk holds the round's column,
-    // bwk its column << 1 | (1 for the column's first round)
+    // bwk its column << 1 | (1 for the column's first round).  The forward solve's lists
+    // end at top_nints_fwd; after them, the transposed sweeps' rounds (the adjoint):
+    // ftk[nft] and ft[32 nft] (ascending columns j, U's row j: (k, U(j, k)), k > j; ftk
+    // j << 1 | first, the first round applying the transposed pivot inverse), btk[nbt]
+    // and bt[32 nbt] (descending columns i, L's row i: (k, L(i, k)), k < i; btk i)
     std::vector<int> top_ints;
-    int top_nl = 0, top_nfw = 0, top_nbw = 0;
+    int top_nl = 0, top_nfw = 0, top_nbw = 0, top_nft = 0, top_nbt = 0, top_nints_fwd = 0;
     // Schur triples of the region pivots: (target, L block | U block << 16), per pivot
     std::vector<int> top_tr_t, top_tr_lu;
     int top_blocks() const { return (int)top_map.size(); }

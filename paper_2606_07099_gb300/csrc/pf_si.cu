@@ -539,7 +539,7 @@ __device__ void si_top_lu(const DevPlan& P, const SiLayout& L, const Pack<FT>& k
     const int nb = P.top_nblk;
     const bool resident = nsc <= L.top_slots;
     int* I = si_top_arena<FT>(P, L, 0).I;
-    for (int q = (int)threadIdx.x; q < P.top_nints; q += (int)blockDim.x) I[q] = __ldg(P.top_ints + q);
+    for (int q = (int)threadIdx.x; q < P.top_nints_fwd; q += (int)blockDim.x) I[q] = __ldg(P.top_ints + q);
     for (int c0 = 0; c0 < nsc; c0 += L.top_slots) {
         const int m = min(L.top_slots, nsc - c0);  // a power of two that divides blockDim
         for (int u = (int)threadIdx.x; u < m * nb; u += (int)blockDim.x) {

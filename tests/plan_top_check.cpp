@@ -10,7 +10,9 @@
 //      and column the list says);
 //   3. solves L U x = b with reference sweeps, and with level sweeps below the region plus
 //      the region's forward and backward rounds (one entry per lane and round, the row
-//      owned by lane i mod 32, slot i / 32).
+//      owned by lane i mod 32, slot i / 32);
+//   4. solves (L U)^T x = b (the adjoint's solve) both ways, with the region's transposed
+//      rounds.
 // Prints the region's size and the largest differences; exits 1 if a list entry is wrong
 // or a difference exceeds 1e-12.
 #include <algorithm>
@@ -118,7 +120,7 @@ int main(int argc, char** argv) {
     const int *fwk = trp + R + 1, *fw = fwk + P.top_nfw, *bwk = fw + 32 * P.top_nfw,
               *bw = bwk + P.top_nbw;
     if (R > 0) {
-        if ((size_t)(bw + 32 * P.top_nbw - I) != P.top_ints.size()) ++bad;
+        if ((int)(bw + 32 * P.top_nbw - I) != P.top_nints_fwd) ++bad;
         T.resize(P.top_blocks());
         for (int r = 0; r < P.top_blocks(); ++r) T[r] = Y[P.top_map[r]];
         for (int k = 0; k < R; ++k) {
@@ -224,6 +226,80 @@ int main(int argc, char** argv) {
     }
     double dsol = 0.0;
     for (int k = 0; k < 2 * n; ++k) dsol = std::max(dsol, std::fabs(xs[k] - xr[k]));
-    std::printf("list errors %lld, factor max diff %.3e, solution max diff %.3e\n", bad, dfac, dsol);
-    return (bad == 0 && dfac <= 1e-12 && dsol <= 1e-12) ? 0 : 1;
+
+    // 4. (L U)^T x = b (the adjoint's solve): U^T forward then L^T backward, reference
+    //    against level sweeps plus the region's transposed rounds
+    auto applyT = [](const B& m, double x0, double x1, double* y) {  // y -= M^T x
+        y[0] -= m.a * x0 + m.c * x1;
+        y[1] -= m.b * x0 + m.d * x1;
+    };
+    auto pivT = [](const B& d, double* y) {  // y <- Dinv^T y
+        const double y0 = y[0], y1 = y[1];
+        y[0] = d.a * y0 + d.c * y1;
+        y[1] = d.b * y0 + d.d * y1;
+    };
+    std::vector<double> tr = b0, tp = b0;
+    for (int p = 0; p < n; ++p) {  // row p of U^T: the mirrors of row p's L part
+        for (int e = P.lu_ptr[p]; e < P.lu_diag[p]; ++e)
+            applyT(X[P.lu_mirror[e]], tr[2 * P.lu_col[e]], tr[2 * P.lu_col[e] + 1], &tr[2 * p]);
+        pivT(X[P.lu_diag[p]], &tr[2 * p]);
+    }
+    for (int p = n - 1; p >= 0; --p)  // row p of L^T: the mirrors of row p's U part
+        for (int e = P.lu_diag[p] + 1; e < P.lu_ptr[p + 1]; ++e)
+            applyT(X[P.lu_mirror[e]], tr[2 * P.lu_col[e]], tr[2 * P.lu_col[e] + 1], &tr[2 * p]);
+    for (int p = 0; p < p0; ++p) {
+        for (int e = P.lu_ptr[p]; e < P.lu_diag[p]; ++e)
+            applyT(Y[P.lu_mirror[e]], tp[2 * P.lu_col[e]], tp[2 * P.lu_col[e] + 1], &tp[2 * p]);
+        pivT(Y[P.lu_diag[p]], &tp[2 * p]);
+    }
+    if (R > 0) {
+        const int *ftk = bw + 32 * P.top_nbw, *ft = ftk + P.top_nft, *btk = ft + 32 * P.top_nft,
+                  *bt = btk + P.top_nbt;
+        if ((int)(ftk - I) != P.top_nints_fwd || (size_t)(bt + 32 * P.top_nbt - I) != P.top_ints.size()) ++bad;
+        std::vector<double> ts(2 * R);
+        for (int p = p0; p < n; ++p) {
+            double s[2] = {tp[2 * p], tp[2 * p + 1]};
+            for (int e = P.lu_ptr[p]; e < P.top_split[p - p0]; ++e)
+                applyT(Y[P.lu_mirror[e]], tp[2 * P.lu_col[e]], tp[2 * P.lu_col[e] + 1], s);
+            ts[2 * (p - p0)] = s[0];
+            ts[2 * (p - p0) + 1] = s[1];
+        }
+        int lastj = -1;
+        for (int u = 0; u < P.top_nft; ++u) {
+            const int j = ftk[u] >> 1;
+            if (ftk[u] & 1) {
+                if (j != lastj + 1) ++bad;  // every column, ascending
+                lastj = j;
+                pivT(T[piv[j]], &ts[2 * j]);
+            }
+            for (int l = 0; l < 32; ++l) {
+                const int v = ft[u * 32 + l];
+                if (v < 0) continue;
+                const int k = (v >> 16) * 32 + l;
+                if (!at(v & 0xffff, j, k) || k <= j) ++bad;  // U(j, k), k > j
+                applyT(T[v & 0xffff], ts[2 * j], ts[2 * j + 1], &ts[2 * k]);
+            }
+        }
+        if (lastj != R - 1) ++bad;
+        for (int u = 0; u < P.top_nbt; ++u) {
+            const int i = btk[u];
+            if (u > 0 && i > btk[u - 1]) ++bad;  // descending
+            for (int l = 0; l < 32; ++l) {
+                const int v = bt[u * 32 + l];
+                if (v < 0) continue;
+                const int k = (v >> 16) * 32 + l;
+                if (!at(v & 0xffff, i, k) || k >= i) ++bad;  // L(i, k), k < i
+                applyT(T[v & 0xffff], ts[2 * i], ts[2 * i + 1], &ts[2 * k]);
+            }
+        }
+        for (int k = 0; k < 2 * R; ++k) tp[2 * p0 + k] = ts[k];
+    }
+    for (int p = p0 - 1; p >= 0; --p)
+        for (int e = P.lu_diag[p] + 1; e < P.lu_ptr[p + 1]; ++e)
+            applyT(Y[P.lu_mirror[e]], tp[2 * P.lu_col[e]], tp[2 * P.lu_col[e] + 1], &tp[2 * p]);
+    double dsolt = 0.0;
+    for (int k = 0; k < 2 * n; ++k) dsolt = std::max(dsolt, std::fabs(tp[k] - tr[k]));
+    std::printf("list errors %lld, factor max diff %.3e, solution max diff %.3e, transposed %.3e\n",
+                bad, dfac, dsol, dsolt);
+    return (bad == 0 && dfac <= 1e-12 && dsol <= 1e-12 && dsolt <= 1e-12) ? 0 : 1;
 }

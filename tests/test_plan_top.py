@@ -2,7 +2,7 @@
 LU.  `plan_top_check.cpp` (built here against the planner's source) factors a random
 matrix with the plan's filled pattern by a right-looking block LU in pivot order and by
 the plan (level schedule below the region, the region's pivot lists above), checks every
-list entry against the pattern, and solves L U x = b both ways."""
+list entry against the pattern, and solves L U x = b and (L U)^T x = b both ways."""
 import os
 import shutil
 import subprocess
