@@ -626,8 +626,29 @@ def gpu_leg(args, rank, world):
     rese = SolveResult(Vm=out_host[0], Va=out_host[1], Pg=None, Qg=None, iters=None,
                        status=st_host, final_mismatch=None)
 
-    def e2e():  # the default plan (a top region slows this network's per-scenario kernels)
-        pf.solve_host(*host_views, out=rese, **opts)
+    # two ways through the public API, the faster kept (setup, not timed): the default
+    # plan's per-scenario kernels (what pf_solve_host picks by itself), and the headline's
+    # plan and interleaved shape given explicitly
+    e2e_ways = {"per_scenario": (pf, dict(opts))}
+    tm = tuned.get("mixed", {})
+    if tm.get("placement") == 5:
+        e2e_ways["interleaved"] = (pfh, dict(opts, placement=5, pack=tm["pack"],
+                                             cluster=tm["cluster"],
+                                             group_threads=tm["group_threads"]))
+    e2e_ms = {}
+    for wname, (pfx, kw) in e2e_ways.items():
+        pfx.solve_host(*host_views, out=rese, **kw)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            pfx.solve_host(*host_views, out=rese, **kw)
+        torch.cuda.synchronize(dev)
+        e2e_ms[wname] = (time.perf_counter() - t0) / 3 * 1e3
+    e2e_way = min(e2e_ms, key=e2e_ms.get)
+    e2e_pf, e2e_kw = e2e_ways[e2e_way]
+
+    def e2e():
+        e2e_pf.solve_host(*host_views, out=rese, **e2e_kw)
 
     none = [float("nan")]
     with ClockSampler(dev.index) as clk:
@@ -845,7 +866,8 @@ def gpu_leg(args, rank, world):
         "e2e": {"value": over_ranks(world, dev, 0.0, conve)[1] * K / (T_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * nb * 8, "d2h_bytes_per_step": 2 * N * nb * 8 + 4 * N,
                 "api": "pf_solve_host: the solve kernel reads the inputs from and writes Vm, Va "
-                       "and status to page-locked host memory in place"},
+                       "and status to page-locked host memory in place",
+                "kernel": e2e_way, "setup_ms": e2e_ms},
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": f64 / (ms_launch / 1e3) / 1e12, "peak": peak64,
                      "unit": "TFLOP/s", "frac": f64 / (ms_launch / 1e3) / 1e12 / peak64,
