@@ -669,9 +669,11 @@ def autotune_multi(items, tol=1e-8, max_iter=20, precision="mixed", ir_steps=2, 
 
 
 # Schedule candidates of the plan autotuner: the ordering's degree slack and the top
-# region's row and block caps (split rules at their defaults).
+# region's row and block caps (split rules at their defaults), and a small region on a
+# network of any size.
 SCHEDULES = tuple({"order_slack": sl, "top_rows": tr, "top_blocks": tb}
-                  for sl in (0, 1) for tr, tb in ((4, 2048), (4, 4096), (0, 0)))
+                  for sl in (0, 1) for tr, tb in ((4, 2048), (4, 4096), (0, 0))) + (
+    {"order_slack": 1, "top_rows": 2, "top_blocks": 2048, "top_min_pivots": 0},)
 
 
 def _time_ms(fn, reps=3):
