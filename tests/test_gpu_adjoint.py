@@ -31,14 +31,18 @@ def cotangents(n, nb, seed):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("name,idx", [("c0", range(0, 64, 3)), ("c1", [0, 7, 4095]),
-                                      ("c2", [0, 1023]), ("c3", [0, 85, 170, 255])])
-def test_adjoint_matches_oracle(mods, name, idx, precision):
+@pytest.mark.parametrize("name,idx,threads", [("c0", range(0, 64, 3), 0), ("c1", [0, 7, 4095], 0),
+                                              ("c2", [0, 1023], 0), ("c3", [0, 85, 170, 255], 0),
+                                              ("c3", [3, 200], 1024)])
+def test_adjoint_matches_oracle(mods, name, idx, threads, precision):
+    """The adjoint against the oracle's; C2, and C3 on 1024-thread CTAs, take the top
+    region in their transposed solves, C3 on its default shape walks its levels."""
     torch, pm = mods
     g, sc = workload(name)
     pf = pm.PowerFlow.from_grid(g)
     Pd, Qd, Pg, Vset = to_dev(sc)
-    res = pf.solve(Pd, Qd, Pg, Vset, precision=precision, ir_steps=1, keep_factors=True)
+    res = pf.solve(Pd, Qd, Pg, Vset, precision=precision, ir_steps=1, keep_factors=True,
+                   group_threads=threads, placement=3 if threads else 0)
     cts = cotangents(sc.n, g.n_bus, 5)
     dev = [torch.as_tensor(c, device="cuda") for c in cts]
     gr = pf.adjoint(*dev)

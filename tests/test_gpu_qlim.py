@@ -127,15 +127,19 @@ def _rel(a, b):
     return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
 
 
+@pytest.mark.parametrize("plan", [None, {"top_min_pivots": 0}])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_qlim_adjoint_matches_oracle(pm, precision):
+def test_qlim_adjoint_matches_oracle(pm, precision, plan):
     """pf_adjoint_qlim on each scenario's final partition against the oracle's
-    adjoint_qlim (itself pinned by central differences), random cotangents, 1e-6."""
+    adjoint_qlim (itself pinned by central differences), random cotangents, 1e-6; also
+    on a plan with a top region (the solve's factorisation and the adjoint's transposed
+    solve take it)."""
     import torch
     g = configs.grid("c1")
     sc = configs.scenarios("c1", 96, g)
     Qmin, Qmax, Y = limits(g, sc, 4)
-    pf = pm.PowerFlow.from_grid(g)
+    pf = pm.PowerFlow.from_grid(g, plan)
+    assert (pf.info()["top_pivots"] > 0) == (plan is not None)
     dev = to_dev(sc)
     tq = [torch.as_tensor(a, device="cuda") for a in (Qmin, Qmax)]
     r = pf.solve_qlim(*dev, *tq, tol=1e-10, max_iter=30, precision=precision, keep_factors=True)
