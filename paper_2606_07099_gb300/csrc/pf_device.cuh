@@ -171,6 +171,9 @@ struct SiLayout {
 
 struct SiArgs {
     int batch;
+    // packs of the launch: pack k holds scenarios k q + min(k, r) .. of count q + (k < r)
+    // (q = batch / npacks, r = batch % npacks; at most S each)
+    int npacks, q, r;
     int max_iter;
     int ir_steps;
     double tol;

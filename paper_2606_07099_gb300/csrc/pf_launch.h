@@ -31,6 +31,9 @@ cudaError_t launch_solve_si(const DevPlan& P, const SiArgs& A, cudaStream_t s);
 // Whether a pack shape can be scheduled on the current device (at least one cluster).
 template <typename FT>
 cudaError_t si_shape_fits(int S, int cluster, int threads, size_t smem, bool* fits);
+// CTAs of the shape one SM holds (cluster 1), or clusters the GPU holds; 0: cannot run.
+template <typename FT>
+cudaError_t si_resident(int S, int cluster, int threads, size_t smem, int* n);
 // Device address of pf_solve_noalloc's static scratch array on the current device
 // (pf_noalloc.cu; called once per handle by pf_create).
 cudaError_t noalloc_lookup(void** out);

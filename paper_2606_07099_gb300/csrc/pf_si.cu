@@ -769,8 +769,10 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
     const int NS = (int)(blockDim.x / S);
     const unsigned rank = cluster_rank(), C = cluster_ncta(), pack = cluster_index();
     const int gs = (int)rank * NS + slot, TS = (int)C * NS;
-    const int b = (int)pack * S + s;
-    const bool valid = b < A.batch;
+    // this pack's scenarios: b0 .. b0 + nb - 1 in lanes 0 .. nb - 1
+    const int b0 = (int)pack * A.q + min((int)pack, A.r), nb = A.q + ((int)pack < A.r ? 1 : 0);
+    const int b = b0 + s;
+    const bool valid = s < nb;
     const Pack<FT> k = carve_pack<FT>(A, pack);
     int round = 0;
 
@@ -783,10 +785,10 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
     // memory and each transaction crosses the chip-to-chip link
     const int nflat = S * P.n_bus;
     for (int f = (int)(rank * blockDim.x + threadIdx.x); f < nflat; f += (int)(C * blockDim.x)) {
-        const int sf = f / P.n_bus, i = f - sf * P.n_bus, bf = (int)pack * S + sf;
+        const int sf = f / P.n_bus, i = f - sf * P.n_bus, bf = b0 + sf;
         const int t = __ldg(P.bus_type + i);
         double vm = 1.0, psp = 0.0, qsp = 0.0;
-        if (bf < A.batch) {
+        if (sf < nb) {
             const size_t r = (size_t)bf * P.n_bus + i;
             if (t != 0) vm = A.Vset[r];
             psp = (t == 1 ? A.Pg[r] : 0.0) - A.Pd[r];
@@ -852,8 +854,8 @@ __global__ void __launch_bounds__(1024, 1) nr_solve_si_kernel(DevPlan P, SiArgs 
     // Step 2 (Eq. F2_completion) and outputs, from the state of each scenario's last
     // mismatch evaluation; written in row order, like the inputs were read
     for (int f = (int)(rank * blockDim.x + threadIdx.x); f < nflat; f += (int)(C * blockDim.x)) {
-        const int sf = f / P.n_bus, i = f - sf * P.n_bus, bf = (int)pack * S + sf;
-        if (bf >= A.batch) continue;
+        const int sf = f / P.n_bus, i = f - sf * P.n_bus, bf = b0 + sf;
+        if (sf >= nb) continue;
         const size_t o = (size_t)i * S + sf, r = (size_t)bf * P.n_bus + i;
         const int t = __ldg(P.bus_type + i);
         const double2 m = ldm<CL>(k.M + o), v = ldm<CL>(k.V + o), I = ldm<CL>(k.I + o);
@@ -914,7 +916,7 @@ static cudaError_t launch_s(const DevPlan& P, const SiArgs& A, cudaStream_t st) 
     e = ensure_smem_limit(reinterpret_cast<const void*>(si::nr_solve_si_kernel<FT, S, CL>),
                           A.L.smem_bytes);
     if (e != cudaSuccess) return e;
-    const int packs = (A.batch + S - 1) / S;
+    const int packs = A.npacks;
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = si_config<FT, S, CL>(packs * A.L.cluster, A.L.cluster,
                                                         A.L.threads, A.L.smem_bytes, st, at);
@@ -940,47 +942,44 @@ cudaError_t launch_solve_si(const DevPlan& P, const SiArgs& A, cudaStream_t s) {
     }
 }
 
+// How many of the shape's CTAs one SM holds (one CTA per pack), or how many of its
+// clusters the GPU holds (clusters); 0 if the shape cannot run.
 template <typename FT, int S, bool CL>
-static cudaError_t fits_s(int cluster, int threads, size_t smem, bool* fits) {
+static cudaError_t resident_s(int cluster, int threads, size_t smem, int* n) {
+    *n = 0;
     cudaError_t e = prepare<FT, S, CL>();
     if (e != cudaSuccess) return e;
     if (ensure_smem_limit(reinterpret_cast<const void*>(si::nr_solve_si_kernel<FT, S, CL>), smem) !=
         cudaSuccess) {
         cudaGetLastError();  // more shared memory than a CTA may have: the shape does not fit
-        *fits = false;
         return cudaSuccess;
     }
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = si_config<FT, S, CL>(cluster, cluster, threads, smem, 0, at);
-    int n = 0;
     if (CL) {
-        e = cudaOccupancyMaxActiveClusters(&n, si::nr_solve_si_kernel<FT, S, CL>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(n, si::nr_solve_si_kernel<FT, S, CL>, &cfg);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, si::nr_solve_si_kernel<FT, S, CL>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, si::nr_solve_si_kernel<FT, S, CL>,
                                                           threads, smem);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();  // a refused shape is an answer, not an error
-        *fits = false;
-        return cudaSuccess;
+        *n = 0;
     }
-    *fits = n > 0;
     return cudaSuccess;
 }
 
 template <typename FT, int S>
-static cudaError_t fits_c(int cluster, int threads, size_t smem, bool* fits) {
-    return cluster > 1 ? fits_s<FT, S, true>(cluster, threads, smem, fits)
-                       : fits_s<FT, S, false>(cluster, threads, smem, fits);
+static cudaError_t resident_c(int cluster, int threads, size_t smem, int* n) {
+    return cluster > 1 ? resident_s<FT, S, true>(cluster, threads, smem, n)
+                       : resident_s<FT, S, false>(cluster, threads, smem, n);
 }
 
-// The answer is kept per (device, shape), so that only a shape's first solve queries the
-// occupancy API (later calls may be recorded into a CUDA graph).
 template <typename FT>
-cudaError_t si_shape_fits(int S, int cluster, int threads, size_t smem, bool* fits) {
-    *fits = false;
+cudaError_t si_resident(int S, int cluster, int threads, size_t smem, int* n) {
+    *n = 0;
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, size_t>, bool> known;
+    static std::map<std::tuple<int, int, int, int, size_t>, int> known;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -989,22 +988,30 @@ cudaError_t si_shape_fits(int S, int cluster, int threads, size_t smem, bool* fi
         std::lock_guard<std::mutex> lock(mu);
         const auto it = known.find(key);
         if (it != known.end()) {
-            *fits = it->second;
+            *n = it->second;
             return cudaSuccess;
         }
     }
     switch (S) {
-        case 2: e = fits_c<FT, 2>(cluster, threads, smem, fits); break;
-        case 4: e = fits_c<FT, 4>(cluster, threads, smem, fits); break;
-        case 8: e = fits_c<FT, 8>(cluster, threads, smem, fits); break;
-        case 16: e = fits_c<FT, 16>(cluster, threads, smem, fits); break;
-        case 32: e = fits_c<FT, 32>(cluster, threads, smem, fits); break;
+        case 2: e = resident_c<FT, 2>(cluster, threads, smem, n); break;
+        case 4: e = resident_c<FT, 4>(cluster, threads, smem, n); break;
+        case 8: e = resident_c<FT, 8>(cluster, threads, smem, n); break;
+        case 16: e = resident_c<FT, 16>(cluster, threads, smem, n); break;
+        case 32: e = resident_c<FT, 32>(cluster, threads, smem, n); break;
         default: return cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) {
         std::lock_guard<std::mutex> lock(mu);
-        known[key] = *fits;
+        known[key] = *n;
     }
+    return e;
+}
+
+template <typename FT>
+cudaError_t si_shape_fits(int S, int cluster, int threads, size_t smem, bool* fits) {
+    int n = 0;
+    const cudaError_t e = si_resident<FT>(S, cluster, threads, smem, &n);
+    *fits = n > 0;
     return e;
 }
 
@@ -1012,5 +1019,7 @@ template cudaError_t launch_solve_si<float>(const DevPlan&, const SiArgs&, cudaS
 template cudaError_t launch_solve_si<double>(const DevPlan&, const SiArgs&, cudaStream_t);
 template cudaError_t si_shape_fits<float>(int, int, int, size_t, bool*);
 template cudaError_t si_shape_fits<double>(int, int, int, size_t, bool*);
+template cudaError_t si_resident<float>(int, int, int, size_t, int*);
+template cudaError_t si_resident<double>(int, int, int, size_t, int*);
 
 }  // namespace pf
