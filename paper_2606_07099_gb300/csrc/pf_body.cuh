@@ -432,7 +432,8 @@ template <typename FT>
 struct TopArena {
     FT* T;   // the region's blocks
     FT* ts;  // the region rows' part of the solve vector
-    int* I;  // the plan's staged lists: piv | lc_ptr | lc | tr_ptr | fw_ptr | fw | bw_ptr | bw
+    int* I;  // the plan's staged lists: piv | lc_ptr | lc | tr_ptr | fwk | fw | bwk | bw, then
+             // for the adjoint ftk | ft | btk | bt
 };
 
 // The region's arena at byte offset `off` of the kernel's dynamic shared memory (every
@@ -470,9 +471,9 @@ __device__ __forceinline__ void top_bar(int nt) {
 // no thread reads those blocks any more (pivot k + 1 reads column k + 1 and row k + 1
 // only, and its targets lie beyond both); every thread forms the pivot inverse.
 // FP64: two barriers per pivot, as in the level schedule (L column scaling, then the
-// Schur triples): a 2x2 inverse, and the scaling repeated in every triple, would cost
-// each FP64 warp instruction the scarce FP64 pipe, so only the threads that scale an L
-// block (and thread 0) form the inverse.
+// Schur triples): a 2x2 inverse formed by every thread, and the scaling repeated in
+// every triple, would add instructions on this GPU's narrow FP64 pipe, so only the
+// threads that scale an L block (and thread 0) form the inverse.
 template <typename FT, typename Bar>
 __device__ __forceinline__ void top_factor(const DevPlan& P, const TopArena<FT>& A, int t, int nt,
                                            Bar bar, int& bk) {
