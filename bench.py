@@ -34,9 +34,11 @@ WORKLOAD = "c1"
 WORKLOAD_DESC = ("synthetic 118-bus meshed grid (186 branches, 9 transformers, 1 slack, 53 PV, "
                  "64 PQ), 4096 load scenarios x U(0.7, 1.3), flat start, tol 1e-8 pu, max 20 iterations")
 # Plan schedules the headline's tuner compares: the default plan, and top regions of
-# levels of at most 2, 3 or 4 rows whatever the network's size.
+# levels of at most 2, 3 or 5 rows whatever the network's size (and of at most 8 rows on
+# the ordering with degree slack 2).
 HEADLINE_SCHEDULES = ({}, {"top_rows": 2, "top_min_pivots": 0}, {"top_rows": 3, "top_min_pivots": 0},
-                      {"top_rows": 4, "top_min_pivots": 0})
+                      {"top_rows": 5, "top_min_pivots": 0},
+                      {"order_slack": 2, "top_rows": 8, "top_min_pivots": 0})
 METRIC = "PF solves/s at <=1e-8 pu mismatch (mixed precision form)"
 
 UNIT = "solves/s"
@@ -363,13 +365,21 @@ def gpu_leg(args, rank, world):
     # the largest workspace any section needs, allocated once (captured graphs keep its address)
     pf.workspace(N, pf.make_opts("fp64", keep_factors=True, placement=3))
     pfh = pf  # the headline solve's network plan (the default one unless tuned)
+    if args.plan:  # an explicit plan schedule for the headline solve (no schedule tuning)
+        plan = {k: int(v) for k, v in (kv.split("=") for kv in args.plan.split(","))}
+        pfh = PowerFlow.from_grid(g, plan)
     hopts = dict(opts)  # the headline solve's options
     if args.shape:  # an explicit launch shape for the headline solve (no tuning for it)
         pl, th, pk, cl = (int(v) for v in args.shape.split(","))
         hopts.update(placement=pl, group_threads=th, pack=pk, cluster=cl)
         tuned["mixed"] = {"group_threads": th, "placement": pl, "instances_per_cta": 1,
-                          "pack": pk, "cluster": cl, "fixed": True}
+                          "pack": pk, "cluster": cl, "fixed": True, "schedule": pfh.plan}
         if args.autotune and "fp64" in secs:
+            tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
+    elif args.autotune and args.plan:  # the launch shape of the given plan
+        tuned["mixed"] = {**pfh.autotune(Pd, Qd, Pg, Vset, **opts), "schedule": pfh.plan}
+        tuned["mixed_default_plan"] = pf.autotune(Pd, Qd, Pg, Vset, **opts)
+        if "fp64" in secs:
             tuned["fp64"] = pf.autotune(Pd, Qd, Pg, Vset, precision="fp64")
     elif args.autotune:  # plan schedule and launch shape, picked on these inputs (setup)
         # the headline's mixed solve: the default plan against top regions on this network
@@ -932,6 +942,9 @@ def main():
     ap.add_argument("--shape", default="",
                     help="placement,threads,pack,cluster of the headline solve instead of the "
                          "autotuned one (e.g. 3,32,0,0: per-scenario, 32 threads, global)")
+    ap.add_argument("--plan", default="",
+                    help="key=value,... plan schedule of the headline solve instead of the "
+                         "tuned one (e.g. order_slack=1,top_rows=5,top_min_pivots=0)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="scenarios the CPU oracle solves for cpu_baseline (0 = skip)")
