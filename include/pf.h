@@ -87,6 +87,8 @@ typedef struct {
                                   instead of level by level (0: none) */
     int top_levels;            /* elimination levels in the top region */
     int top_blocks;            /* 2x2 blocks the top region holds in shared memory */
+    int top_arena_bytes;       /* bytes of one scenario's top-region arena in FP64
+                                  (blocks, solve vector, index lists), at most 160 KB */
 } pf_plan_info;
 
 /* Tunables of a solve; zero-initialise and set what you need. */
@@ -230,6 +232,16 @@ pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices,
                   const double* y_re, const double* y_im, const int* bus_type,
                   pf_plan_info* info, int* pos2bus, int* lu_ptr, int* lu_col, int* lev_ptr,
                   int* j1_ptr, int* j1_col);
+
+/*
+ * pf_analyze_ex -- pf_analyze with explicit schedule choices (host, NULL = the defaults,
+ * as in pf_create_ex): the plan pf_create_ex would build, without any device work.
+ * Errors: as pf_analyze, and PF_EINVAL for schedule choices pf_create_ex refuses.
+ */
+pf_err pf_analyze_ex(int n_bus, const int* y_indptr, const int* y_indices,
+                     const double* y_re, const double* y_im, const int* bus_type,
+                     const pf_plan_opts* plan_opts, pf_plan_info* info, int* pos2bus,
+                     int* lu_ptr, int* lu_col, int* lev_ptr, int* j1_ptr, int* j1_col);
 
 /* Plan facts (host only, no device work).  PF_EINVAL on NULL arguments. */
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info);

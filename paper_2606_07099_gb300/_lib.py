@@ -26,7 +26,8 @@ class PlanInfo(C.Structure):
                 ("n_unknowns", C.c_int), ("n_block", C.c_int), ("nnz_ybus", C.c_int),
                 ("nnz_j1", C.c_int), ("nnzb_lu", C.c_int), ("n_levels", C.c_int),
                 ("schur_block_ops", C.c_longlong), ("plan_bytes", C.c_longlong),
-                ("top_pivots", C.c_int), ("top_levels", C.c_int), ("top_blocks", C.c_int)]
+                ("top_pivots", C.c_int), ("top_levels", C.c_int), ("top_blocks", C.c_int),
+                ("top_arena_bytes", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -66,6 +67,8 @@ SIGNATURES = {
     "pf_plan_opts_default": (None, [C.POINTER(PlanOpts)]),
     "pf_analyze": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanInfo), _ip, _ip, _ip, _ip,
                         _ip, _ip]),
+    "pf_analyze_ex": (_i, [_i, _ip, _ip, _dp, _dp, _ip, C.POINTER(PlanOpts), C.POINTER(PlanInfo),
+                           _ip, _ip, _ip, _ip, _ip, _ip]),
     "pf_jacobian_pattern": (_i, [_p, _ip, _ip]),
     "pf_bde_pattern": (_i, [_p, _i, _p, _p, _p]),
     "pf_export_jacobian": (_i, [_p, _i, _p, _p, _p, _p]),

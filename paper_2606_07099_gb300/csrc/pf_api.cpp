@@ -694,25 +694,31 @@ pf_err pf_create(int n_bus, const int* y_indptr, const int* y_indices, const dou
     return pf_create_ex(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, nullptr, out);
 }
 
+// The planner's parameters from the caller's schedule choices (NULL: the defaults);
+// false if a choice is out of range.
+static bool plan_params(const pf_plan_opts* o, pf::PlanParams& pp) {
+    pp = pf::PlanParams();
+    if (!o) return true;
+    if (o->order_slack < 0 || o->order_slack > 8 || o->top_rows < 0 || o->top_blocks < 0 ||
+        o->top_blocks > pf::kTopMaxBlocks || o->top_min_pivots < 0 || o->split_len < 1 ||
+        o->split_rows < 0)
+        return false;
+    pp.order_slack = o->order_slack;
+    pp.top_rows = o->top_rows;
+    pp.top_blocks = o->top_blocks;
+    pp.top_min_pivots = o->top_min_pivots;
+    pp.split_len = o->split_len;
+    pp.split_rows = o->split_rows;
+    return true;
+}
+
 pf_err pf_create_ex(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
                     const double* y_im, const int* bus_type, const pf_plan_opts* plan_opts,
                     pf_handle** out) {
     if (!out) return PF_EINVAL;
     *out = nullptr;
     pf::PlanParams pp;
-    if (plan_opts) {
-        if (plan_opts->order_slack < 0 || plan_opts->order_slack > 8 || plan_opts->top_rows < 0 ||
-            plan_opts->top_blocks < 0 || plan_opts->top_blocks > pf::kTopMaxBlocks ||
-            plan_opts->top_min_pivots < 0 ||
-            plan_opts->split_len < 1 || plan_opts->split_rows < 0)
-            return PF_EINVAL;
-        pp.order_slack = plan_opts->order_slack;
-        pp.top_rows = plan_opts->top_rows;
-        pp.top_blocks = plan_opts->top_blocks;
-        pp.top_min_pivots = plan_opts->top_min_pivots;
-        pp.split_len = plan_opts->split_len;
-        pp.split_rows = plan_opts->split_rows;
-    }
+    if (!plan_params(plan_opts, pp)) return PF_EINVAL;
     pf_handle* h = new (std::nothrow) pf_handle();
     if (!h) return PF_ENOMEM;
     pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, h->plan, pp);
@@ -817,6 +823,7 @@ static void fill_info(const pf::Plan& P, size_t plan_bytes, pf_plan_info* info) 
     info->top_pivots = P.top_R;
     info->top_levels = P.n_levels - P.top_l0;
     info->top_blocks = P.top_blocks();
+    info->top_arena_bytes = (int)top_bytes(P, 8, true);
 }
 
 pf_err pf_get_plan_info(const pf_handle* h, pf_plan_info* info) {
@@ -853,9 +860,19 @@ pf_err pf_export_jacobian(const pf_handle* h, int batch, const double* Vm, const
 pf_err pf_analyze(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
                   const double* y_im, const int* bus_type, pf_plan_info* info, int* pos2bus,
                   int* lu_ptr, int* lu_col, int* lev_ptr, int* j1_ptr, int* j1_col) {
+    return pf_analyze_ex(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, nullptr, info, pos2bus,
+                         lu_ptr, lu_col, lev_ptr, j1_ptr, j1_col);
+}
+
+pf_err pf_analyze_ex(int n_bus, const int* y_indptr, const int* y_indices, const double* y_re,
+                     const double* y_im, const int* bus_type, const pf_plan_opts* plan_opts,
+                     pf_plan_info* info, int* pos2bus, int* lu_ptr, int* lu_col, int* lev_ptr,
+                     int* j1_ptr, int* j1_col) {
     if (!info) return PF_EINVAL;
+    pf::PlanParams pp;
+    if (!plan_params(plan_opts, pp)) return PF_EINVAL;
     pf::Plan P;
-    pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, P);
+    pf::BuildStatus bs = pf::build_plan(n_bus, y_indptr, y_indices, y_re, y_im, bus_type, P, pp);
     if (bs != pf::BUILD_OK) return bs == pf::BUILD_ESINGULAR ? PF_ESINGULAR_PATTERN : PF_EINVAL;
     std::vector<unsigned char> buf;
     PlanOffsets po;

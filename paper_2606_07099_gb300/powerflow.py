@@ -46,22 +46,36 @@ def build_ybus(n_bus, f, t, r, x, b, tap):
     return indptr, idx, g, bv
 
 
-def analyze(n_bus, indptr, indices, g, bv, bus_type):
-    """Host-only symbolic analysis: (info dict, pos2bus, lu_ptr, lu_col, lev_ptr)."""
+def _plan_opts(lib, plan):
+    """pf_plan_opts: the defaults with the choices of ``plan`` (dict) applied."""
+    po = L.PlanOpts()
+    lib.pf_plan_opts_default(C.byref(po))
+    for k, v in (plan or {}).items():
+        if k not in dict(L.PlanOpts._fields_):
+            raise KeyError(f"unknown plan schedule choice {k!r}")
+        setattr(po, k, int(v))
+    return po
+
+
+def analyze(n_bus, indptr, indices, g, bv, bus_type, plan=None):
+    """Host-only symbolic analysis (pf_analyze_ex; ``plan`` as for PowerFlow): (info dict,
+    pos2bus, lu_ptr, lu_col, lev_ptr)."""
     lib = L.load()
     ip, ix = np.ascontiguousarray(indptr, np.int32), np.ascontiguousarray(indices, np.int32)
     gg, bb = np.ascontiguousarray(g, np.float64), np.ascontiguousarray(bv, np.float64)
     bt = np.ascontiguousarray(bus_type, np.int32)
+    po = _plan_opts(lib, plan)
     info = L.PlanInfo()
-    L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
-                           C.byref(info), None, None, None, None, None, None), "pf_analyze")
+    L.check(lib.pf_analyze_ex(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
+                              C.byref(po), C.byref(info), None, None, None, None, None, None),
+            "pf_analyze_ex")
     pos2bus = np.zeros(info.n_block, np.int32)
     lu_ptr = np.zeros(info.n_block + 1, np.int32)
     lu_col = np.zeros(info.nnzb_lu, np.int32)
     lev_ptr = np.zeros(info.n_levels + 1, np.int32)
-    L.check(lib.pf_analyze(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
-                           C.byref(info), _iptr(pos2bus), _iptr(lu_ptr), _iptr(lu_col),
-                           _iptr(lev_ptr), None, None), "pf_analyze")
+    L.check(lib.pf_analyze_ex(n_bus, _iptr(ip), _iptr(ix), _dptr(gg), _dptr(bb), _iptr(bt),
+                              C.byref(po), C.byref(info), _iptr(pos2bus), _iptr(lu_ptr),
+                              _iptr(lu_col), _iptr(lev_ptr), None, None), "pf_analyze_ex")
     return _info_dict(info), pos2bus, lu_ptr, lu_col, lev_ptr
 
 
@@ -141,10 +155,7 @@ class PowerFlow:
                         np.ascontiguousarray(y_im, np.float64)]
         h = C.c_void_p()
         ip, ix, g, bv = self._arrays
-        po = L.PlanOpts()
-        lib.pf_plan_opts_default(C.byref(po))
-        for k, v in (plan or {}).items():
-            setattr(po, k, int(v))
+        po = _plan_opts(lib, plan)
         self.plan = {k: getattr(po, k) for k, _ in L.PlanOpts._fields_}
         L.check(lib.pf_create_ex(self.n_bus, _iptr(ip), _iptr(ix), _dptr(g), _dptr(bv),
                                  _iptr(self.bus_type), C.byref(po), C.byref(h)), "pf_create_ex")

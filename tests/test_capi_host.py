@@ -240,3 +240,67 @@ def test_top_region_is_the_largest_allowed(pfm, name):
     assert info["top_pivots"] == rows
     assert info["top_levels"] == L - l0
     assert info["top_blocks"] == (blocks(lev_ptr[l0]) if rows else 0)
+
+
+# Schedules the bench's tuners try, with the regions their plans have: (grid, schedule,
+# (pivots, levels, blocks)).  The 118-bus grid gets regions only with top_min_pivots 0;
+# on the large grids, row caps from 4 to 32 and block caps from 4096 up all give the
+# same region, which the region's FP64 shared-memory arena (at most 160 KB: its blocks,
+# its solve vector and its lists) limits.
+REGION_SCHEDULES = [
+    ("c1", {"top_rows": 2, "top_min_pivots": 0}, (12, 9, 94)),
+    ("c1", {"top_rows": 3, "top_min_pivots": 0}, (15, 10, 117)),
+    ("c1", {"top_rows": 5, "top_min_pivots": 0}, (24, 12, 194)),
+    ("c3", {"top_rows": 4, "top_blocks": 4096}, (70, 52, 3078)),
+    ("c3", {"top_rows": 32, "top_blocks": 5000}, (70, 52, 3078)),
+    ("c5", {"order_slack": 0, "top_rows": 8, "top_blocks": 4096}, (67, 44, 2957)),
+]
+
+
+@pytest.mark.parametrize("name,plan,expect", REGION_SCHEDULES)
+def test_top_region_under_schedule_choices(pfm, name, plan, expect):
+    """pf_analyze_ex builds the plan pf_create_ex would: the region is a run of trailing
+    levels within the schedule's row cap, the 128-row limit and the block cap, its FP64
+    arena within 160 KB, with the sizes the GPU runs reported for these schedules.  On
+    the large grids the row and block caps would let it reach further down: there the
+    arena is what stops it (the planner shrinks the region only for the arena)."""
+    g = configs.raw_grid(name)
+    ip, ix, gg, bb = _ybus(pfm, g)
+    info, pos2bus, lu_ptr, lu_col, lev_ptr = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type, plan)
+    n, L = info["n_block"], info["n_levels"]
+    sizes = np.diff(lev_ptr)
+    caps = dict(top_rows=4, top_blocks=2048)
+    caps.update(plan)
+
+    def blocks(p0):
+        return sum(int(np.count_nonzero(lu_col[lu_ptr[p]:lu_ptr[p + 1]] >= p0))
+                   for p in range(p0, n))
+
+    assert (info["top_pivots"], info["top_levels"], info["top_blocks"]) == expect
+    l0 = L - info["top_levels"]
+    assert info["top_pivots"] == n - lev_ptr[l0] <= 128
+    assert np.all(sizes[l0:] <= caps["top_rows"])
+    assert info["top_blocks"] == blocks(lev_ptr[l0]) <= caps["top_blocks"]
+    a16 = lambda v: (v + 15) // 16 * 16
+    arena = info["top_arena_bytes"]
+    assert a16((info["top_blocks"] + 1) * 32) + a16(16 * info["top_pivots"]) < arena <= 160 * 1024
+    # the next level down: refused by the row or block caps (118-bus), else by the arena
+    caps_allow = (l0 > 0 and sizes[l0 - 1] <= caps["top_rows"] and n - lev_ptr[l0 - 1] <= 128
+                  and blocks(lev_ptr[l0 - 1]) <= caps["top_blocks"])
+    assert caps_allow == (name != "c1")
+
+
+def test_analyze_ex_refuses_what_create_ex_refuses(pfm, lib):
+    """Schedule choices out of range are refused on the host (PF_EINVAL), before any
+    device work, and an unknown choice name is refused by the binding."""
+    from paper_2606_07099_gb300._lib import PFError, PF_EINVAL
+    g = configs.raw_grid("c0")
+    ip, ix, gg, bb = _ybus(pfm, g)
+    for bad in ({"top_blocks": 65535}, {"order_slack": 9}, {"split_len": 0}, {"top_rows": -1}):
+        with pytest.raises(PFError) as e:
+            pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type, bad)
+        assert e.value.code == PF_EINVAL
+    with pytest.raises(KeyError):
+        pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type, {"top_row": 4})
+    base = pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type)[0]
+    assert pfm.analyze(g.n_bus, ip, ix, gg, bb, g.bus_type, {})[0] == base
